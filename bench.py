@@ -1,0 +1,438 @@
+#!/usr/bin/env python
+"""Benchmark of the statevector hot path: a 30-qubit complex128 statevector
+(16 GiB, random normalised Gaussian amplitudes) through a seeded 500-operation
+circuit (one-qubit Haar unitaries; Haar unitaries on 2-5 targets with 0-5
+controls; 1-3-qubit diagonal phase gates; Pauli gadgets of weight 1-30).
+
+One step = the whole 500-operation circuit applied in place on the resident
+state.  Prints ONE JSON line on rank 0.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (oracle/qsim_oracle.py) as it stands, on
+a bounded sample of the same workload, on the host cores.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "gates/s & HBM GB/s on 30q FP64 SV; fused-TC speedup at 1e-6 infidelity"
+UNIT = "gates/s"
+NUM_OPS = 500
+CIRCUIT_TAG = "sv30-circuit"
+STATE_SEED = 2311015121
+CPU_SAMPLE_QUBITS = 26
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--qubits", type=int, default=30, help="statevector size (the workload is 30)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--detail", default="", help="write per-kernel-family statistics to this JSON file")
+    ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# Workload description shared by both arms
+# ---------------------------------------------------------------------------
+
+def make_ops(nq):
+    from paper_2311_01512_gb300 import workloads as wl
+    return wl.statevector_circuit(nq, NUM_OPS, wl.rng_for(CIRCUIT_TAG))
+
+
+def op_family(op):
+    """Kernel family the CUDA path launches for one operation record."""
+    kind = op["op"]
+    if kind == "unitary":
+        return "k_gate1" if len(op["targs"]) == 1 else "k_dense"
+    if kind == "diagonal":
+        return "k_diag"
+    if kind == "gadget":
+        return "k_gadget" if any(p in (1, 2) for p in op["paulis"]) else "k_phase"
+    raise ValueError(kind)
+
+
+def op_bytes(op, nq, amp_bytes):
+    """Algorithmic HBM bytes of one operation: every amplitude it updates is
+    read once and written once, 2 * sizeof(amp) * (amplitudes touched).
+    A gate with s controls touches 2^(N - s) amplitudes."""
+    if op["op"] == "unitary":
+        return 2 * amp_bytes * (1 << (nq - len(op["ctrls"])))
+    return 2 * amp_bytes * (1 << nq)
+
+
+def op_h2d_bytes(op):
+    """Host-to-device bytes the C ABI moves for one operation (the staged
+    matrix of a dense gate; small parameters travel in the launch)."""
+    if op["op"] == "unitary" and len(op["targs"]) > 1:
+        return 16 * (1 << (2 * len(op["targs"])))
+    return 0
+
+
+def config_dict(nq, args):
+    return {"workload": "%d-qubit complex128 statevector, seeded %d-op circuit "
+                        "(1q Haar; 2-5 target Haar with 0-5 controls; 1-3q diagonal phases; "
+                        "Pauli gadgets of weight 1-%d)" % (nq, NUM_OPS, nq),
+            "qubits": nq, "ops_per_step": NUM_OPS, "amp": "complex128",
+            "state_bytes": 16 * (1 << nq),
+            "l2": "inputs larger than L2 (state 16 GiB vs 129 MB L2); no flush",
+            "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (runs in a fresh process; never imports torch or CUDA)
+# ---------------------------------------------------------------------------
+
+def cpu_sample_main(num_ops):
+    import numpy as np
+    from oracle import qsim_oracle as orc
+    from paper_2311_01512_gb300 import workloads as wl
+    nq = CPU_SAMPLE_QUBITS
+    ops = make_ops(nq)[:num_ops]
+    psi = wl.random_statevector(nq, wl.rng_for("cpu-sample"))
+    t0 = time.perf_counter()
+    psi = orc.run_ops(psi, ops, is_density=False)
+    dt = time.perf_counter() - t0
+    scale = 2.0 ** (nq - 30)
+    print(json.dumps({"ops": num_ops, "seconds": dt, "qubits": nq,
+                      "value_30q_equiv": num_ops / dt * scale,
+                      "norm": float(np.sum(np.abs(psi) ** 2))}))
+
+
+def run_cpu_sample(num_ops):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(num_ops)],
+                         capture_output=True, text=True, env=env, cwd=ROOT, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError("cpu sample failed: " + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_dict(res):
+    return {"value": res["value_30q_equiv"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "first %d ops of the same circuit recipe on a %d-qubit complex128 state "
+                      "(%.1f s, one thread); gates/s scaled to 30 qubits by 2^(%d-30)"
+                      % (res["ops"], res["qubits"], res["seconds"], res["qubits"])}
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Distributed helpers (replicas: each rank runs the whole workload)
+# ---------------------------------------------------------------------------
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+
+def device_random_state(nq, device):
+    """Seeded complex Gaussian amplitudes, normalised (input generation)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(STATE_SEED)
+    psi = torch.randn(1 << nq, dtype=torch.complex128, device=device, generator=g)
+    psi /= torch.linalg.vector_norm(psi)
+    return psi
+
+
+def load_traffic(family):
+    """DRAM bytes per launch measured by ncu for a kernel family, if the record
+    matches the current kernel sources (profiles/dram_traffic.json)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+        from paper_2311_01512_gb300 import build as b
+        import hashlib
+        h = hashlib.sha256()
+        for src in b.SOURCES:
+            h.update(open(os.path.join(b.CSRC, src), "rb").read())
+        if rec.get("sources_sha256") != h.hexdigest():
+            return None
+        return rec.get("families", {}).get(family)
+    except Exception:
+        return None
+
+
+def main_ours(args):
+    world, rank, local = dist_setup(args)
+    cpu_res = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_res = run_cpu_sample(6)       # before the first GPU call; a separate process
+    import torch
+    from paper_2311_01512_gb300 import qs
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    nq = args.qubits
+    ops = make_ops(nq)
+    stream = torch.cuda.Stream(device=device)
+    with torch.cuda.stream(stream):
+        psi = device_random_state(nq, device)
+    stream.synchronize()
+    st = qs.State(nq, density=False, prec=qs.QS_C128, stream=stream, storage=psi)
+    h = st.handle
+    fams = [op_family(op) for op in ops]
+    nbytes = [op_bytes(op, nq, 16) for op in ops]
+
+    for _ in range(args.warmup):
+        for op in ops:
+            qs.apply_op(h, op)
+    stream.synchronize()
+
+    # timed region: K steps, events around every operation on the launching stream
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(NUM_OPS + 1)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        for i, op in enumerate(ops):
+            evs[k][i].record(stream)
+            qs.apply_op(h, op)
+        evs[k][NUM_OPS].record(stream)
+    t_end.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    total_ms = max_over_ranks(total_ms, world, device)
+    ms_per_step = total_ms / args.steps
+
+    # per-family statistics from the per-operation events
+    fam_time, fam_bytes, fam_count = {}, {}, {}
+    for k in range(args.steps):
+        for i in range(NUM_OPS):
+            dt = evs[k][i].elapsed_time(evs[k][i + 1])
+            f = fams[i]
+            fam_time[f] = fam_time.get(f, 0.0) + dt
+            fam_bytes[f] = fam_bytes.get(f, 0) + nbytes[i]
+            fam_count[f] = fam_count.get(f, 0) + 1
+    dom = max(fam_time, key=fam_time.get)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    achieved = fam_bytes[dom] / (fam_time[dom] * 1e-3) / 1e9
+    traffic = load_traffic(dom)
+    step_bytes = sum(nbytes)
+    value = world * NUM_OPS * args.steps / (total_ms * 1e-3)
+
+    norm = qs.qs_calc_norm_or_trace(h).real
+
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.empty(1 << nq, dtype=torch.complex128, pin_memory=True)
+        with torch.cuda.stream(stream):
+            fresh = device_random_state(nq, device)
+        stream.synchronize()
+        pinned.copy_(fresh)
+        del fresh
+        h2d = 16 * (1 << nq) + sum(op_h2d_bytes(op) for op in ops)
+        e_ms = []
+        for k in range(1 + args.steps):            # one untimed warm-up step
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            barrier(world)
+            e0.record(stream)
+            qs.qs_set_amps_ptr(h, pinned.data_ptr(), 0, 1 << nq)
+            for op in ops:
+                qs.apply_op(h, op)
+            out_norm = qs.qs_calc_norm_or_trace(h)      # device -> host read; synchronises
+            e1.record(stream)
+            e1.synchronize()
+            if k > 0:
+                e_ms.append(e0.elapsed_time(e1))
+        e_total = max_over_ranks(sum(e_ms), world, device)
+        e2e = {"value": world * NUM_OPS * args.steps / (e_total * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16,
+               "note": "pinned host state uploaded through qs_set_amps, %d ops, norm read back" % NUM_OPS,
+               "final_norm": out_norm.real}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
+            "config": config_dict(nq, args),
+            "hbm_gbs": step_bytes / (ms_per_step * 1e-3) / 1e9,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                         "peak_source": peak_src,
+                         "time_share": fam_time[dom] / sum(fam_time.values())},
+            "gpu_launches": NUM_OPS * args.steps,
+            "clocks": clk,
+            "final_norm": norm,
+        }
+        if e2e is not None:
+            line["e2e"] = e2e
+        if cpu_res is not None:
+            line["cpu_baseline"] = cpu_baseline_dict(cpu_res)
+        print(json.dumps(line), flush=True)
+        detail = {f: {"launches": fam_count[f], "ms_total": fam_time[f],
+                      "share": fam_time[f] / sum(fam_time.values()),
+                      "gbs": fam_bytes[f] / (fam_time[f] * 1e-3) / 1e9} for f in fam_time}
+        print("per-family: " + json.dumps(detail), file=sys.stderr)
+        if args.detail:
+            with open(args.detail, "w") as f:
+                json.dump({"line": line, "families": detail,
+                           "per_op_ms": [[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(NUM_OPS)]
+                                         for k in range(args.steps)],
+                           "ops": [{"op": op["op"], "targs": op["targs"], "ctrls": op.get("ctrls", []),
+                                    "family": fams[i]} for i, op in enumerate(ops)]}, f)
+    st.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the CPU oracle on a bounded sample, on the host cores
+# ---------------------------------------------------------------------------
+
+def main_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    ops_per_step = 3
+    for _ in range(args.warmup):
+        run_cpu_sample(ops_per_step)
+    res = [run_cpu_sample(ops_per_step) for _ in range(args.steps)]
+    secs = sum(r["seconds"] for r in res)
+    value = ops_per_step * args.steps / secs * 2.0 ** (CPU_SAMPLE_QUBITS - 30)
+    cb = cpu_baseline_dict({"ops": ops_per_step * args.steps, "qubits": CPU_SAMPLE_QUBITS,
+                            "seconds": secs, "value_30q_equiv": value})
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)",
+            "data": "synthetic", "config": config_dict(30, args), "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.cpu_sample:
+        cpu_sample_main(args.cpu_sample)
+        return
+    if args.impl == "reference":
+        main_reference(args)
+    else:
+        main_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * qs.h -- C ABI of a single-GPU (GB300, sm_103a) full-state quantum simulator
+ * for statevectors and density matrices, after "Distributed Simulation of
+ * Statevectors and Density Matrices" (arXiv 2311.01512).  Only the paper's
+ * local (single-node) operations are provided; its distributed exchange
+ * algorithms have no counterpart here.
+ *
+ * Conventions (paper, Sec. "Notation"):
+ *   - qubit 0 is the least significant bit of a basis index;
+ *   - a statevector of N qubits is 2^N complex amplitudes, interleaved
+ *     (re, im), complex128 (QS_C128) or complex64 (QS_C64);
+ *   - bit q of a gate-matrix row/column index belongs to target targs[q]
+ *     (Sec. "Many-target gate": the order of targets is the order of the
+ *     matrix's index bits);
+ *   - a density matrix rho = sum_kl alpha_kl |k><l| of N qubits is stored as
+ *     its Choi vector of 2N qubits, beta_i = alpha_{i mod 2^N, i / 2^N}
+ *     (Sec. "State representation"): row index in the low N bits, column
+ *     index in the high N bits;
+ *   - Pauli codes: 0 = I, 1 = X, 2 = Y, 3 = Z (the order of the matrices in
+ *     the paper's pauliTensorElem, Sec. "Pauli string expectation value").
+ *
+ * Memory and ownership:
+ *   - amplitude storage is DEVICE memory owned by the caller (for example a
+ *     torch tensor).  A state handle wraps it and never frees it; the caller
+ *     keeps it alive until qs_destroy.  The pointer must be 256-byte aligned.
+ *   - each handle owns a little library memory: a device scratch area for
+ *     reductions and a pinned staging ring for gate matrices.  It is allocated
+ *     by qs_create_* and freed by qs_destroy.
+ *   - host arrays passed to any call are read before the call returns; the
+ *     caller may reuse them at once.
+ *
+ * Streams: every call is ordered on the CUDA stream given at creation (NULL =
+ * the legacy default stream).  Calls that apply operations return as soon as
+ * the work is queued.  Calls that return a value to the host
+ * (qs_expec_pauli_sum, qs_calc_norm_or_trace, qs_get_amps) synchronise that
+ * stream.
+ *
+ * Errors: no call aborts or throws.  Each returns a qs_status; arguments are
+ * validated on the host before anything is queued, so a call that returns an
+ * argument error has changed nothing.  QS_ERR_CUDA reports a CUDA runtime
+ * error from a launch or copy.  The gate matrices, Kraus operators and
+ * probabilities are not checked for unitarity or complete positivity: the
+ * paper's algorithms do not need either (Sec. "Many-target gate",
+ * Sec. "Kraus map").
+ */
+#ifndef QS_H
+#define QS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qs_state qs_state;
+
+typedef enum {
+  QS_OK = 0,
+  QS_ERR_ARG = 1,              /* null pointer, bad size, bad enum, probability outside [0, 1] */
+  QS_ERR_QUBIT_RANGE = 2,      /* a qubit index outside [0, N) */
+  QS_ERR_DUP_QUBIT = 3,        /* a qubit repeated within targets or within controls */
+  QS_ERR_TARGET_IS_CTRL = 4,   /* a qubit both target and control */
+  QS_ERR_TOO_MANY_TARGETS = 5, /* more targets than the operation allows */
+  QS_ERR_NOT_DENSMATR = 6,     /* a density-matrix-only call on a statevector */
+  QS_ERR_OOM = 7,              /* the library's own scratch allocation failed */
+  QS_ERR_CUDA = 8,             /* a CUDA runtime error */
+  QS_ERR_TIMEOUT = 9,          /* a bounded device wait ran out */
+  QS_ERR_ALIGN = 10            /* a device pointer that is not 256-byte aligned */
+} qs_status;
+
+typedef enum { QS_C64 = 0, QS_C128 = 1 } qs_prec;
+
+/* Largest number of storage qubits (N for a statevector, 2N for a density
+ * matrix): 2^34 complex64 amplitudes are 128 GiB. */
+#define QS_MAX_STORAGE_QUBITS 34
+/* Largest number of targets of a dense gate (the matrix is at most 64 x 64). */
+#define QS_MAX_DENSE_TARGETS 6
+
+/* Text of a status code (static storage). */
+const char* qs_status_str(qs_status status);
+
+/* Wrap caller-owned device memory d_amps (2^num_qubits amplitudes of the given
+ * precision) as a statevector (Sec. "Local statevector algorithms").  The
+ * contents are left as they are.  cuda_stream is a cudaStream_t or NULL. */
+qs_status qs_create_statevector(int num_qubits, qs_prec prec, void* d_amps, void* cuda_stream,
+                                qs_state** out);
+
+/* Wrap caller-owned device memory d_amps (2^(2 num_qubits) amplitudes) as the
+ * Choi vector of a num_qubits-qubit density matrix (Sec. "State
+ * representation"). */
+qs_status qs_create_densmatr(int num_qubits, qs_prec prec, void* d_amps, void* cuda_stream,
+                             qs_state** out);
+
+/* Release the handle and its library memory (waits for its queued work).  The
+ * wrapped amplitude storage is not freed. */
+qs_status qs_destroy(qs_state* state);
+
+/* num_qubits: N; storage_qubits: N (statevector) or 2N (density matrix). */
+qs_status qs_get_info(const qs_state* state, int* num_qubits, int* storage_qubits, int* is_density,
+                      int* prec);
+
+/* Device address of the wrapped amplitudes. */
+qs_status qs_device_ptr(const qs_state* state, void** d_amps);
+
+/* Copy count amplitudes from host memory (interleaved re, im in the state's
+ * precision) into storage indices [first, first + count).  Queued on the
+ * state's stream; pinned host memory makes the copy asynchronous. */
+qs_status qs_set_amps(qs_state* state, const void* host_amps, size_t first, size_t count);
+
+/* Copy storage indices [first, first + count) to host memory; synchronises. */
+qs_status qs_get_amps(const qs_state* state, void* host_amps, size_t first, size_t count);
+
+/* |0><0| or |0>: amplitude 0 set to 1, every other amplitude to 0. */
+qs_status qs_init_zero(qs_state* state);
+
+/* Pure-state initialisation of a density matrix (Sec. "State
+ * representation"): beta_{j + k 2^N} = weight psi_j psi_k^*, written
+ * (accumulate = 0) or added (accumulate = 1), so that a mixture
+ * sum_m w_m |psi_m><psi_m| is built by repeated calls.  psi must be a
+ * statevector handle of the same N and precision, on the same stream. */
+qs_status qs_init_pure_densmatr(qs_state* rho, const qs_state* psi, double weight, int accumulate);
+
+/* Many-control many-target dense gate (Sec. "Many-control one-target gate",
+ * Sec. "Many-target gate", Eq. (local many-target amplitude update)):
+ * alpha_{kj} -> sum_l m_{jl} alpha_{kl} on the amplitudes whose control bits
+ * are all 1.  mat: 2^ntarg x 2^ntarg complex128, row-major, interleaved
+ * (re, im) doubles.  1 <= ntarg <= QS_MAX_DENSE_TARGETS, nctrl >= 0; ctrls
+ * may be NULL when nctrl = 0.  On a density matrix this applies
+ * U rho U^dagger: U on (ctrls, targs), then U^* on the same qubits shifted by
+ * N (Sec. "Unitary gates", Eq. (unitary on a vectorised density matrix)). */
+qs_status qs_apply_ctrl_multi_target(qs_state* state, const int* ctrls, int nctrl, const int* targs,
+                                     int ntarg, const double* mat);
+
+/* Diagonal operator on ntarg <= QS_MAX_DENSE_TARGETS targets:
+ * alpha_i -> diag[j] alpha_i with j the value of the target bits of i (bit q
+ * of j on targs[q]); diag: 2^ntarg complex128 (re, im).  The diagonal case of
+ * Eq. (local many-target amplitude update); the phase gadget of Sec. "Phase
+ * gadget" is one such.  Density matrix: D on targs, then D^* on targs + N. */
+qs_status qs_apply_diagonal(qs_state* state, const int* targs, int ntarg, const double* diag);
+
+/* Pauli gadget exp(-i theta P / 2), P = (x)_q paulis[q] on targs[q]
+ * (Sec. "Pauli gadget": the paper's exp(i phi P) with phi = -theta/2).
+ * n >= 0 targets, paulis[q] in 0..3.  With only Z (and I) factors it is the
+ * phase gadget of Sec. "Phase gadget".  Density matrix: the gadget on targs,
+ * then on targs + N with angle (-1)^(#Y + 1) theta (Algorithm "specific
+ * unitaries on density matrices"). */
+qs_status qs_apply_pauli_gadget(qs_state* state, const int* targs, const int* paulis, int n,
+                                double theta);
+
+/* Kraus map rho -> sum_m K_m rho K_m^dagger on n targets, 1 <= n <= 3
+ * (Sec. "Kraus map"): the superoperator S = sum_m conj(K_m) (x) K_m is built
+ * on the device and applied as a dense 2n-target gate on targs u targs + N.
+ * kraus: num_ops matrices of 2^n x 2^n complex128, each row-major (re, im).
+ * Density matrices only. */
+qs_status qs_apply_kraus(qs_state* state, const int* targs, int n, const double* kraus, int num_ops);
+
+/* One-qubit dephasing (Sec. "Dephasing channel"): beta_i *= 1 - 2p where
+ * bit t and bit t + N of i differ.  Density matrices only; p in [0, 1]. */
+qs_status qs_apply_dephasing(qs_state* state, int t, double p);
+
+/* Two-qubit dephasing (Sec. "Dephasing channel", two-qubit update rule):
+ * beta_i *= 1 - 4p/3 where bit t1 != bit t1 + N or bit t2 != bit t2 + N. */
+qs_status qs_apply_two_qubit_dephasing(qs_state* state, int t1, int t2, double p);
+
+/* One-qubit depolarising (Sec. "Depolarising channel", Eq. (one-qubit
+ * depolarising amplitude update)). */
+qs_status qs_apply_depolarising(qs_state* state, int t, double p);
+
+/* Two-qubit depolarising (Sec. "Depolarising channel", Eq. (two-qubit
+ * depolarising Choi amplitude update)).  The equation is implemented; the
+ * coefficients of the paper's listing for this channel disagree with it. */
+qs_status qs_apply_two_qubit_depolarising(qs_state* state, int t1, int t2, double p);
+
+/* Amplitude damping (Sec. "Damping channel", Eq. (damping amplitude
+ * update)). */
+qs_status qs_apply_damping(qs_state* state, int t, double p);
+
+/* Partial trace over n targets, 1 <= n < N (Sec. "Partial trace", Eqs.
+ * (reduced amplitude definition) and (index function)):
+ * beta'_i = sum_v beta_{g(i, v)}.  The input is not modified.  The result is a
+ * NEW density-matrix handle of N - n qubits wrapping caller-owned device
+ * memory d_out_amps (2^(2(N - n)) amplitudes, same precision, 256-byte
+ * aligned), on the input's stream; the kept qubits keep their order. */
+qs_status qs_partial_trace(const qs_state* in, const int* targs, int n, void* d_out_amps,
+                           qs_state** out);
+
+/* Expectation value of H = sum_n coeffs[n] P_n, paulis: num_terms x N codes,
+ * row n for term n, entry q for qubit q (Sec. "Pauli string expectation
+ * value").  Density matrix: Tr(H rho) = sum_i H_i beta_i, summed over the
+ * entries where H_i is non-zero (column k, row k xor x_n of each term).
+ * Statevector: <psi|H|psi>.  out[0] = real part (the expectation value),
+ * out[1] = imaginary part (zero up to rounding for Hermitian rho).  The sum is
+ * in FP64.  Synchronises. */
+qs_status qs_expec_pauli_sum(const qs_state* state, const int* paulis, const double* coeffs,
+                             int num_terms, double* out);
+
+/* Statevector: out[0] = sum_i |alpha_i|^2, out[1] = 0.  Density matrix:
+ * out = Tr rho = sum_j beta_{j (2^N + 1)} (re, im).  FP64 sum.  Synchronises. */
+qs_status qs_calc_norm_or_trace(const qs_state* state, double* out);
+
+/* Wait for all work queued on the state's stream. */
+qs_status qs_synchronize(const qs_state* state);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QS_H */

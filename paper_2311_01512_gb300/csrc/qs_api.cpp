@@ -1,0 +1,562 @@
+// C ABI (include/qs.h): state handles, argument validation, and the host-side
+// lowering of each operation to kernel parameters.  All arithmetic on
+// amplitudes runs in the CUDA kernels; this file only computes index masks,
+// sorted positions, cos/sin of gadget angles and channel coefficients.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "qs.h"
+#include "qs_internal.h"
+
+using qsk::kMaxQ;
+
+namespace {
+
+constexpr int kRingSlots = 16;
+constexpr size_t kSlotBytes = 64 * 1024;  // one 64 x 64 complex128 matrix
+
+}  // namespace
+
+struct qs_state {
+  void* amps = nullptr;
+  int nq = 0;          // N
+  int ns = 0;          // storage qubits
+  int is_density = 0;
+  qs_prec prec = QS_C128;
+  cudaStream_t stream = nullptr;
+  // reduction scratch (device) and its pinned host mirror
+  double2* d_partials = nullptr;
+  double2* d_result = nullptr;
+  double2* h_result = nullptr;
+  // staging ring for matrices and term lists: pinned host slot -> device slot
+  unsigned char* h_ring = nullptr;
+  unsigned char* d_ring = nullptr;
+  cudaEvent_t ring_ev[kRingSlots] = {};
+  int ring_next = 0;
+};
+
+namespace {
+
+size_t amp_bytes(qs_prec p) { return p == QS_C128 ? 16 : 8; }
+
+qs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? QS_OK : QS_ERR_CUDA; }
+
+void release(qs_state* s) {
+  if (!s) return;
+  if (s->d_partials) cudaFree(s->d_partials);
+  if (s->d_ring) cudaFree(s->d_ring);
+  if (s->h_result) cudaFreeHost(s->h_result);
+  if (s->h_ring) cudaFreeHost(s->h_ring);
+  for (auto& ev : s->ring_ev)
+    if (ev) cudaEventDestroy(ev);
+  delete s;
+}
+
+qs_status create(int nq, int ns, int is_density, qs_prec prec, void* d_amps, void* stream, qs_state** out) {
+  if (!out || !d_amps) return QS_ERR_ARG;
+  *out = nullptr;
+  if (prec != QS_C64 && prec != QS_C128) return QS_ERR_ARG;
+  if (nq < 1 || ns > QS_MAX_STORAGE_QUBITS) return QS_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(d_amps) % 256 != 0) return QS_ERR_ALIGN;
+  qs_state* s = new (std::nothrow) qs_state();
+  if (!s) return QS_ERR_OOM;
+  s->amps = d_amps;
+  s->nq = nq;
+  s->ns = ns;
+  s->is_density = is_density;
+  s->prec = prec;
+  s->stream = static_cast<cudaStream_t>(stream);
+  const size_t scratch = sizeof(double2) * (qsk::kReduceBlocks + 2);
+  if (cudaMalloc(&s->d_partials, scratch) != cudaSuccess || cudaMalloc(&s->d_ring, kRingSlots * kSlotBytes) != cudaSuccess ||
+      cudaMallocHost(&s->h_result, sizeof(double2) * 2) != cudaSuccess ||
+      cudaMallocHost(&s->h_ring, kRingSlots * kSlotBytes) != cudaSuccess) {
+    cudaGetLastError();
+    release(s);
+    return QS_ERR_OOM;
+  }
+  s->d_result = s->d_partials + qsk::kReduceBlocks;
+  for (auto& ev : s->ring_ev) {
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      release(s);
+      return QS_ERR_CUDA;
+    }
+  }
+  *out = s;
+  return QS_OK;
+}
+
+// Stage `bytes` of host data through the next ring slot and return its device
+// copy.  The slot is reused only after the event recorded by its previous user
+// has completed.  The caller records the slot's event after queuing the
+// kernels that read it (ring_done).
+qs_status ring_put(qs_state* s, const void* host, size_t bytes, const void** dev, int* slot) {
+  if (bytes > kSlotBytes) return QS_ERR_ARG;
+  const int k = s->ring_next;
+  s->ring_next = (k + 1) % kRingSlots;
+  if (cudaEventSynchronize(s->ring_ev[k]) != cudaSuccess) return QS_ERR_CUDA;
+  unsigned char* h = s->h_ring + (size_t)k * kSlotBytes;
+  unsigned char* d = s->d_ring + (size_t)k * kSlotBytes;
+  std::memcpy(h, host, bytes);
+  if (cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) return QS_ERR_CUDA;
+  *dev = d;
+  *slot = k;
+  return QS_OK;
+}
+
+// A device-side ring slot with no host data (written by a kernel).
+qs_status ring_take(qs_state* s, void** dev, int* slot) {
+  const int k = s->ring_next;
+  s->ring_next = (k + 1) % kRingSlots;
+  if (cudaEventSynchronize(s->ring_ev[k]) != cudaSuccess) return QS_ERR_CUDA;
+  *dev = s->d_ring + (size_t)k * kSlotBytes;
+  *slot = k;
+  return QS_OK;
+}
+
+qs_status ring_done(qs_state* s, int slot) { return cuda_status(cudaEventRecord(s->ring_ev[slot], s->stream)); }
+
+// Validate qubits: each in [0, nq), no repeats within a list, targets and
+// controls disjoint (Sec. "Many-control one-target gate": t not in c).
+qs_status check_qubits(int nq, const int* targs, int ntarg, const int* ctrls, int nctrl) {
+  if (ntarg < 0 || nctrl < 0) return QS_ERR_ARG;
+  if ((ntarg > 0 && !targs) || (nctrl > 0 && !ctrls)) return QS_ERR_ARG;
+  uint64_t tm = 0, cm = 0;
+  for (int i = 0; i < ntarg; ++i) {
+    if (targs[i] < 0 || targs[i] >= nq) return QS_ERR_QUBIT_RANGE;
+    if (tm >> targs[i] & 1) return QS_ERR_DUP_QUBIT;
+    tm |= 1ull << targs[i];
+  }
+  for (int i = 0; i < nctrl; ++i) {
+    if (ctrls[i] < 0 || ctrls[i] >= nq) return QS_ERR_QUBIT_RANGE;
+    if (cm >> ctrls[i] & 1) return QS_ERR_DUP_QUBIT;
+    cm |= 1ull << ctrls[i];
+  }
+  if (tm & cm) return QS_ERR_TARGET_IS_CTRL;
+  return QS_OK;
+}
+
+qs_status check_prob(double p) { return (p >= 0.0 && p <= 1.0) ? QS_OK : QS_ERR_ARG; }
+
+// One dense or one-target gate pass on storage positions (already shifted).
+qs_status gate_pass(qs_state* s, const std::vector<int>& ctrls, const std::vector<int>& targs, const double* host_mat,
+                    const void* dev_mat, int conj) {
+  const int n = (int)targs.size();
+  uint64_t cmask = 0;
+  for (int c : ctrls) cmask |= 1ull << c;
+  if (n == 1) {
+    qsk::Gate1Params p{};
+    for (int e = 0; e < 4; ++e) {
+      p.m[2 * e] = host_mat[2 * e];
+      p.m[2 * e + 1] = conj ? -host_mat[2 * e + 1] : host_mat[2 * e + 1];
+    }
+    std::vector<int> ins(ctrls);
+    ins.push_back(targs[0]);
+    std::sort(ins.begin(), ins.end());
+    p.nins = (int)ins.size();
+    for (int i = 0; i < p.nins; ++i) p.ins[i] = (int8_t)ins[i];
+    p.t = targs[0];
+    p.ctrl_mask = cmask;
+    p.npairs = 1ull << (s->ns - p.nins);
+    return cuda_status(qsk::launch_gate1(s->prec, s->amps, p, s->stream));
+  }
+  // Dense tile: P = targets u the lowest free qubits, |P| = min(kTileBits, free + n).
+  uint64_t fixed = cmask;
+  for (int t : targs) fixed |= 1ull << t;
+  const int nfree = s->ns - n - (int)ctrls.size();
+  const int g = std::min(qsk::kTileBits - n, nfree) < 0 ? 0 : std::min(qsk::kTileBits - n, nfree);
+  std::vector<int> P(targs);
+  for (int q = 0, added = 0; q < s->ns && added < g; ++q)
+    if (!(fixed >> q & 1)) {
+      P.push_back(q);
+      ++added;
+    }
+  std::sort(P.begin(), P.end());
+  qsk::DenseParams p{};
+  p.mat = static_cast<const double*>(dev_mat);
+  p.ctrl_mask = cmask;
+  p.n = n;
+  p.conj = conj;
+  p.tile_bits = (int)P.size();
+  for (int b = 0; b < p.tile_bits; ++b) p.P[b] = (int8_t)P[b];
+  for (int q = 0; q < n; ++q)
+    p.tslot[q] = (int8_t)(std::find(P.begin(), P.end(), targs[q]) - P.begin());
+  std::vector<int> hi(P);
+  hi.insert(hi.end(), ctrls.begin(), ctrls.end());
+  std::sort(hi.begin(), hi.end());
+  p.nhi = (int)hi.size();
+  for (int i = 0; i < p.nhi; ++i) p.hi_ins[i] = (int8_t)hi[i];
+  p.ntiles = 1ull << (s->ns - p.nhi);
+  return cuda_status(qsk::launch_dense(s->prec, s->amps, p, s->stream));
+}
+
+qs_status gadget_pass(qs_state* s, const std::vector<int>& targs, const int* paulis, double theta) {
+  qsk::GadgetParams p{};
+  int num_y = 0;
+  for (size_t q = 0; q < targs.size(); ++q) {
+    const int c = paulis[q];
+    if (c == 1 || c == 2) p.xy |= 1ull << targs[q];
+    if (c == 2 || c == 3) p.yz |= 1ull << targs[q];
+    if (c == 2) ++num_y;
+  }
+  const double phi = -0.5 * theta;
+  p.c = std::cos(phi);
+  p.s = std::sin(phi);
+  p.eta = num_y & 3;
+  if (p.xy) {
+    p.h = 63 - __builtin_clzll(p.xy);
+    p.nwork = 1ull << (s->ns - 1);
+  } else {
+    p.h = 0;
+    p.nwork = 1ull << s->ns;
+  }
+  return cuda_status(qsk::launch_gadget(s->prec, s->amps, p, s->stream));
+}
+
+qs_status reduce_to_host(qs_state* s, double* out) {
+  if (cudaMemcpyAsync(s->h_result, s->d_result, sizeof(double2), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+    return QS_ERR_CUDA;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return QS_ERR_CUDA;
+  out[0] = s->h_result[0].x;
+  out[1] = s->h_result[0].y;
+  return QS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qs_status_str(qs_status status) {
+  switch (status) {
+    case QS_OK: return "ok";
+    case QS_ERR_ARG: return "invalid argument";
+    case QS_ERR_QUBIT_RANGE: return "qubit index out of range";
+    case QS_ERR_DUP_QUBIT: return "repeated qubit";
+    case QS_ERR_TARGET_IS_CTRL: return "qubit is both target and control";
+    case QS_ERR_TOO_MANY_TARGETS: return "too many targets";
+    case QS_ERR_NOT_DENSMATR: return "operation needs a density matrix";
+    case QS_ERR_OOM: return "library scratch allocation failed";
+    case QS_ERR_CUDA: return "CUDA runtime error";
+    case QS_ERR_TIMEOUT: return "bounded device wait ran out";
+    case QS_ERR_ALIGN: return "device pointer not 256-byte aligned";
+  }
+  return "unknown status";
+}
+
+qs_status qs_create_statevector(int num_qubits, qs_prec prec, void* d_amps, void* cuda_stream, qs_state** out) {
+  return create(num_qubits, num_qubits, 0, prec, d_amps, cuda_stream, out);
+}
+
+qs_status qs_create_densmatr(int num_qubits, qs_prec prec, void* d_amps, void* cuda_stream, qs_state** out) {
+  if (num_qubits < 1 || 2 * num_qubits > QS_MAX_STORAGE_QUBITS) {
+    if (out) *out = nullptr;
+    return QS_ERR_ARG;
+  }
+  return create(num_qubits, 2 * num_qubits, 1, prec, d_amps, cuda_stream, out);
+}
+
+qs_status qs_destroy(qs_state* state) {
+  if (!state) return QS_ERR_ARG;
+  const cudaError_t e = cudaStreamSynchronize(state->stream);
+  release(state);
+  return cuda_status(e);
+}
+
+qs_status qs_get_info(const qs_state* s, int* num_qubits, int* storage_qubits, int* is_density, int* prec) {
+  if (!s) return QS_ERR_ARG;
+  if (num_qubits) *num_qubits = s->nq;
+  if (storage_qubits) *storage_qubits = s->ns;
+  if (is_density) *is_density = s->is_density;
+  if (prec) *prec = (int)s->prec;
+  return QS_OK;
+}
+
+qs_status qs_device_ptr(const qs_state* s, void** d_amps) {
+  if (!s || !d_amps) return QS_ERR_ARG;
+  *d_amps = s->amps;
+  return QS_OK;
+}
+
+qs_status qs_set_amps(qs_state* s, const void* host_amps, size_t first, size_t count) {
+  if (!s || (!host_amps && count)) return QS_ERR_ARG;
+  const size_t total = size_t(1) << s->ns;
+  if (first > total || count > total - first) return QS_ERR_ARG;
+  const size_t b = amp_bytes(s->prec);
+  return cuda_status(cudaMemcpyAsync(static_cast<char*>(s->amps) + first * b, host_amps, count * b,
+                                     cudaMemcpyHostToDevice, s->stream));
+}
+
+qs_status qs_get_amps(const qs_state* s, void* host_amps, size_t first, size_t count) {
+  if (!s || (!host_amps && count)) return QS_ERR_ARG;
+  const size_t total = size_t(1) << s->ns;
+  if (first > total || count > total - first) return QS_ERR_ARG;
+  const size_t b = amp_bytes(s->prec);
+  if (cudaMemcpyAsync(host_amps, static_cast<const char*>(s->amps) + first * b, count * b, cudaMemcpyDeviceToHost,
+                      s->stream) != cudaSuccess)
+    return QS_ERR_CUDA;
+  return cuda_status(cudaStreamSynchronize(s->stream));
+}
+
+qs_status qs_init_zero(qs_state* s) {
+  if (!s) return QS_ERR_ARG;
+  return cuda_status(qsk::launch_init_zero(s->prec, s->amps, s->ns, s->stream));
+}
+
+qs_status qs_init_pure_densmatr(qs_state* rho, const qs_state* psi, double weight, int accumulate) {
+  if (!rho || !psi) return QS_ERR_ARG;
+  if (!rho->is_density) return QS_ERR_NOT_DENSMATR;
+  if (psi->is_density || psi->nq != rho->nq || psi->prec != rho->prec) return QS_ERR_ARG;
+  return cuda_status(qsk::launch_dm_from_pure(rho->prec, rho->amps, psi->amps, rho->nq, weight, accumulate ? 1 : 0,
+                                              rho->stream));
+}
+
+qs_status qs_apply_ctrl_multi_target(qs_state* s, const int* ctrls, int nctrl, const int* targs, int ntarg,
+                                     const double* mat) {
+  if (!s || !mat) return QS_ERR_ARG;
+  if (ntarg < 1) return QS_ERR_ARG;
+  if (ntarg > QS_MAX_DENSE_TARGETS) return QS_ERR_TOO_MANY_TARGETS;
+  qs_status st = check_qubits(s->nq, targs, ntarg, ctrls, nctrl);
+  if (st != QS_OK) return st;
+  std::vector<int> c(ctrls, ctrls + nctrl), t(targs, targs + ntarg);
+  const size_t mat_bytes = sizeof(double) * 2 * (size_t(1) << (2 * ntarg));
+  const void* dmat = nullptr;
+  int slot = -1;
+  if (ntarg > 1) {
+    st = ring_put(s, mat, mat_bytes, &dmat, &slot);
+    if (st != QS_OK) return st;
+  }
+  st = gate_pass(s, c, t, mat, dmat, 0);
+  if (st == QS_OK && s->is_density) {
+    // U^* on the same qubits shifted by N (Eq. (unitary on a vectorised density matrix))
+    for (int& q : c) q += s->nq;
+    for (int& q : t) q += s->nq;
+    st = gate_pass(s, c, t, mat, dmat, 1);
+  }
+  if (slot >= 0) {
+    const qs_status st2 = ring_done(s, slot);
+    if (st == QS_OK) st = st2;
+  }
+  return st;
+}
+
+qs_status qs_apply_diagonal(qs_state* s, const int* targs, int ntarg, const double* diag) {
+  if (!s || !diag) return QS_ERR_ARG;
+  if (ntarg < 1) return QS_ERR_ARG;
+  if (ntarg > QS_MAX_DENSE_TARGETS) return QS_ERR_TOO_MANY_TARGETS;
+  qs_status st = check_qubits(s->nq, targs, ntarg, nullptr, 0);
+  if (st != QS_OK) return st;
+  qsk::DiagParams p{};
+  p.n = ntarg;
+  p.namps = 1ull << s->ns;
+  for (int j = 0; j < (1 << ntarg); ++j) {
+    p.d[2 * j] = diag[2 * j];
+    p.d[2 * j + 1] = diag[2 * j + 1];
+  }
+  for (int q = 0; q < ntarg; ++q) p.tpos[q] = (int8_t)targs[q];
+  st = cuda_status(qsk::launch_diag(s->prec, s->amps, p, s->stream));
+  if (st == QS_OK && s->is_density) {
+    for (int j = 0; j < (1 << ntarg); ++j) p.d[2 * j + 1] = -diag[2 * j + 1];
+    for (int q = 0; q < ntarg; ++q) p.tpos[q] = (int8_t)(targs[q] + s->nq);
+    st = cuda_status(qsk::launch_diag(s->prec, s->amps, p, s->stream));
+  }
+  return st;
+}
+
+qs_status qs_apply_pauli_gadget(qs_state* s, const int* targs, const int* paulis, int n, double theta) {
+  if (!s || n < 0 || (n > 0 && (!targs || !paulis))) return QS_ERR_ARG;
+  qs_status st = check_qubits(s->nq, targs, n, nullptr, 0);
+  if (st != QS_OK) return st;
+  int num_y = 0;
+  for (int q = 0; q < n; ++q) {
+    if (paulis[q] < 0 || paulis[q] > 3) return QS_ERR_ARG;
+    if (paulis[q] == 2) ++num_y;
+  }
+  std::vector<int> t(targs, targs + n);
+  st = gadget_pass(s, t, paulis, theta);
+  if (st == QS_OK && s->is_density) {
+    // U(theta)^* = U((-1)^(#Y + 1) theta) (Algorithm "specific unitaries on density matrices")
+    for (int& q : t) q += s->nq;
+    const double theta2 = (num_y % 2 == 0) ? -theta : theta;
+    st = gadget_pass(s, t, paulis, theta2);
+  }
+  return st;
+}
+
+qs_status qs_apply_kraus(qs_state* s, const int* targs, int n, const double* kraus, int num_ops) {
+  if (!s || !kraus || num_ops < 1) return QS_ERR_ARG;
+  if (!s->is_density) return QS_ERR_NOT_DENSMATR;
+  if (n < 1) return QS_ERR_ARG;
+  if (2 * n > QS_MAX_DENSE_TARGETS) return QS_ERR_TOO_MANY_TARGETS;
+  qs_status st = check_qubits(s->nq, targs, n, nullptr, 0);
+  if (st != QS_OK) return st;
+  const size_t kbytes = sizeof(double) * 2 * (size_t(1) << (2 * n)) * (size_t)num_ops;
+  if (kbytes > kSlotBytes) return QS_ERR_ARG;
+  const void* dk = nullptr;
+  void* dsup = nullptr;
+  int slot_k = -1, slot_s = -1;
+  st = ring_put(s, kraus, kbytes, &dk, &slot_k);
+  if (st != QS_OK) return st;
+  st = ring_take(s, &dsup, &slot_s);
+  if (st == QS_OK)
+    st = cuda_status(qsk::launch_superop(static_cast<const double*>(dk), num_ops, n, static_cast<double*>(dsup),
+                                         s->stream));
+  if (st == QS_OK) {
+    // S on t u (t + N): matrix bit q on t[q], bit n + q on t[q] + N (Sec. "Kraus map")
+    std::vector<int> t(targs, targs + n);
+    for (int q = 0; q < n; ++q) t.push_back(targs[q] + s->nq);
+    st = gate_pass(s, {}, t, nullptr, dsup, 0);
+  }
+  const qs_status a = ring_done(s, slot_k);
+  const qs_status b = slot_s >= 0 ? ring_done(s, slot_s) : QS_OK;
+  if (st == QS_OK) st = a != QS_OK ? a : b;
+  return st;
+}
+
+namespace {
+
+qs_status group_channel(qs_state* s, int op, int t1, int t2, const double f[3]) {
+  if (!s) return QS_ERR_ARG;
+  if (!s->is_density) return QS_ERR_NOT_DENSMATR;
+  const bool two = (op == qsk::G_DEPHASE2 || op == qsk::G_DEPOL2);
+  int tt[2] = {t1, t2};
+  qs_status st = check_qubits(s->nq, tt, two ? 2 : 1, nullptr, 0);
+  if (st != QS_OK) return st;
+  qsk::GroupParams p{};
+  std::vector<int> pos;
+  if (two)
+    pos = {t1, t2, t1 + s->nq, t2 + s->nq};
+  else
+    pos = {t1, t1 + s->nq};
+  p.nbits = (int)pos.size();
+  for (int b = 0; b < p.nbits; ++b) p.mpos[b] = (int8_t)pos[b];
+  std::sort(pos.begin(), pos.end());
+  for (int b = 0; b < p.nbits; ++b) p.ins[b] = (int8_t)pos[b];
+  p.ngroups = 1ull << (s->ns - p.nbits);
+  p.f[0] = f[0];
+  p.f[1] = f[1];
+  p.f[2] = f[2];
+  return cuda_status(qsk::launch_group(s->prec, s->amps, op, p, s->stream));
+}
+
+}  // namespace
+
+qs_status qs_apply_dephasing(qs_state* s, int t, double p) {
+  if (check_prob(p) != QS_OK) return QS_ERR_ARG;
+  const double f[3] = {1.0 - 2.0 * p, 0.0, 0.0};
+  return group_channel(s, qsk::G_DEPHASE1, t, t, f);
+}
+
+qs_status qs_apply_two_qubit_dephasing(qs_state* s, int t1, int t2, double p) {
+  if (check_prob(p) != QS_OK) return QS_ERR_ARG;
+  const double f[3] = {1.0 - 4.0 * p / 3.0, 0.0, 0.0};
+  return group_channel(s, qsk::G_DEPHASE2, t1, t2, f);
+}
+
+qs_status qs_apply_depolarising(qs_state* s, int t, double p) {
+  if (check_prob(p) != QS_OK) return QS_ERR_ARG;
+  const double f[3] = {1.0 - 2.0 * p / 3.0, 2.0 * p / 3.0, 1.0 - 4.0 * p / 3.0};
+  return group_channel(s, qsk::G_DEPOL1, t, t, f);
+}
+
+qs_status qs_apply_two_qubit_depolarising(qs_state* s, int t1, int t2, double p) {
+  if (check_prob(p) != QS_OK) return QS_ERR_ARG;
+  const double f[3] = {1.0 - 4.0 * p / 5.0, 4.0 * p / 15.0, 1.0 - 16.0 * p / 15.0};
+  return group_channel(s, qsk::G_DEPOL2, t1, t2, f);
+}
+
+qs_status qs_apply_damping(qs_state* s, int t, double p) {
+  if (check_prob(p) != QS_OK) return QS_ERR_ARG;
+  const double f[3] = {1.0 - p, p, std::sqrt(1.0 - p)};
+  return group_channel(s, qsk::G_DAMP, t, t, f);
+}
+
+qs_status qs_partial_trace(const qs_state* in, const int* targs, int n, void* d_out_amps, qs_state** out) {
+  if (!in || !out || !d_out_amps) return QS_ERR_ARG;
+  *out = nullptr;
+  if (!in->is_density) return QS_ERR_NOT_DENSMATR;
+  if (n < 1 || n >= in->nq) return QS_ERR_ARG;
+  qs_status st = check_qubits(in->nq, targs, n, nullptr, 0);
+  if (st != QS_OK) return st;
+  if (reinterpret_cast<uintptr_t>(d_out_amps) % 256 != 0) return QS_ERR_ALIGN;
+  const int m = in->nq - n;
+  qs_state* o = nullptr;
+  st = qs_create_densmatr(m, in->prec, d_out_amps, in->stream, &o);
+  if (st != QS_OK) return st;
+  qsk::PtraceParams p{};
+  p.n = n;
+  std::vector<int> pos;
+  for (int q = 0; q < n; ++q) {
+    pos.push_back(targs[q]);
+    pos.push_back(targs[q] + in->nq);
+    p.pair_mask[q] = (1ull << targs[q]) | (1ull << (targs[q] + in->nq));
+  }
+  std::sort(pos.begin(), pos.end());
+  p.nins = (int)pos.size();
+  for (int i = 0; i < p.nins; ++i) p.ins[i] = (int8_t)pos[i];
+  p.nout = 1ull << (2 * m);
+  st = cuda_status(qsk::launch_ptrace(in->prec, in->amps, d_out_amps, p, in->stream));
+  if (st != QS_OK) {
+    release(o);
+    return st;
+  }
+  *out = o;
+  return QS_OK;
+}
+
+qs_status qs_expec_pauli_sum(const qs_state* cs, const int* paulis, const double* coeffs, int num_terms,
+                             double* out) {
+  qs_state* s = const_cast<qs_state*>(cs);
+  if (!s || !paulis || !coeffs || !out || num_terms < 1) return QS_ERR_ARG;
+  std::vector<qsk::PauliTerm> terms((size_t)num_terms);
+  for (int n = 0; n < num_terms; ++n) {
+    qsk::PauliTerm t{};
+    int num_y = 0;
+    for (int q = 0; q < s->nq; ++q) {
+      const int c = paulis[(size_t)n * s->nq + q];
+      if (c < 0 || c > 3) return QS_ERR_ARG;
+      if (c == 1 || c == 2) t.xy |= 1ull << q;
+      if (c == 2 || c == 3) t.yz |= 1ull << q;
+      if (c == 2) ++num_y;
+    }
+    t.h = coeffs[n];
+    t.eta = num_y & 3;
+    terms[(size_t)n] = t;
+  }
+  for (int first = 0; first < num_terms; first += qsk::kTermChunk) {
+    const int cnt = std::min(qsk::kTermChunk, num_terms - first);
+    const void* dterms = nullptr;
+    int slot = -1;
+    qs_status st = ring_put(s, terms.data() + first, sizeof(qsk::PauliTerm) * (size_t)cnt, &dterms, &slot);
+    if (st != QS_OK) return st;
+    const auto* dt = static_cast<const qsk::PauliTerm*>(dterms);
+    cudaError_t e = s->is_density ? qsk::launch_expec_dm(s->prec, s->amps, s->nq, dt, cnt, s->d_partials, s->stream)
+                                  : qsk::launch_expec_sv(s->prec, s->amps, s->nq, dt, cnt, s->d_partials, s->stream);
+    if (e == cudaSuccess) e = qsk::launch_reduce_final(s->d_partials, s->d_result, first > 0, s->stream);
+    st = ring_done(s, slot);
+    if (e != cudaSuccess) return QS_ERR_CUDA;
+    if (st != QS_OK) return st;
+  }
+  return reduce_to_host(s, out);
+}
+
+qs_status qs_calc_norm_or_trace(const qs_state* cs, double* out) {
+  qs_state* s = const_cast<qs_state*>(cs);
+  if (!s || !out) return QS_ERR_ARG;
+  cudaError_t e = s->is_density ? qsk::launch_trace(s->prec, s->amps, s->nq, s->d_partials, s->stream)
+                                : qsk::launch_norm(s->prec, s->amps, s->ns, s->d_partials, s->stream);
+  if (e == cudaSuccess) e = qsk::launch_reduce_final(s->d_partials, s->d_result, 0, s->stream);
+  if (e != cudaSuccess) return QS_ERR_CUDA;
+  return reduce_to_host(s, out);
+}
+
+qs_status qs_synchronize(const qs_state* s) {
+  if (!s) return QS_ERR_ARG;
+  return cuda_status(cudaStreamSynchronize(s->stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,119 @@
+// Internal interface between the C-ABI layer (qs_api.cpp) and the CUDA kernels.
+// Host-visible declarations only: parameter structs passed by value to the
+// kernels, and one launcher per kernel family.  No torch types anywhere.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qs.h"
+
+namespace qsk {
+
+constexpr int kMaxQ = QS_MAX_STORAGE_QUBITS;
+constexpr int kMaxDense = QS_MAX_DENSE_TARGETS;
+constexpr int kTileBits = 10;        // amplitudes staged per tile of the dense kernel: 2^10
+constexpr int kReduceBlocks = 1216;  // 152 SMs x 8: fixed grid of every stage-one reduction
+constexpr int kTermChunk = 2048;     // Pauli terms per device upload
+
+// One-target gate on pairs (i0, i1 = i0 | 2^t) (Sec. "One-target gate",
+// Sec. "Many-control one-target gate").
+struct Gate1Params {
+  double m[8];           // m00, m01, m10, m11 as (re, im), already conjugated if needed
+  uint64_t npairs;       // 2^(Ns - 1 - s)
+  uint64_t ctrl_mask;    // control bits, set in every enumerated index
+  int t;
+  int nins;              // 1 + s
+  int8_t ins[kMaxQ];     // sorted target and control positions (zero bits inserted)
+};
+
+// Dense gate on n <= 6 targets staged through shared memory
+// (Sec. "Many-target gate").  A tile is the 2^tile_bits amplitudes whose
+// indices differ only at the positions P (the targets plus the lowest free
+// qubits); the remaining free bits number the tile.
+struct DenseParams {
+  const double* mat;     // device, 2^n x 2^n complex128 row-major (re, im)
+  uint64_t ctrl_mask;
+  uint64_t ntiles;
+  int n;
+  int conj;              // use conj(mat)
+  int tile_bits;
+  int nhi;
+  int8_t tslot[kMaxDense];  // tslot[q]: index within P of target q
+  int8_t P[16];             // ascending tile positions
+  int8_t hi_ins[kMaxQ];     // sorted (P u controls): zero bits inserted into the tile number
+};
+
+// Diagonal on n <= 6 targets.
+struct DiagParams {
+  double d[2 * 64];
+  uint64_t namps;
+  int n;
+  int8_t tpos[kMaxDense];
+};
+
+// Pauli gadget / phase gadget (Sec. "Pauli gadget", Sec. "Phase gadget").
+struct GadgetParams {
+  uint64_t xy;           // qubits with X or Y: the flipped bits
+  uint64_t yz;           // qubits with Y or Z: the sign bits
+  uint64_t nwork;        // pairs (xy != 0) or amplitudes (xy == 0)
+  double c, s;           // cos(phi), sin(phi), phi = -theta/2
+  int eta;               // number of Y factors mod 4
+  int h;                 // highest bit of xy (pair enumeration)
+};
+
+// Density-matrix channels acting on groups of 4 (one qubit: bits t, t+N) or 16
+// (two qubits: t1, t2, t1+N, t2+N) Choi amplitudes.
+enum GroupOp { G_DEPHASE1 = 0, G_DEPHASE2 = 1, G_DEPOL1 = 2, G_DEPOL2 = 3, G_DAMP = 4 };
+struct GroupParams {
+  uint64_t ngroups;
+  int nbits;             // 2 or 4
+  int8_t ins[4];         // sorted member positions
+  int8_t mpos[4];        // member bit b -> qubit position
+  double f[3];           // channel coefficients (see the kernel)
+};
+
+// Partial trace (Sec. "Partial trace").
+struct PtraceParams {
+  uint64_t nout;         // 2^(2(N - n))
+  int n;
+  int nins;              // 2n
+  int8_t ins[kMaxQ];     // sorted t u (t + N)
+  uint64_t pair_mask[kMaxQ / 2 + 1];  // (1 << t[q]) | (1 << (t[q] + N))
+};
+
+// One Pauli term of an expectation value.
+struct PauliTerm {
+  uint64_t xy;
+  uint64_t yz;
+  double h;
+  int eta;               // number of Y factors mod 4
+  int pad;
+};
+
+// Launchers.  Each returns cudaGetLastError() after the launch.  amps is the
+// state's device storage, ns its number of storage qubits.
+cudaError_t launch_gate1(qs_prec prec, void* amps, const Gate1Params& p, cudaStream_t st);
+cudaError_t launch_dense(qs_prec prec, void* amps, const DenseParams& p, cudaStream_t st);
+cudaError_t launch_diag(qs_prec prec, void* amps, const DiagParams& p, cudaStream_t st);
+cudaError_t launch_gadget(qs_prec prec, void* amps, const GadgetParams& p, cudaStream_t st);
+cudaError_t launch_group(qs_prec prec, void* amps, int op, const GroupParams& p, cudaStream_t st);
+cudaError_t launch_ptrace(qs_prec prec, const void* in, void* out, const PtraceParams& p,
+                          cudaStream_t st);
+cudaError_t launch_superop(const double* kraus, int num_ops, int n, double* sup, cudaStream_t st);
+cudaError_t launch_dm_from_pure(qs_prec prec, void* rho, const void* psi, int nq, double weight,
+                                int accumulate, cudaStream_t st);
+cudaError_t launch_init_zero(qs_prec prec, void* amps, int ns, cudaStream_t st);
+
+// Reductions: stage one writes kReduceBlocks complex128 partial sums, stage two
+// sums them in a fixed order into result[0] (added to result[0] if accumulate).
+cudaError_t launch_norm(qs_prec prec, const void* amps, int ns, double2* partials, cudaStream_t st);
+cudaError_t launch_trace(qs_prec prec, const void* amps, int nq, double2* partials, cudaStream_t st);
+cudaError_t launch_expec_dm(qs_prec prec, const void* amps, int nq, const PauliTerm* terms,
+                            int nterms, double2* partials, cudaStream_t st);
+cudaError_t launch_expec_sv(qs_prec prec, const void* amps, int nq, const PauliTerm* terms,
+                            int nterms, double2* partials, cudaStream_t st);
+cudaError_t launch_reduce_final(const double2* partials, double2* result, int accumulate,
+                                cudaStream_t st);
+
+}  // namespace qsk

@@ -1,0 +1,161 @@
+// Reductions in FP64: norm, trace, and Pauli-sum expectation values.  Stage one
+// runs a fixed grid of kReduceBlocks blocks, each writing one complex128
+// partial sum; stage two adds the partials in a fixed order, so results do not
+// depend on scheduling.
+#include "qs_device.cuh"
+
+namespace qsk {
+
+// sum_i |alpha_i|^2 (Sec. "Local statevector algorithms": the state model).
+template <typename R>
+__global__ void __launch_bounds__(256) k_norm(const typename Cplx<R>::T* __restrict__ psi, uint64_t n,
+                                              double2* __restrict__ partials) {
+  double acc = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const auto a = psi[i];
+    acc += (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+  }
+  const double2 s = block_sum(make_double2(acc, 0.0));
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// Tr rho = sum_j beta_{j (2^N + 1)} (Sec. "Pauli string expectation value").
+template <typename R>
+__global__ void __launch_bounds__(256) k_trace(const typename Cplx<R>::T* __restrict__ rho, int nq,
+                                               double2* __restrict__ partials) {
+  double sr = 0.0, si = 0.0;
+  const uint64_t dim = 1ull << nq;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < dim; j += stride) {
+    const auto a = rho[j * (dim + 1)];
+    sr += (double)a.x;
+    si += (double)a.y;
+  }
+  const double2 s = block_sum(make_double2(sr, si));
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// Tr(H rho) = sum_i H_i beta_i (Sec. "Pauli string expectation value",
+// Eq. (density expectation sum)).  For the term h P, H_i is non-zero only
+// where the row index l = i >> N equals the column index k = i mod 2^N with
+// the X/Y bits flipped, and there pauliTensorElem = eta (-1)^{popc(k & yz)}:
+// Y contributes i (-1)^{k_q}, Z contributes (-1)^{k_q}, X contributes 1.  The
+// sum runs over those 2^N entries per term.
+template <typename R>
+__global__ void __launch_bounds__(256) k_expec_dm(const typename Cplx<R>::T* __restrict__ rho, int nq,
+                                                  const PauliTerm* __restrict__ terms, int nterms,
+                                                  double2* __restrict__ partials) {
+  double sr = 0.0, si = 0.0;
+  const uint64_t dim = 1ull << nq;
+  const uint64_t total = dim * (uint64_t)nterms;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += stride) {
+    const int n = (int)(w >> nq);
+    const uint64_t k = w & (dim - 1);
+    const PauliTerm t = terms[n];
+    const auto b = rho[k | ((k ^ t.xy) << nq)];
+    double2 v = make_double2((double)b.x, (double)b.y);
+    v = rot_i(v, t.eta);
+    const double h = parity64(k & t.yz) ? -t.h : t.h;
+    sr += h * v.x;
+    si += h * v.y;
+  }
+  const double2 s = block_sum(make_double2(sr, si));
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// <psi|H|psi> = sum_n h_n sum_i conj(alpha_i) (P_n psi)_i with
+// (P psi)_i = beta_{i'} alpha_{i'}, i' = i xor xy (Sec. "Pauli tensor",
+// Eq. (Pauli tensor amplitude update)).
+template <typename R>
+__global__ void __launch_bounds__(256) k_expec_sv(const typename Cplx<R>::T* __restrict__ psi, int nq,
+                                                  const PauliTerm* __restrict__ terms, int nterms,
+                                                  double2* __restrict__ partials) {
+  double sr = 0.0, si = 0.0;
+  const uint64_t dim = 1ull << nq;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride) {
+    const auto a = psi[i];
+    const double ar = (double)a.x, ai = (double)a.y;
+    for (int n = 0; n < nterms; ++n) {
+      const PauliTerm t = terms[n];
+      const uint64_t ip = i ^ t.xy;
+      const auto b = psi[ip];
+      double2 v = rot_i(make_double2((double)b.x, (double)b.y), t.eta);
+      const double h = parity64(ip & t.yz) ? -t.h : t.h;
+      // conj(a) * v * h
+      sr += h * (ar * v.x + ai * v.y);
+      si += h * (ar * v.y - ai * v.x);
+    }
+  }
+  const double2 s = block_sum(make_double2(sr, si));
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// Stage two: one block of 1024 threads; thread j adds partials j, j + 1024, ...
+__global__ void __launch_bounds__(1024) k_reduce_final(const double2* __restrict__ partials, int n,
+                                                       double2* __restrict__ result, int accumulate) {
+  double sr = 0.0, si = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    sr += partials[j].x;
+    si += partials[j].y;
+  }
+  const double2 s = block_sum(make_double2(sr, si));
+  if (threadIdx.x == 0) {
+    if (accumulate) {
+      result[0].x += s.x;
+      result[0].y += s.y;
+    } else {
+      result[0] = s;
+    }
+  }
+}
+
+// Stage-one kernels always run exactly kReduceBlocks blocks; blocks with no
+// work write a zero partial.
+cudaError_t launch_norm(qs_prec prec, const void* amps, int ns, double2* partials, cudaStream_t st) {
+  const uint64_t n = 1ull << ns;
+  if (prec == QS_C128)
+    k_norm<double><<<kReduceBlocks, 256, 0, st>>>(static_cast<const double2*>(amps), n, partials);
+  else
+    k_norm<float><<<kReduceBlocks, 256, 0, st>>>(static_cast<const float2*>(amps), n, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace(qs_prec prec, const void* amps, int nq, double2* partials, cudaStream_t st) {
+  if (prec == QS_C128)
+    k_trace<double><<<kReduceBlocks, 256, 0, st>>>(static_cast<const double2*>(amps), nq, partials);
+  else
+    k_trace<float><<<kReduceBlocks, 256, 0, st>>>(static_cast<const float2*>(amps), nq, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expec_dm(qs_prec prec, const void* amps, int nq, const PauliTerm* terms, int nterms,
+                            double2* partials, cudaStream_t st) {
+  if (prec == QS_C128)
+    k_expec_dm<double><<<kReduceBlocks, 256, 0, st>>>(static_cast<const double2*>(amps), nq, terms, nterms,
+                                                      partials);
+  else
+    k_expec_dm<float><<<kReduceBlocks, 256, 0, st>>>(static_cast<const float2*>(amps), nq, terms, nterms,
+                                                     partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expec_sv(qs_prec prec, const void* amps, int nq, const PauliTerm* terms, int nterms,
+                            double2* partials, cudaStream_t st) {
+  if (prec == QS_C128)
+    k_expec_sv<double><<<kReduceBlocks, 256, 0, st>>>(static_cast<const double2*>(amps), nq, terms, nterms,
+                                                      partials);
+  else
+    k_expec_sv<float><<<kReduceBlocks, 256, 0, st>>>(static_cast<const float2*>(amps), nq, terms, nterms,
+                                                     partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_final(const double2* partials, double2* result, int accumulate, cudaStream_t st) {
+  k_reduce_final<<<1, 1024, 0, st>>>(partials, kReduceBlocks, result, accumulate);
+  return cudaGetLastError();
+}
+
+}  // namespace qsk

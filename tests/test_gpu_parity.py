@@ -1,0 +1,342 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Sizes span several shared-memory tiles (a tile is 2^10 amplitudes) and ragged
+cases (states with fewer free qubits than a tile, gates with no free qubits
+at all).  Tolerances: complex128 single operations 1e-13 absolute (amplitudes
+are at most 1 in modulus), circuits 1e-12 per 1000 operations; complex64
+single operations 2e-6 absolute, circuits scaled by the number of operations.
+Integer-valued results (which amplitudes an operation touches) are checked
+exactly through the parity of untouched amplitudes.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import qsim_oracle as orc
+from paper_2311_01512_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+ATOL = {1: 1e-13, 0: 2e-6}
+
+
+@pytest.fixture(scope="module")
+def qs():
+    from paper_2311_01512_gb300 import qs as mod
+    return mod
+
+
+def new_sv(qs, nq, prec, psi):
+    st = qs.State(nq, density=False, prec=prec)
+    st.set_amps(psi)
+    return st
+
+
+def new_dm(qs, nq, prec, beta):
+    st = qs.State(nq, density=True, prec=prec)
+    st.set_amps(beta)
+    return st
+
+
+def rand_dm(nq, rank, rng):
+    states, w = wl.random_mixed_state_vectors(nq, rank, rng)
+    return sum(wi * orc.densmatr_from_pure(s) for wi, s in zip(w, states))
+
+
+def close(got, want, prec, scale=1.0):
+    err = float(np.max(np.abs(np.asarray(got, dtype=np.complex128) - want)))
+    assert err <= ATOL[prec] * scale, "max |delta amp| = %.3e" % err
+    return err
+
+
+PRECS = [1, 0]
+
+
+# ---------------------------------------------------------------------------
+# statevector gates
+# ---------------------------------------------------------------------------
+
+def gate_cases():
+    cases = []
+    for nq in (10, 13):
+        for n in range(1, 7):
+            for s in (0, 1, 3):
+                cases.append((nq, n, s))
+    cases += [(6, 6, 0), (8, 6, 2), (7, 5, 2), (1, 1, 0), (2, 1, 1), (5, 2, 3), (11, 1, 10)]
+    return cases
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("nq,n,s", gate_cases())
+def test_ctrl_multi_target_gate(qs, prec, nq, n, s):
+    rng = np.random.default_rng(1000 * nq + 10 * n + s)
+    placements = []
+    for _ in range(2):
+        qsel = [int(x) for x in rng.choice(nq, n + s, replace=False)]
+        placements.append((qsel[:n], qsel[n:]))
+    placements.append((list(range(n)), list(range(n, n + s))))                         # lowest qubits
+    placements.append((list(range(nq - 1, nq - 1 - n, -1)), list(range(s))))            # highest, reversed
+    for targs, ctrls in placements:
+        psi = wl.random_statevector(nq, rng)
+        mat = rng.standard_normal((1 << n, 1 << n)) + 1j * rng.standard_normal((1 << n, 1 << n))
+        mat /= np.sqrt(1 << n)
+        st = new_sv(qs, nq, prec, psi)
+        qs.qs_apply_ctrl_multi_target(st.handle, ctrls, targs, mat)
+        want = orc.apply_ctrl_multi_target(psi, ctrls, targs, mat)
+        close(st.get_amps(), want, prec, scale=4)
+        st.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n", range(1, 7))
+def test_diagonal(qs, prec, n):
+    rng = np.random.default_rng(50 + n)
+    nq = 11
+    targs = [int(x) for x in rng.choice(nq, n, replace=False)]
+    d = np.exp(1j * rng.uniform(0, 2 * np.pi, 1 << n)) * rng.uniform(0.5, 1.5, 1 << n)
+    psi = wl.random_statevector(nq, rng)
+    st = new_sv(qs, nq, prec, psi)
+    qs.qs_apply_diagonal(st.handle, targs, d)
+    close(st.get_amps(), orc.apply_diagonal(psi, targs, d), prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("seed", range(8))
+def test_pauli_gadget(qs, prec, seed):
+    rng = np.random.default_rng(300 + seed)
+    nq = 12
+    psi = wl.random_statevector(nq, rng)
+    st = new_sv(qs, nq, prec, psi)
+    want = psi
+    cases = [wl.random_pauli_string(nq, 1, nq, rng) for _ in range(4)]
+    cases.append(([0, 5, 11], [3, 3, 3]))            # phase gadget (Z only)
+    cases.append(([11], [1]))                        # X on the top qubit
+    cases.append(([0, 1], [2, 2]))                   # two Y on the lowest qubits
+    cases.append(([], []))                           # global phase exp(-i theta/2)
+    for targs, paulis in cases:
+        theta = float(rng.uniform(0, 2 * np.pi))
+        qs.qs_apply_pauli_gadget(st.handle, targs, paulis, theta)
+        want = orc.apply_pauli_gadget(want, targs, paulis, theta)
+    close(st.get_amps(), want, prec, scale=4)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_norm_and_statevector_expectation(qs, prec):
+    rng = np.random.default_rng(8)
+    nq = 11
+    psi = wl.random_statevector(nq, rng) * 0.7
+    st = new_sv(qs, nq, prec, psi)
+    norm = qs.qs_calc_norm_or_trace(st.handle)
+    assert abs(norm - orc.calc_norm(psi)) < (1e-13 if prec else 1e-6)
+    paulis, coeffs = wl.random_pauli_sum(nq, 13, rng)
+    got = qs.qs_expec_pauli_sum(st.handle, paulis, coeffs)
+    want = orc.expec_pauli_sum_statevector(psi, paulis, coeffs)
+    assert abs(got - want) < (1e-12 if prec else 1e-5)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_statevector_circuit(qs, prec):
+    """500 seeded operations of the 30-qubit workload's mix at 14 qubits."""
+    rng = wl.rng_for("sv-circuit-14")
+    nq = 14
+    psi = wl.random_statevector(nq, rng)
+    ops = wl.statevector_circuit(nq, 500, rng)
+    st = new_sv(qs, nq, prec, psi)
+    for op in ops:
+        qs.apply_op(st.handle, op)
+    want = orc.run_ops(psi, ops, is_density=False)
+    got = st.get_amps()
+    if prec == 1:
+        err = float(np.max(np.abs(got - want)))
+        assert err <= 0.5e-12, err        # 1e-12 per 1000 operations
+    else:
+        close(got, want, prec, scale=50)
+    assert abs(qs.qs_calc_norm_or_trace(st.handle) - 1.0) < (1e-12 if prec else 1e-4)
+
+
+# ---------------------------------------------------------------------------
+# density matrices
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_densmatr_init_pure_and_trace(qs, prec):
+    rng = np.random.default_rng(21)
+    nq = 5
+    states, w = wl.random_mixed_state_vectors(nq, 3, rng)
+    dm = qs.State(nq, density=True, prec=prec)
+    for m, (s, wi) in enumerate(zip(states, w)):
+        sv = new_sv(qs, nq, prec, s)
+        qs.qs_init_pure_densmatr(dm.handle, sv.handle, wi, accumulate=m > 0)
+        qs.qs_synchronize(dm.handle)
+        sv.close()
+    want = sum(wi * orc.densmatr_from_pure(s) for wi, s in zip(w, states))
+    close(dm.get_amps(), want, prec)
+    tr = qs.qs_calc_norm_or_trace(dm.handle)
+    assert abs(tr - orc.calc_trace(want)) < (1e-13 if prec else 1e-6)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,s", [(1, 0), (1, 2), (2, 0), (2, 3), (3, 1), (3, 3)])
+def test_densmatr_unitary(qs, prec, n, s):
+    rng = np.random.default_rng(70 + 10 * n + s)
+    nq = 6
+    beta = rand_dm(nq, 4, rng)
+    qsel = [int(x) for x in rng.choice(nq, n + s, replace=False)]
+    u = wl.haar_unitary(1 << n, rng)
+    dm = new_dm(qs, nq, prec, beta)
+    qs.qs_apply_ctrl_multi_target(dm.handle, qsel[n:], qsel[:n], u)
+    close(dm.get_amps(), orc.densmatr_apply_ctrl_multi_target(beta, qsel[n:], qsel[:n], u), prec, scale=4)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_densmatr_diag_and_gadget(qs, prec):
+    rng = np.random.default_rng(90)
+    nq = 6
+    beta = rand_dm(nq, 3, rng)
+    dm = new_dm(qs, nq, prec, beta)
+    want = beta
+    d = np.exp(1j * rng.uniform(0, 2 * np.pi, 8))
+    qs.qs_apply_diagonal(dm.handle, [4, 0, 2], d)
+    want = orc.densmatr_apply_diagonal(want, [4, 0, 2], d)
+    for _ in range(6):
+        targs, paulis = wl.random_pauli_string(nq, 1, nq, rng)
+        theta = float(rng.uniform(0, 2 * np.pi))
+        qs.qs_apply_pauli_gadget(dm.handle, targs, paulis, theta)
+        want = orc.densmatr_apply_pauli_gadget(want, targs, paulis, theta)
+    close(dm.get_amps(), want, prec, scale=4)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("nq,n,m", [(6, 1, 2), (6, 2, 4), (6, 3, 3), (3, 3, 2), (4, 2, 1)])
+def test_kraus(qs, prec, nq, n, m):
+    rng = np.random.default_rng(110 + nq + n + m)
+    beta = rand_dm(nq, 3, rng)
+    targs = [int(x) for x in rng.choice(nq, n, replace=False)]
+    ks = wl.haar_kraus(n, m, rng)
+    dm = new_dm(qs, nq, prec, beta)
+    qs.qs_apply_kraus(dm.handle, targs, ks)
+    close(dm.get_amps(), orc.densmatr_apply_kraus(beta, targs, ks), prec, scale=4)
+
+
+CHANNELS = [
+    ("dephasing", lambda qs, h, t, p: qs.qs_apply_dephasing(h, t[0], p),
+     lambda b, t, p: orc.densmatr_apply_dephasing(b, t[0], p), 1),
+    ("dephasing2", lambda qs, h, t, p: qs.qs_apply_two_qubit_dephasing(h, t[0], t[1], p),
+     lambda b, t, p: orc.densmatr_apply_two_qubit_dephasing(b, t[0], t[1], p), 2),
+    ("depolarising", lambda qs, h, t, p: qs.qs_apply_depolarising(h, t[0], p),
+     lambda b, t, p: orc.densmatr_apply_depolarising(b, t[0], p), 1),
+    ("depolarising2", lambda qs, h, t, p: qs.qs_apply_two_qubit_depolarising(h, t[0], t[1], p),
+     lambda b, t, p: orc.densmatr_apply_two_qubit_depolarising(b, t[0], t[1], p), 2),
+    ("damping", lambda qs, h, t, p: qs.qs_apply_damping(h, t[0], p),
+     lambda b, t, p: orc.densmatr_apply_damping(b, t[0], p), 1),
+]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name,gpu_fn,orc_fn,nt", CHANNELS, ids=[c[0] for c in CHANNELS])
+def test_channels(qs, prec, name, gpu_fn, orc_fn, nt):
+    rng = np.random.default_rng(sum(ord(c) for c in name))
+    nq = 6
+    beta = rand_dm(nq, 4, rng)
+    dm = new_dm(qs, nq, prec, beta)
+    want = beta
+    placements = [[int(x) for x in rng.choice(nq, nt, replace=False)] for _ in range(3)]
+    placements += [[0, nq - 1][:nt], [nq - 1, 0][:nt]]
+    for t in placements:
+        p = float(rng.uniform(0, 1))
+        gpu_fn(qs, dm.handle, t, p)
+        want = orc_fn(want, t, p)
+    close(dm.get_amps(), want, prec, scale=4)
+    tr = qs.qs_calc_norm_or_trace(dm.handle)
+    assert abs(tr - orc.calc_trace(want)) < (1e-13 if prec else 1e-5)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("nq,targs", [(6, [2, 4]), (6, [0]), (6, [5, 0, 3]), (5, [4, 3, 2, 1]), (7, [6, 1])])
+def test_partial_trace(qs, prec, nq, targs):
+    rng = np.random.default_rng(200 + nq + len(targs))
+    beta = rand_dm(nq, 3, rng)
+    dm = new_dm(qs, nq, prec, beta)
+    red = dm.partial_trace(targs)
+    close(red.get_amps(), orc.partial_trace(beta, targs), prec, scale=4)
+    # the input is untouched
+    close(dm.get_amps(), beta, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_densmatr_expectation(qs, prec):
+    rng = np.random.default_rng(31)
+    nq = 6
+    beta = rand_dm(nq, 4, rng)
+    dm = new_dm(qs, nq, prec, beta)
+    paulis, coeffs = wl.random_pauli_sum(nq, 20, rng)
+    got = qs.qs_expec_pauli_sum(dm.handle, paulis, coeffs)
+    want = orc.expec_pauli_sum_densmatr(beta, paulis, coeffs)
+    assert abs(got - want) < (1e-13 if prec else 1e-5)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_small_density_workload(qs, prec):
+    """6-qubit density matrix (12-qubit Choi vector): random mixture of 4
+    Gaussian pure states, 300 seeded operations, partial trace over 2 qubits,
+    20-term Pauli-sum expectation of the reduced state."""
+    rng = wl.rng_for("dm6")
+    nq = 6
+    states, w = wl.random_mixed_state_vectors(nq, 4, rng)
+    ops = wl.small_densmatr_circuit(nq, 300, rng)
+    traced = [int(x) for x in rng.choice(nq, 2, replace=False)]
+    paulis, coeffs = wl.random_pauli_sum(nq - 2, 20, rng)
+    dm = qs.State(nq, density=True, prec=prec)
+    for m, (s, wi) in enumerate(zip(states, w)):
+        sv = new_sv(qs, nq, prec, s)
+        qs.qs_init_pure_densmatr(dm.handle, sv.handle, wi, accumulate=m > 0)
+        qs.qs_synchronize(dm.handle)
+        sv.close()
+    for op in ops:
+        qs.apply_op(dm.handle, op)
+    red = dm.partial_trace(traced)
+    got_e = qs.qs_expec_pauli_sum(red.handle, paulis, coeffs)
+    beta = sum(wi * orc.densmatr_from_pure(s) for wi, s in zip(w, states))
+    want = orc.run_ops(beta, ops, is_density=True)
+    want_red = orc.partial_trace(want, traced)
+    want_e = orc.expec_pauli_sum_densmatr(want_red, paulis, coeffs)
+    if prec == 1:
+        assert float(np.max(np.abs(dm.get_amps() - want))) <= 0.3e-12
+        assert float(np.max(np.abs(red.get_amps() - want_red))) <= 0.3e-12
+        assert abs(got_e - want_e) <= 1e-12
+    else:
+        close(dm.get_amps(), want, prec, scale=100)
+        assert abs(got_e - want_e) <= 1e-4
+
+
+# ---------------------------------------------------------------------------
+# argument validation through a live handle
+# ---------------------------------------------------------------------------
+
+def test_validation_errors(qs):
+    sv = qs.State(5, density=False)
+    qs.qs_init_zero(sv.handle)
+    eye = np.eye(2, dtype=np.complex128)
+    cases = [
+        (lambda: qs.qs_apply_ctrl_multi_target(sv.handle, [], [5], eye), "QS_ERR_QUBIT_RANGE"),
+        (lambda: qs.qs_apply_ctrl_multi_target(sv.handle, [1], [1], eye), "QS_ERR_TARGET_IS_CTRL"),
+        (lambda: qs.qs_apply_ctrl_multi_target(sv.handle, [2, 2], [1], eye), "QS_ERR_DUP_QUBIT"),
+        (lambda: qs.qs_apply_ctrl_multi_target(sv.handle, [], list(range(7)), np.eye(128)), "QS_ERR_TOO_MANY_TARGETS"),
+        (lambda: qs.qs_apply_dephasing(sv.handle, 0, 0.1), "QS_ERR_NOT_DENSMATR"),
+        (lambda: qs.qs_apply_pauli_gadget(sv.handle, [0], [4], 0.1), "QS_ERR_ARG"),
+    ]
+    for fn, want in cases:
+        with pytest.raises(qs.QSError) as ei:
+            fn()
+        assert want in str(ei.value)
+    dm = qs.State(3, density=True)
+    qs.qs_init_zero(dm.handle)
+    with pytest.raises(qs.QSError) as ei:
+        qs.qs_apply_depolarising(dm.handle, 0, 1.5)
+    assert "QS_ERR_ARG" in str(ei.value)
+    with pytest.raises(qs.QSError) as ei:
+        qs.qs_apply_kraus(dm.handle, [0, 1, 2, 0], [np.eye(16)])
+    # nothing changed after the rejected calls
+    amps = dm.get_amps()
+    assert amps[0] == 1 and np.count_nonzero(amps) == 1
+    assert sv.get_amps()[0] == 1
