@@ -194,6 +194,31 @@ qs_status qs_partial_trace(const qs_state* in, const int* targs, int n, void* d_
 qs_status qs_expec_pauli_sum(const qs_state* state, const int* paulis, const double* coeffs,
                              int num_terms, double* out);
 
+/* Largest number of terms qs_expec_pauli_sum_noalloc accepts. */
+#define QS_NOALLOC_MAX_TERMS 256
+
+/* The expectation value of qs_expec_pauli_sum, for callers that cannot
+ * allocate GPU memory: it takes a raw device pointer instead of a handle
+ * (creating a handle allocates scratch and a pinned ring) and allocates
+ * nothing, not even the scratch its reduction needs.  The paper has no
+ * counterpart; this is a deployment variant of the same computation.
+ *
+ * d_amps: 2^num_qubits amplitudes (statevector) or 2^(2 num_qubits) (Choi
+ * vector, is_density = 1) of precision prec, 256-byte aligned, read only.
+ * paulis, coeffs, out: as for qs_expec_pauli_sum; out is host memory.
+ * num_terms must be 1..QS_NOALLOC_MAX_TERMS; more returns QS_ERR_ARG.
+ *
+ * Scratch: a fixed array of about 28 KB in the library's device image (term
+ * list, one partial sum per reduction block, the result), held by every GPU
+ * that loads the library until the process exits.  The first call on a device
+ * looks up that array's device address, so make the first call on each device
+ * before capturing any stream.  All calls share the array: calls that overlap
+ * on the GPU (other streams, other host threads) race and must be serialised
+ * by the caller.  Synchronises cuda_stream. */
+qs_status qs_expec_pauli_sum_noalloc(const void* d_amps, int num_qubits, int is_density, qs_prec prec,
+                                     const int* paulis, const double* coeffs, int num_terms,
+                                     void* cuda_stream, double* out);
+
 /* Statevector: out[0] = sum_i |alpha_i|^2, out[1] = 0.  Density matrix:
  * out = Tr rho = sum_j beta_{j (2^N + 1)} (re, im).  FP64 sum.  Synchronises. */
 qs_status qs_calc_norm_or_trace(const qs_state* state, double* out);

@@ -58,7 +58,10 @@ SIGNATURES = {
     "qs_expec_pauli_sum": (_I, [_P, _IP, _DP, _I, _DP]),
     "qs_calc_norm_or_trace": (_I, [_P, _DP]),
     "qs_synchronize": (_I, [_P]),
+    "qs_expec_pauli_sum_noalloc": (_I, [_P, _I, _I, _I, _IP, _DP, _I, _P, _DP]),
 }
+
+NOALLOC_MAX_TERMS = 256
 for _name, (_res, _args) in SIGNATURES.items():
     _fn = getattr(_lib, _name)
     _fn.restype = _res
@@ -202,6 +205,21 @@ def qs_expec_pauli_sum(h, paulis, coeffs):
     out = (ctypes.c_double * 2)()
     _check(_lib.qs_expec_pauli_sum(h, p.ctypes.data_as(_IP), c.ctypes.data_as(_DP), c.shape[0], out),
            "qs_expec_pauli_sum")
+    return complex(out[0], out[1])
+
+
+def qs_expec_pauli_sum_noalloc(d_amps, num_qubits, is_density, prec, paulis, coeffs, stream):
+    """Expectation value from a raw device pointer, with no allocation inside
+    the library (see include/qs.h).  For callers that cannot allocate GPU
+    memory; at most NOALLOC_MAX_TERMS terms."""
+    p = np.ascontiguousarray(np.asarray(paulis, dtype=np.int32))
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+    if c.shape[0] > NOALLOC_MAX_TERMS:
+        raise ValueError("qs_expec_pauli_sum_noalloc takes at most %d terms, got %d" % (NOALLOC_MAX_TERMS, c.shape[0]))
+    out = (ctypes.c_double * 2)()
+    _check(_lib.qs_expec_pauli_sum_noalloc(_P(d_amps), num_qubits, 1 if is_density else 0, prec,
+                                           p.ctypes.data_as(_IP), c.ctypes.data_as(_DP), c.shape[0],
+                                           _P(stream), out), "qs_expec_pauli_sum_noalloc")
     return complex(out[0], out[1])
 
 
