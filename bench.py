@@ -43,6 +43,10 @@ def parse_args(argv=None):
     ap.add_argument("--qubits", type=int, default=30, help="statevector size (the workload is 30)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--arith", choices=["df", "f64"], default="df",
+                    help="complex128 arithmetic: double-float on the FP32 pipes (default) or native FP64")
+    ap.add_argument("--f64-share", type=int, default=0,
+                    help="sixteenths of one-target-gate work done in native FP64 beside double-float")
     ap.add_argument("--detail", default="", help="write per-kernel-family statistics to this JSON file")
     ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args(argv)
@@ -61,7 +65,7 @@ def op_family(op):
     """Kernel family the CUDA path launches for one operation record."""
     kind = op["op"]
     if kind == "unitary":
-        return "k_gate1" if len(op["targs"]) == 1 else "k_dense"
+        return "k_gate1" if len(op["targs"]) == 1 else "k_dense<%d>" % len(op["targs"])
     if kind == "diagonal":
         return "k_diag"
     if kind == "gadget":
@@ -277,6 +281,7 @@ def main_ours(args):
     stream.synchronize()
     st = qs.State(nq, density=False, prec=qs.QS_C128, stream=stream, storage=psi)
     h = st.handle
+    qs.qs_set_arithmetic(h, qs.QS_ARITH_DF if args.arith == "df" else qs.QS_ARITH_F64, args.f64_share)
     fams = [op_family(op) for op in ops]
     nbytes = [op_bytes(op, nq, 16) for op in ops]
 
@@ -365,8 +370,10 @@ def main_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
-            "config": config_dict(nq, args),
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": ("c128 storage, double-float (2xf32, 47-bit) arithmetic" if args.arith == "df"
+                      else "c128 storage, f64 arithmetic"),
+            "data": "synthetic", "config": config_dict(nq, args),
             "hbm_gbs": step_bytes / (ms_per_step * 1e-3) / 1e9,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
                          "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,

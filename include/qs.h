@@ -70,6 +70,16 @@ typedef enum {
 
 typedef enum { QS_C64 = 0, QS_C128 = 1 } qs_prec;
 
+/* Arithmetic of complex128 gate kernels.  GB300 executes FP64 FMA about 58
+ * times slower than FP32 FMA, so by default complex128 amplitudes are split
+ * into pairs of floats (integer bit operations, 47-bit significand) and
+ * combined with error-free FP32 transformations; the result is stored back as
+ * IEEE complex128.  Relative error per operation: a few units of 2^-46 for
+ * amplitudes of modulus in [2^-80, 2^128) (absolute error below 2^-103 for
+ * smaller ones).  QS_ARITH_F64 uses native FP64 throughout.  complex64 states
+ * ignore the setting. */
+typedef enum { QS_ARITH_DF = 0, QS_ARITH_F64 = 1 } qs_arith;
+
 /* Largest number of storage qubits (N for a statevector, 2N for a density
  * matrix): 2^34 complex64 amplitudes are 128 GiB. */
 #define QS_MAX_STORAGE_QUBITS 34
@@ -98,6 +108,17 @@ qs_status qs_destroy(qs_state* state);
 /* num_qubits: N; storage_qubits: N (statevector) or 2N (density matrix). */
 qs_status qs_get_info(const qs_state* state, int* num_qubits, int* storage_qubits, int* is_density,
                       int* prec);
+
+/* Select the complex128 arithmetic of this handle (default QS_ARITH_DF).
+ * f64_share_16ths (0..16): with QS_ARITH_DF, the share of one-target-gate
+ * work, in sixteenths, done in native FP64 at the same time (the FP64 pipe is
+ * otherwise idle); 0 = none. */
+qs_status qs_set_arithmetic(qs_state* state, qs_arith arith, int f64_share_16ths);
+
+/* complex64 dense gates with 3..5 targets run on the tensor cores (tcgen05,
+ * 3xTF32 with FP32 accumulation: FP32-level accuracy) unless disabled here
+ * (enable = 0: CUDA-core FP32 kernels).  complex128 states ignore it. */
+qs_status qs_set_tensor_cores(qs_state* state, int enable);
 
 /* Device address of the wrapped amplitudes. */
 qs_status qs_device_ptr(const qs_state* state, void** d_amps);
@@ -223,7 +244,9 @@ qs_status qs_expec_pauli_sum_noalloc(const void* d_amps, int num_qubits, int is_
  * out = Tr rho = sum_j beta_{j (2^N + 1)} (re, im).  FP64 sum.  Synchronises. */
 qs_status qs_calc_norm_or_trace(const qs_state* state, double* out);
 
-/* Wait for all work queued on the state's stream. */
+/* Wait for all work queued on the state's stream.  Returns QS_ERR_TIMEOUT
+ * (once) if a kernel's bounded wait ran out since the last check; the state's
+ * amplitudes are then unspecified. */
 qs_status qs_synchronize(const qs_state* state);
 
 #ifdef __cplusplus

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "qs.h"
+#include "qs_df.cuh"
 #include "qs_internal.h"
 
 using qsk::kMaxQ;
@@ -29,6 +30,10 @@ struct qs_state {
   int ns = 0;          // storage qubits
   int is_density = 0;
   qs_prec prec = QS_C128;
+  qs_arith arith = QS_ARITH_DF;
+  int f64_share = 0;   // sixteenths of one-target-gate chunks run in native FP64
+  int tensor_cores = 1;  // complex64 dense gates with 3..5 targets on tcgen05
+  int* d_err = nullptr;  // device error word (bounded waits that ran out)
   cudaStream_t stream = nullptr;
   // reduction scratch (device) and its pinned host mirror
   double2* d_partials = nullptr;
@@ -81,6 +86,11 @@ qs_status create(int nq, int ns, int is_density, qs_prec prec, void* d_amps, voi
     return QS_ERR_OOM;
   }
   s->d_result = s->d_partials + qsk::kReduceBlocks;
+  s->d_err = reinterpret_cast<int*>(s->d_partials + qsk::kReduceBlocks + 1);
+  if (cudaMemset(s->d_err, 0, sizeof(int)) != cudaSuccess) {
+    release(s);
+    return QS_ERR_CUDA;
+  }
   for (auto& ev : s->ring_ev) {
     if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
       release(s);
@@ -149,6 +159,28 @@ qs_status gate_pass(qs_state* s, const std::vector<int>& ctrls, const std::vecto
   const int n = (int)targs.size();
   uint64_t cmask = 0;
   for (int c : ctrls) cmask |= 1ull << c;
+  const bool df = s->prec == QS_C128 && s->arith == QS_ARITH_DF;
+  if (n == 1 && df) {
+    qsk::Gate1DfParams p{};
+    for (int e = 0; e < 8; ++e) {
+      const double v = (conj && (e & 1)) ? -host_mat[e] : host_mat[e];
+      const qsdf::df sv = qsdf::split_const(v);
+      p.mh[e] = sv.h;
+      p.ml[e] = sv.l;
+      p.m[e] = v;
+    }
+    std::vector<int> ins(ctrls);
+    ins.push_back(targs[0]);
+    std::sort(ins.begin(), ins.end());
+    p.nins = (int)ins.size();
+    for (int i = 0; i < p.nins; ++i) p.ins[i] = (int8_t)ins[i];
+    p.t = targs[0];
+    p.ctrl_mask = cmask;
+    p.npairs = 1ull << (s->ns - p.nins);
+    p.f64_mod = 16;
+    p.f64_count = s->f64_share;
+    return cuda_status(qsk::launch_gate1_df(s->amps, p, s->stream));
+  }
   if (n == 1) {
     qsk::Gate1Params p{};
     for (int e = 0; e < 4; ++e) {
@@ -165,10 +197,41 @@ qs_status gate_pass(qs_state* s, const std::vector<int>& ctrls, const std::vecto
     p.npairs = 1ull << (s->ns - p.nins);
     return cuda_status(qsk::launch_gate1(s->prec, s->amps, p, s->stream));
   }
-  // Dense tile: P = targets u the lowest free qubits, |P| = min(kTileBits, free + n).
   uint64_t fixed = cmask;
   for (int t : targs) fixed |= 1ull << t;
   const int nfree = s->ns - n - (int)ctrls.size();
+  if (s->prec == QS_C64 && s->tensor_cores && n >= 3 && n <= 5) {
+    // tensor-core tile: 128 groups, P = targets u the 7 lowest free qubits
+    const int g = std::min(7, nfree);
+    std::vector<int> P(targs);
+    for (int q = 0, added = 0; q < s->ns && added < g; ++q)
+      if (!(fixed >> q & 1)) {
+        P.push_back(q);
+        ++added;
+      }
+    std::sort(P.begin(), P.end());
+    qsk::TcParams p{};
+    p.mat = static_cast<const double*>(dev_mat);
+    p.err = s->d_err;
+    p.ctrl_mask = cmask;
+    p.n = n;
+    p.conj = conj;
+    p.tile_bits = (int)P.size();
+    for (int b = 0; b < p.tile_bits; ++b) p.P[b] = (int8_t)P[b];
+    for (int q = 0; q < n; ++q) {
+      p.tslot[q] = (int8_t)(std::find(P.begin(), P.end(), targs[q]) - P.begin());
+      p.tslot_mask |= 1u << p.tslot[q];
+      p.tpos[q] = (int8_t)targs[q];
+    }
+    std::vector<int> hi(P);
+    hi.insert(hi.end(), ctrls.begin(), ctrls.end());
+    std::sort(hi.begin(), hi.end());
+    p.nhi = (int)hi.size();
+    for (int i = 0; i < p.nhi; ++i) p.hi_ins[i] = (int8_t)hi[i];
+    p.ntiles = 1ull << (s->ns - p.nhi);
+    return cuda_status(qsk::launch_dense_tc(s->amps, p, s->stream));
+  }
+  // Dense tile: P = targets u the lowest free qubits, |P| = min(kTileBits, free + n).
   const int g = std::min(qsk::kTileBits - n, nfree) < 0 ? 0 : std::min(qsk::kTileBits - n, nfree);
   std::vector<int> P(targs);
   for (int q = 0, added = 0; q < s->ns && added < g; ++q)
@@ -192,6 +255,7 @@ qs_status gate_pass(qs_state* s, const std::vector<int>& ctrls, const std::vecto
   p.nhi = (int)hi.size();
   for (int i = 0; i < p.nhi; ++i) p.hi_ins[i] = (int8_t)hi[i];
   p.ntiles = 1ull << (s->ns - p.nhi);
+  if (df) return cuda_status(qsk::launch_dense_df(s->amps, p, s->stream));
   return cuda_status(qsk::launch_dense(s->prec, s->amps, p, s->stream));
 }
 
@@ -214,6 +278,20 @@ qs_status gadget_pass(qs_state* s, const std::vector<int>& targs, const int* pau
   } else {
     p.h = 0;
     p.nwork = 1ull << s->ns;
+  }
+  if (s->prec == QS_C128 && s->arith == QS_ARITH_DF) {
+    qsk::GadgetDfParams q{};
+    q.xy = p.xy;
+    q.yz = p.yz;
+    q.nwork = p.nwork;
+    const qsdf::df c = qsdf::split_const(p.c), sn = qsdf::split_const(p.s);
+    q.ch = c.h;
+    q.cl = c.l;
+    q.sh = sn.h;
+    q.sl = sn.l;
+    q.eta = p.eta;
+    q.h = p.h;
+    return cuda_status(qsk::launch_gadget_df(s->amps, q, s->stream));
   }
   return cuda_status(qsk::launch_gadget(s->prec, s->amps, p, s->stream));
 }
@@ -273,6 +351,20 @@ qs_status qs_get_info(const qs_state* s, int* num_qubits, int* storage_qubits, i
   if (storage_qubits) *storage_qubits = s->ns;
   if (is_density) *is_density = s->is_density;
   if (prec) *prec = (int)s->prec;
+  return QS_OK;
+}
+
+qs_status qs_set_arithmetic(qs_state* s, qs_arith arith, int f64_share_16ths) {
+  if (!s || (arith != QS_ARITH_DF && arith != QS_ARITH_F64)) return QS_ERR_ARG;
+  if (f64_share_16ths < 0 || f64_share_16ths > 16) return QS_ERR_ARG;
+  s->arith = arith;
+  s->f64_share = f64_share_16ths;
+  return QS_OK;
+}
+
+qs_status qs_set_tensor_cores(qs_state* s, int enable) {
+  if (!s) return QS_ERR_ARG;
+  s->tensor_cores = enable ? 1 : 0;
   return QS_OK;
 }
 
@@ -358,11 +450,13 @@ qs_status qs_apply_diagonal(qs_state* s, const int* targs, int ntarg, const doub
     p.d[2 * j + 1] = diag[2 * j + 1];
   }
   for (int q = 0; q < ntarg; ++q) p.tpos[q] = (int8_t)targs[q];
-  st = cuda_status(qsk::launch_diag(s->prec, s->amps, p, s->stream));
+  const bool df = s->prec == QS_C128 && s->arith == QS_ARITH_DF;
+  auto launch = [&]() { return df ? qsk::launch_diag_df(s->amps, p, s->stream) : qsk::launch_diag(s->prec, s->amps, p, s->stream); };
+  st = cuda_status(launch());
   if (st == QS_OK && s->is_density) {
     for (int j = 0; j < (1 << ntarg); ++j) p.d[2 * j + 1] = -diag[2 * j + 1];
     for (int q = 0; q < ntarg; ++q) p.tpos[q] = (int8_t)(targs[q] + s->nq);
-    st = cuda_status(qsk::launch_diag(s->prec, s->amps, p, s->stream));
+    st = cuda_status(launch());
   }
   return st;
 }
@@ -556,7 +650,14 @@ qs_status qs_calc_norm_or_trace(const qs_state* cs, double* out) {
 
 qs_status qs_synchronize(const qs_state* s) {
   if (!s) return QS_ERR_ARG;
-  return cuda_status(cudaStreamSynchronize(s->stream));
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return QS_ERR_CUDA;
+  int err = 0;
+  if (cudaMemcpy(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return QS_ERR_CUDA;
+  if (err) {
+    cudaMemset(s->d_err, 0, sizeof(int));
+    return QS_ERR_TIMEOUT;
+  }
+  return QS_OK;
 }
 
 }  // extern "C"

@@ -27,6 +27,21 @@ struct Gate1Params {
   int8_t ins[kMaxQ];     // sorted target and control positions (zero bits inserted)
 };
 
+// The same gate for complex128 with double-float arithmetic: the matrix split
+// into float pairs on the host, plus the plain doubles for the share of
+// 32-pair chunks (chunk mod f64_mod < f64_count) run in native FP64.
+struct Gate1DfParams {
+  float mh[8], ml[8];
+  double m[8];
+  uint64_t npairs;
+  uint64_t ctrl_mask;
+  int t;
+  int nins;
+  int f64_mod;
+  int f64_count;
+  int8_t ins[kMaxQ];
+};
+
 // Dense gate on n <= 6 targets staged through shared memory
 // (Sec. "Many-target gate").  A tile is the 2^tile_bits amplitudes whose
 // indices differ only at the positions P (the targets plus the lowest free
@@ -42,6 +57,24 @@ struct DenseParams {
   int8_t tslot[kMaxDense];  // tslot[q]: index within P of target q
   int8_t P[16];             // ascending tile positions
   int8_t hi_ins[kMaxQ];     // sorted (P u controls): zero bits inserted into the tile number
+};
+
+// Dense gate on the tensor cores (complex64, 3xTF32): a tile is 128 groups,
+// P = the targets plus the 7 lowest free qubits (fewer in small states).
+struct TcParams {
+  const double* mat;     // device, 2^n x 2^n complex128 row-major (re, im)
+  int* err;              // device error word: set to 1 when a bounded wait runs out
+  uint64_t ctrl_mask;
+  uint64_t ntiles;
+  int n;
+  int conj;
+  int tile_bits;
+  int nhi;
+  uint32_t tslot_mask;   // bits of P that are targets
+  int8_t tslot[kMaxDense];
+  int8_t tpos[kMaxDense];
+  int8_t P[16];
+  int8_t hi_ins[kMaxQ];
 };
 
 // Diagonal on n <= 6 targets.
@@ -60,6 +93,14 @@ struct GadgetParams {
   double c, s;           // cos(phi), sin(phi), phi = -theta/2
   int eta;               // number of Y factors mod 4
   int h;                 // highest bit of xy (pair enumeration)
+};
+
+// Gadget parameters for double-float arithmetic: cos(phi), sin(phi) split.
+struct GadgetDfParams {
+  uint64_t xy, yz, nwork;
+  float ch, cl, sh, sl;
+  int eta;
+  int h;
 };
 
 // Density-matrix channels acting on groups of 4 (one qubit: bits t, t+N) or 16
@@ -97,6 +138,13 @@ cudaError_t launch_gate1(qs_prec prec, void* amps, const Gate1Params& p, cudaStr
 cudaError_t launch_dense(qs_prec prec, void* amps, const DenseParams& p, cudaStream_t st);
 cudaError_t launch_diag(qs_prec prec, void* amps, const DiagParams& p, cudaStream_t st);
 cudaError_t launch_gadget(qs_prec prec, void* amps, const GadgetParams& p, cudaStream_t st);
+// complex128 with double-float arithmetic (qs_gates_df.cu)
+cudaError_t launch_gate1_df(void* amps, const Gate1DfParams& p, cudaStream_t st);
+cudaError_t launch_dense_df(void* amps, const DenseParams& p, cudaStream_t st);
+cudaError_t launch_diag_df(void* amps, const DiagParams& p, cudaStream_t st);
+cudaError_t launch_gadget_df(void* amps, const GadgetDfParams& p, cudaStream_t st);
+// complex64 dense gates on the tensor cores, 3 <= n <= 5 (qs_tc.cu)
+cudaError_t launch_dense_tc(void* amps, const TcParams& p, cudaStream_t st);
 cudaError_t launch_group(qs_prec prec, void* amps, int op, const GroupParams& p, cudaStream_t st);
 cudaError_t launch_ptrace(qs_prec prec, const void* in, void* out, const PtraceParams& p,
                           cudaStream_t st);

@@ -20,6 +20,8 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 QS_C64 = 0
 QS_C128 = 1
+QS_ARITH_DF = 0
+QS_ARITH_F64 = 1
 
 STATUS = {
     0: "QS_OK", 1: "QS_ERR_ARG", 2: "QS_ERR_QUBIT_RANGE", 3: "QS_ERR_DUP_QUBIT",
@@ -41,6 +43,8 @@ SIGNATURES = {
     "qs_destroy": (_I, [_P]),
     "qs_get_info": (_I, [_P, _IP, _IP, _IP, _IP]),
     "qs_device_ptr": (_I, [_P, ctypes.POINTER(_P)]),
+    "qs_set_arithmetic": (_I, [_P, _I, _I]),
+    "qs_set_tensor_cores": (_I, [_P, _I]),
     "qs_set_amps": (_I, [_P, _P, _S, _S]),
     "qs_get_amps": (_I, [_P, _P, _S, _S]),
     "qs_init_zero": (_I, [_P]),
@@ -134,6 +138,14 @@ def qs_set_amps_ptr(h, host_ptr, first, count):
 def qs_get_amps(h, out_array, first=0):
     _check(_lib.qs_get_amps(h, out_array.ctypes.data, first, out_array.shape[0]), "qs_get_amps")
     return out_array
+
+
+def qs_set_arithmetic(h, arith, f64_share_16ths=0):
+    _check(_lib.qs_set_arithmetic(h, int(arith), int(f64_share_16ths)), "qs_set_arithmetic")
+
+
+def qs_set_tensor_cores(h, enable):
+    _check(_lib.qs_set_tensor_cores(h, 1 if enable else 0), "qs_set_tensor_cores")
 
 
 def qs_init_zero(h):

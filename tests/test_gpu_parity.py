@@ -17,7 +17,9 @@ from paper_2311_01512_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-ATOL = {1: 1e-13, 0: 2e-6}
+# precision modes: 1 = complex128 with the default double-float arithmetic,
+# 2 = complex128 with native FP64 arithmetic, 0 = complex64
+ATOL = {1: 1e-13, 2: 1e-13, 0: 2e-6}
 
 
 @pytest.fixture(scope="module")
@@ -26,14 +28,21 @@ def qs():
     return mod
 
 
+def make_state(qs, nq, density, mode):
+    st = qs.State(nq, density=density, prec=0 if mode == 0 else 1)
+    if mode == 2:
+        qs.qs_set_arithmetic(st.handle, qs.QS_ARITH_F64)
+    return st
+
+
 def new_sv(qs, nq, prec, psi):
-    st = qs.State(nq, density=False, prec=prec)
+    st = make_state(qs, nq, False, prec)
     st.set_amps(psi)
     return st
 
 
 def new_dm(qs, nq, prec, beta):
-    st = qs.State(nq, density=True, prec=prec)
+    st = make_state(qs, nq, True, prec)
     st.set_amps(beta)
     return st
 
@@ -49,7 +58,7 @@ def close(got, want, prec, scale=1.0):
     return err
 
 
-PRECS = [1, 0]
+PRECS = [1, 2, 0]
 
 
 # ---------------------------------------------------------------------------
@@ -146,7 +155,7 @@ def test_statevector_circuit(qs, prec):
         qs.apply_op(st.handle, op)
     want = orc.run_ops(psi, ops, is_density=False)
     got = st.get_amps()
-    if prec == 1:
+    if prec in (1, 2):
         err = float(np.max(np.abs(got - want)))
         assert err <= 0.5e-12, err        # 1e-12 per 1000 operations
     else:
@@ -163,7 +172,7 @@ def test_densmatr_init_pure_and_trace(qs, prec):
     rng = np.random.default_rng(21)
     nq = 5
     states, w = wl.random_mixed_state_vectors(nq, 3, rng)
-    dm = qs.State(nq, density=True, prec=prec)
+    dm = make_state(qs, nq, True, prec)
     for m, (s, wi) in enumerate(zip(states, w)):
         sv = new_sv(qs, nq, prec, s)
         qs.qs_init_pure_densmatr(dm.handle, sv.handle, wi, accumulate=m > 0)
@@ -286,7 +295,7 @@ def test_small_density_workload(qs, prec):
     ops = wl.small_densmatr_circuit(nq, 300, rng)
     traced = [int(x) for x in rng.choice(nq, 2, replace=False)]
     paulis, coeffs = wl.random_pauli_sum(nq - 2, 20, rng)
-    dm = qs.State(nq, density=True, prec=prec)
+    dm = make_state(qs, nq, True, prec)
     for m, (s, wi) in enumerate(zip(states, w)):
         sv = new_sv(qs, nq, prec, s)
         qs.qs_init_pure_densmatr(dm.handle, sv.handle, wi, accumulate=m > 0)
@@ -300,7 +309,7 @@ def test_small_density_workload(qs, prec):
     want = orc.run_ops(beta, ops, is_density=True)
     want_red = orc.partial_trace(want, traced)
     want_e = orc.expec_pauli_sum_densmatr(want_red, paulis, coeffs)
-    if prec == 1:
+    if prec in (1, 2):
         assert float(np.max(np.abs(dm.get_amps() - want))) <= 0.3e-12
         assert float(np.max(np.abs(red.get_amps() - want_red))) <= 0.3e-12
         assert abs(got_e - want_e) <= 1e-12
