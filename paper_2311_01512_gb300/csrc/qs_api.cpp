@@ -32,7 +32,7 @@ struct qs_state {
   qs_prec prec = QS_C128;
   qs_arith arith = QS_ARITH_DF;
   int f64_share = 0;   // sixteenths of one-target-gate chunks run in native FP64
-  int tensor_cores = 0;  // complex64 dense gates with 3..5 targets on tcgen05 (off until enabled)
+  int tensor_cores = 1;  // complex64 dense gates with 3..5 targets on tcgen05
   int* d_err = nullptr;  // device error word (bounded waits that ran out)
   cudaStream_t stream = nullptr;
   // reduction scratch (device) and its pinned host mirror

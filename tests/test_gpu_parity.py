@@ -349,3 +349,30 @@ def test_validation_errors(qs):
     amps = dm.get_amps()
     assert amps[0] == 1 and np.count_nonzero(amps) == 1
     assert sv.get_amps()[0] == 1
+
+
+# ---------------------------------------------------------------------------
+# tensor-core path (complex64 dense gates, 3..5 targets) against the CUDA cores
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nq,n,s", [(5, 5, 0), (8, 3, 2), (10, 4, 0), (13, 5, 2), (16, 3, 0), (16, 5, 1)])
+def test_tensor_core_gate_matches_cuda_cores(qs, nq, n, s):
+    rng = np.random.default_rng(600 + 10 * nq + n + s)
+    qsel = [int(x) for x in rng.choice(nq, n + s, replace=False)]
+    targs, ctrls = qsel[:n], qsel[n:]
+    psi = wl.random_statevector(nq, rng).astype(np.complex64)
+    mat = wl.haar_unitary(1 << n, rng)
+    want = orc.apply_ctrl_multi_target(psi.astype(np.complex128), ctrls, targs, mat)
+    out = {}
+    for tc in (0, 1):
+        st = qs.State(nq, prec=0)
+        qs.qs_set_tensor_cores(st.handle, tc)
+        st.set_amps(psi)
+        qs.qs_apply_ctrl_multi_target(st.handle, ctrls, targs, mat)
+        qs.qs_synchronize(st.handle)            # also reports a bounded-wait timeout
+        out[tc] = st.get_amps().astype(np.complex128)
+    scale = float(np.max(np.abs(want)))
+    err_cc = float(np.max(np.abs(out[0] - want)))
+    err_tc = float(np.max(np.abs(out[1] - want)))
+    # 3xTF32 keeps FP32-level accuracy: within 2^-20 of the largest amplitude
+    assert err_tc <= scale * 2.0 ** -20, (err_tc, err_cc, scale)
