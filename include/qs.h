@@ -215,6 +215,96 @@ qs_status qs_partial_trace(const qs_state* in, const int* targs, int n, void* d_
 qs_status qs_expec_pauli_sum(const qs_state* state, const int* paulis, const double* coeffs,
                              int num_terms, double* out);
 
+/* ------------------------------------------------------------------------
+ * Circuits and gate fusion.  A circuit records unitary operations (the gates
+ * above); a plan cuts it into blocks of consecutive gates that together touch
+ * at most max_block_qubits (<= QS_MAX_DENSE_TARGETS) qubits.  Each block of
+ * two or more gates is composed on the device into one dense matrix in FP64
+ * and applied as a single dense gate (tensor cores for complex64 blocks of
+ * 3..5 qubits, double-float arithmetic for complex128); a one-gate block
+ * runs that gate's own kernel.  Not in the paper: this groups the paper's
+ * many-target gate updates (Sec. "Many-target gate") so that each pass over
+ * the state does more work.  The applied operation is the same up to rounding.
+ * ------------------------------------------------------------------------ */
+typedef struct qs_circuit qs_circuit;
+
+typedef enum {
+  QS_PLAN_NONE = 0,    /* every gate its own block */
+  QS_PLAN_GREEDY = 1,  /* extend each block while its qubits fit */
+  QS_PLAN_COST = 2     /* minimum predicted time under a cost model (qs_circuit_plan_cost) */
+} qs_plan_kind;
+
+qs_status qs_circuit_create(int num_qubits, qs_circuit** out);
+qs_status qs_circuit_destroy(qs_circuit* circuit);
+/* Record a gate; the arguments are those of the qs_apply_* call of the same
+ * operation (copied; validated now). */
+qs_status qs_circuit_add_unitary(qs_circuit* circuit, const int* ctrls, int nctrl, const int* targs, int ntarg,
+                                 const double* mat);
+qs_status qs_circuit_add_diagonal(qs_circuit* circuit, const int* targs, int ntarg, const double* diag);
+qs_status qs_circuit_add_pauli_gadget(qs_circuit* circuit, const int* targs, const int* paulis, int n,
+                                      double theta);
+/* Plan (QS_PLAN_NONE or QS_PLAN_GREEDY) and compose the fused blocks on the
+ * current device; synchronous.  Recording more gates discards the plan. */
+qs_status qs_circuit_plan(qs_circuit* circuit, int kind, int max_block_qubits);
+qs_status qs_circuit_get_plan(const qs_circuit* circuit, int* num_gates, int* num_blocks, int* num_fused);
+/* Apply the planned circuit to a state of the same number of qubits
+ * (statevector, or density matrix: each block B then B^* on the shifted
+ * qubits).  An unplanned circuit is applied gate by gate.  Queued on the
+ * state's stream. */
+qs_status qs_circuit_apply(qs_circuit* circuit, qs_state* state);
+
+/* Apply a dense matrix on targs through the fused-block kernels (the path a
+ * planned block takes), whatever the number of targets; used to time blocks
+ * for the cost model.  Same arguments and semantics as
+ * qs_apply_ctrl_multi_target without controls. */
+qs_status qs_apply_dense_block(qs_state* state, const int* targs, int ntarg, const double* mat);
+
+/* ------------------------------------------------------------------------
+ * Learned cost model for fusion planning (not in the paper).  A perceptron
+ * with two hidden layers of 64 units predicts log(milliseconds) of one kernel
+ * launch from QS_COST_FEATURES features (qs_costmodel_encode).  It is trained
+ * on the GPU by this library's forward, backward and Adam kernels, on timings
+ * the simulator measures itself.  Plans only regroup gates, so the model never
+ * changes a result.
+ * ------------------------------------------------------------------------ */
+typedef struct qs_costmodel qs_costmodel;
+#define QS_COST_FEATURES 64
+#define QS_COST_PARAMS 8385   /* W1 64x64, b1 64, W2 64x64, b2 64, W3 64, b3 */
+
+typedef enum {
+  QS_COST_FUSED_DENSE = 0,  /* a fused block (qs_apply_dense_block) of `width` qubits */
+  QS_COST_GATE1 = 1,        /* a one-target gate with nctrl controls */
+  QS_COST_DENSE = 2,        /* a dense gate of `width` targets with nctrl controls */
+  QS_COST_DIAGONAL = 3,     /* a diagonal on `width` targets */
+  QS_COST_GADGET = 4,       /* a Pauli gadget with X or Y factors, `weight` factors */
+  QS_COST_PHASE = 5         /* a phase gadget (Z factors only) */
+} qs_cost_kind;
+
+/* New model with He-uniform random weights (splitmix64 stream of seed). */
+qs_status qs_costmodel_create(unsigned long long seed, qs_costmodel** out);
+qs_status qs_costmodel_destroy(qs_costmodel* model);
+/* Flat float parameters, layout as in QS_COST_PARAMS; n must equal it. */
+qs_status qs_costmodel_get_params(const qs_costmodel* model, float* host_params, int n);
+qs_status qs_costmodel_set_params(qs_costmodel* model, const float* host_params, int n);
+/* Features of one launch on `state` (its size, precision and settings). */
+qs_status qs_costmodel_encode(int kind, int width, unsigned long long qmask, int nctrl, int weight,
+                              const qs_state* state, float* out_features);
+/* Predictions (log ms) for n feature rows (host arrays). */
+qs_status qs_costmodel_predict(qs_costmodel* model, const float* features, int n, float* out);
+/* Mean-squared-error loss and its gradient over n rows (one batch). */
+qs_status qs_costmodel_gradient(qs_costmodel* model, const float* features, const float* targets, int n,
+                                float* out_grad, float* out_loss);
+/* Adam training on n rows (minibatches of `batch`, reshuffled every epoch by
+ * a splitmix64 stream of seed); final_loss = MSE over all rows. */
+qs_status qs_costmodel_train(qs_costmodel* model, const float* features, const float* targets, int n, int epochs,
+                             int batch, float lr, unsigned long long seed, float* final_loss);
+/* Plan a circuit for `state` by minimum predicted time: dynamic programming
+ * over cut points, each candidate block (at most max_block_qubits qubits,
+ * at most `window` gates) against running its gates unfused.  Composes the
+ * chosen blocks like qs_circuit_plan. */
+qs_status qs_circuit_plan_cost(qs_circuit* circuit, qs_costmodel* model, const qs_state* state,
+                               int max_block_qubits, int window);
+
 /* Largest number of terms qs_expec_pauli_sum_noalloc accepts. */
 #define QS_NOALLOC_MAX_TERMS 256
 

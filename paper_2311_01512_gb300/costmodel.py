@@ -1,0 +1,159 @@
+"""Training data and training for the fusion cost model.
+
+The simulator times its own kernel launches: random one-gate launches and
+random fused-block launches (qs_apply_dense_block) on states of several sizes
+and both precisions, each timed by CUDA events on the state's stream.  The
+features of each launch come from the library's encoder (qs_costmodel_encode)
+so that training and planning see identical rows; the target is log(ms).
+Training runs on the GPU through qs_costmodel_train (the library's forward,
+backward and Adam kernels).
+
+    python -m paper_2311_01512_gb300.costmodel --samples 20000 --out costmodel_gb300.npz
+"""
+
+import argparse
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+from . import workloads as wl
+
+WEIGHTS_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "costmodel_gb300.npz")
+
+# (kind name, probability): fused blocks dominate the planner's queries
+KINDS = [("fused", 0.40), ("gate1", 0.15), ("dense", 0.15), ("diag", 0.10), ("gadget", 0.10), ("phase", 0.10)]
+
+
+def _random_launch(qs, rng, nq):
+    """One random launch: (callable on a handle, cost kind, width, qubit mask, controls, weight)."""
+    r = rng.random()
+    acc = 0.0
+    for name, p in KINDS:
+        acc += p
+        if r <= acc:
+            break
+    if name == "fused":
+        k = int(rng.integers(1, 7))
+        targs = [int(x) for x in rng.choice(nq, k, replace=False)]
+        mat = wl.haar_unitary(1 << k, rng)
+        mask = sum(1 << t for t in targs)
+        return (lambda h: qs.qs_apply_dense_block(h, targs, mat)), qs.QS_COST_FUSED_DENSE, k, mask, 0, 0
+    if name in ("gate1", "dense"):
+        n = 1 if name == "gate1" else int(rng.integers(2, 4))
+        s = int(rng.integers(0, 4))
+        qsel = [int(x) for x in rng.choice(nq, n + s, replace=False)]
+        targs, ctrls = qsel[:n], qsel[n:]
+        mat = wl.haar_unitary(1 << n, rng)
+        mask = sum(1 << q for q in qsel)
+        kind = qs.QS_COST_GATE1 if n == 1 else qs.QS_COST_DENSE
+        return (lambda h: qs.qs_apply_ctrl_multi_target(h, ctrls, targs, mat)), kind, n, mask, s, 0
+    if name == "diag":
+        n = int(rng.integers(1, 4))
+        targs = [int(x) for x in rng.choice(nq, n, replace=False)]
+        d = np.exp(1j * rng.uniform(0, 2 * np.pi, 1 << n))
+        return (lambda h: qs.qs_apply_diagonal(h, targs, d)), qs.QS_COST_DIAGONAL, n, sum(1 << t for t in targs), 0, 0
+    w = int(rng.integers(1, 7))
+    targs = [int(x) for x in rng.choice(nq, w, replace=False)]
+    if name == "gadget":
+        paulis = [int(x) for x in rng.integers(1, 4, size=w)]
+        if not any(p in (1, 2) for p in paulis):
+            paulis[0] = 1
+        kind = qs.QS_COST_GADGET
+    else:
+        paulis = [3] * w
+        kind = qs.QS_COST_PHASE
+    theta = float(rng.uniform(0, 2 * np.pi))
+    return (lambda h: qs.qs_apply_pauli_gadget(h, targs, paulis, theta)), kind, 0, sum(1 << t for t in targs), 0, w
+
+
+def collect(samples, configs, seed=2311015122, device="cuda"):
+    """Time `samples` random launches spread over configs = [(prec, qubits), ...].
+    Returns (X [samples x 64] float32, t [samples] float32 = log ms, meta)."""
+    import torch
+    from . import qs
+    rng = np.random.default_rng(seed)
+    stream = torch.cuda.Stream()
+    states = []
+    for prec, nq in configs:
+        dtype = torch.complex128 if prec == qs.QS_C128 else torch.complex64
+        with torch.cuda.stream(stream):
+            t = torch.randn(1 << nq, dtype=dtype, device=device)
+            t /= torch.linalg.vector_norm(t)
+        stream.synchronize()
+        states.append((prec, nq, qs.State(nq, prec=prec, stream=stream, storage=t)))
+    X = np.zeros((samples, 64), dtype=np.float32)
+    y = np.zeros(samples, dtype=np.float32)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    # one warm-up launch of every kind on every state (first-launch costs)
+    for _, nq, st in states:
+        for _ in range(12):
+            fn = _random_launch(qs, rng, nq)[0]
+            fn(st.handle)
+    stream.synchronize()
+    t0 = time.time()
+    for i in range(samples):
+        prec, nq, st = states[i % len(states)]
+        fn, kind, width, mask, nctrl, weight = _random_launch(qs, rng, nq)
+        e0.record(stream)
+        fn(st.handle)
+        e1.record(stream)
+        e1.synchronize()
+        X[i] = qs.qs_costmodel_encode(kind, width, mask, nctrl, weight, st.handle)
+        y[i] = math.log(max(e0.elapsed_time(e1), 1e-4))
+    meta = {"samples": samples, "configs": configs, "seconds": time.time() - t0, "seed": seed}
+    for _, _, st in states:
+        st.close()
+    return X, y, meta
+
+
+def train(X, y, epochs=300, batch=512, lr=2e-3, seed=7, holdout=0.2):
+    """Train a fresh model on the GPU; returns (model, metrics)."""
+    from . import qs
+    n = X.shape[0]
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(n)
+    nh = int(n * holdout)
+    hold, tr = perm[:nh], perm[nh:]
+    model = qs.CostModel(seed=seed)
+    train_loss = model.train(X[tr], y[tr], epochs=epochs, batch=batch, lr=lr, seed=seed)
+    pred = model.predict(X[hold]) if nh else np.zeros(0)
+    err = pred - y[hold]
+    metrics = {"train_mse_log": float(train_loss),
+               "holdout_rmse_log": float(np.sqrt(np.mean(err ** 2))) if nh else None,
+               "holdout_median_abs_rel_time_error": float(np.median(np.abs(np.expm1(err)))) if nh else None,
+               "train_rows": int(len(tr)), "holdout_rows": int(nh)}
+    return model, metrics
+
+
+def save(model, path, meta):
+    np.savez(path, params=model.get_params(), meta=json.dumps(meta))
+
+
+def load(path=WEIGHTS_PATH):
+    from . import qs
+    data = np.load(path)
+    model = qs.CostModel()
+    model.set_params(data["params"])
+    return model, json.loads(str(data["meta"]))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--samples", type=int, default=20000)
+    ap.add_argument("--out", default=WEIGHTS_PATH)
+    ap.add_argument("--epochs", type=int, default=300)
+    args = ap.parse_args()
+    configs = [(0, 24), (0, 27), (0, 30), (0, 32), (1, 24), (1, 27), (1, 30), (1, 31)]
+    X, y, meta = collect(args.samples, configs)
+    model, metrics = train(X, y, epochs=args.epochs)
+    meta.update(metrics)
+    save(model, args.out, meta)
+    print(json.dumps(meta))
+
+
+if __name__ == "__main__":
+    main()

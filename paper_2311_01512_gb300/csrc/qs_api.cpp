@@ -17,36 +17,12 @@
 
 using qsk::kMaxQ;
 
-namespace {
+#include "qs_handle.h"
 
-constexpr int kRingSlots = 16;
-constexpr size_t kSlotBytes = 64 * 1024;  // one 64 x 64 complex128 matrix
+using qsapi::kRingSlots;
+using qsapi::kSlotBytes;
 
-}  // namespace
-
-struct qs_state {
-  void* amps = nullptr;
-  int nq = 0;          // N
-  int ns = 0;          // storage qubits
-  int is_density = 0;
-  qs_prec prec = QS_C128;
-  qs_arith arith = QS_ARITH_DF;
-  int f64_share = 0;   // sixteenths of one-target-gate chunks run in native FP64
-  int tensor_cores = 1;  // complex64 dense gates with 3..5 targets on tcgen05
-  int* d_err = nullptr;  // device error word (bounded waits that ran out)
-  cudaStream_t stream = nullptr;
-  // reduction scratch (device) and its pinned host mirror
-  double2* d_partials = nullptr;
-  double2* d_result = nullptr;
-  double2* h_result = nullptr;
-  // staging ring for matrices and term lists: pinned host slot -> device slot
-  unsigned char* h_ring = nullptr;
-  unsigned char* d_ring = nullptr;
-  cudaEvent_t ring_ev[kRingSlots] = {};
-  int ring_next = 0;
-};
-
-namespace {
+namespace qsapi {
 
 size_t amp_bytes(qs_prec p) { return p == QS_C128 ? 16 : 8; }
 
@@ -155,12 +131,12 @@ qs_status check_prob(double p) { return (p >= 0.0 && p <= 1.0) ? QS_OK : QS_ERR_
 
 // One dense or one-target gate pass on storage positions (already shifted).
 qs_status gate_pass(qs_state* s, const std::vector<int>& ctrls, const std::vector<int>& targs, const double* host_mat,
-                    const void* dev_mat, int conj) {
+                    const void* dev_mat, int conj, bool force_dense) {
   const int n = (int)targs.size();
   uint64_t cmask = 0;
   for (int c : ctrls) cmask |= 1ull << c;
   const bool df = s->prec == QS_C128 && s->arith == QS_ARITH_DF;
-  if (n == 1 && df) {
+  if (n == 1 && df && !force_dense) {
     qsk::Gate1DfParams p{};
     for (int e = 0; e < 8; ++e) {
       const double v = (conj && (e & 1)) ? -host_mat[e] : host_mat[e];
@@ -181,7 +157,7 @@ qs_status gate_pass(qs_state* s, const std::vector<int>& ctrls, const std::vecto
     p.f64_count = s->f64_share;
     return cuda_status(qsk::launch_gate1_df(s->amps, p, s->stream));
   }
-  if (n == 1) {
+  if (n == 1 && !force_dense) {
     qsk::Gate1Params p{};
     for (int e = 0; e < 4; ++e) {
       p.m[2 * e] = host_mat[2 * e];
@@ -305,7 +281,10 @@ qs_status reduce_to_host(qs_state* s, double* out) {
   return QS_OK;
 }
 
-}  // namespace
+}  // namespace qsapi
+
+using namespace qsapi;
+
 
 extern "C" {
 
@@ -434,6 +413,27 @@ qs_status qs_apply_ctrl_multi_target(qs_state* s, const int* ctrls, int nctrl, c
     if (st == QS_OK) st = st2;
   }
   return st;
+}
+
+qs_status qs_apply_dense_block(qs_state* s, const int* targs, int ntarg, const double* mat) {
+  if (!s || !mat) return QS_ERR_ARG;
+  if (ntarg < 1) return QS_ERR_ARG;
+  if (ntarg > QS_MAX_DENSE_TARGETS) return QS_ERR_TOO_MANY_TARGETS;
+  qs_status st = check_qubits(s->nq, targs, ntarg, nullptr, 0);
+  if (st != QS_OK) return st;
+  std::vector<int> t(targs, targs + ntarg);
+  const size_t mat_bytes = sizeof(double) * 2 * (size_t(1) << (2 * ntarg));
+  const void* dmat = nullptr;
+  int slot = -1;
+  st = ring_put(s, mat, mat_bytes, &dmat, &slot);
+  if (st != QS_OK) return st;
+  st = gate_pass(s, {}, t, nullptr, dmat, 0, true);
+  if (st == QS_OK && s->is_density) {
+    for (int& q : t) q += s->nq;
+    st = gate_pass(s, {}, t, nullptr, dmat, 1, true);
+  }
+  const qs_status st2 = ring_done(s, slot);
+  return st != QS_OK ? st : st2;
 }
 
 qs_status qs_apply_diagonal(qs_state* s, const int* targs, int ntarg, const double* diag) {

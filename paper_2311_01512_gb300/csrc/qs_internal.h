@@ -15,6 +15,10 @@ constexpr int kMaxDense = QS_MAX_DENSE_TARGETS;
 constexpr int kTileBits = 10;        // amplitudes staged per tile of the dense kernel: 2^10
 constexpr int kReduceBlocks = 1216;  // 152 SMs x 8: fixed grid of every stage-one reduction
 constexpr int kTermChunk = 2048;     // Pauli terms per device upload
+constexpr int kCostFeatures = 64;    // cost-model network: input features
+constexpr int kCostHidden = 64;      // hidden units per layer (two layers)
+constexpr int kCostParams = kCostHidden * kCostFeatures + kCostHidden + kCostHidden * kCostHidden + kCostHidden +
+                            kCostHidden + 1;
 
 // One-target gate on pairs (i0, i1 = i0 | 2^t) (Sec. "One-target gate",
 // Sec. "Many-control one-target gate").
@@ -132,6 +136,22 @@ struct PauliTerm {
   int pad;
 };
 
+// Block composition (qs_fuse.cu): one gate of a block, on block-local bits.
+struct ComposeInstr {
+  int kind;              // 0 dense with controls, 1 diagonal, 2 Pauli gadget
+  int n;                 // targets (dense, diagonal)
+  int ctrl_mask;         // block-local control bits
+  int tbit[kMaxDense];   // block-local bit of target q
+  int data_off;          // offset (doubles) of the matrix or diagonal
+  int xy, yz, eta;       // gadget: block-local masks, number of Y mod 4
+  double c, s;           // gadget: cos(phi), sin(phi), phi = -theta/2
+};
+struct ComposeBlock {
+  int k;                 // block qubits
+  int first, count;      // its instructions
+  int out_off;           // offset (doubles) of its 2^k x 2^k output matrix
+};
+
 // Launchers.  Each returns cudaGetLastError() after the launch.  amps is the
 // state's device storage, ns its number of storage qubits.
 cudaError_t launch_gate1(qs_prec prec, void* amps, const Gate1Params& p, cudaStream_t st);
@@ -145,6 +165,16 @@ cudaError_t launch_diag_df(void* amps, const DiagParams& p, cudaStream_t st);
 cudaError_t launch_gadget_df(void* amps, const GadgetDfParams& p, cudaStream_t st);
 // complex64 dense gates on the tensor cores, 3 <= n <= 5 (qs_tc.cu)
 cudaError_t launch_dense_tc(void* amps, const TcParams& p, cudaStream_t st);
+cudaError_t launch_block_compose(const ComposeBlock* blocks, int nblocks, const ComposeInstr* instrs,
+                                 const double* data, double* out, cudaStream_t st);
+// cost-model network (qs_mlp.cu)
+cudaError_t launch_mlp_forward(const float* params, const float* X, const int* idx, int B, float* y, float* z1,
+                               float* z2, cudaStream_t st);
+cudaError_t launch_mlp_backward(const float* params, const float* X, const float* t, const int* idx, int B,
+                                const float* y, const float* z1, const float* z2, float* dy, float* dz1, float* dz2,
+                                float* grad, cudaStream_t st);
+cudaError_t launch_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr,
+                            cudaStream_t st);
 cudaError_t launch_group(qs_prec prec, void* amps, int op, const GroupParams& p, cudaStream_t st);
 cudaError_t launch_ptrace(qs_prec prec, const void* in, void* out, const PtraceParams& p,
                           cudaStream_t st);

@@ -63,7 +63,35 @@ SIGNATURES = {
     "qs_calc_norm_or_trace": (_I, [_P, _DP]),
     "qs_synchronize": (_I, [_P]),
     "qs_expec_pauli_sum_noalloc": (_I, [_P, _I, _I, _I, _IP, _DP, _I, _P, _DP]),
+    "qs_circuit_create": (_I, [_I, ctypes.POINTER(_P)]),
+    "qs_circuit_destroy": (_I, [_P]),
+    "qs_circuit_add_unitary": (_I, [_P, _IP, _I, _IP, _I, _DP]),
+    "qs_circuit_add_diagonal": (_I, [_P, _IP, _I, _DP]),
+    "qs_circuit_add_pauli_gadget": (_I, [_P, _IP, _IP, _I, _D]),
+    "qs_circuit_plan": (_I, [_P, _I, _I]),
+    "qs_circuit_get_plan": (_I, [_P, _IP, _IP, _IP]),
+    "qs_circuit_apply": (_I, [_P, _P]),
+    "qs_apply_dense_block": (_I, [_P, _IP, _I, _DP]),
+    "qs_costmodel_create": (_I, [ctypes.c_ulonglong, ctypes.POINTER(_P)]),
+    "qs_costmodel_destroy": (_I, [_P]),
+    "qs_costmodel_get_params": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I]),
+    "qs_costmodel_set_params": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I]),
+    "qs_costmodel_encode": (_I, [_I, _I, ctypes.c_ulonglong, _I, _I, _P, ctypes.POINTER(ctypes.c_float)]),
+    "qs_costmodel_predict": (_I, [_P, ctypes.POINTER(ctypes.c_float), _I, ctypes.POINTER(ctypes.c_float)]),
+    "qs_costmodel_gradient": (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _I,
+                                   ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+    "qs_costmodel_train": (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _I, _I, _I,
+                                ctypes.c_float, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_float)]),
+    "qs_circuit_plan_cost": (_I, [_P, _P, _P, _I, _I]),
 }
+
+QS_COST_FEATURES = 64
+QS_COST_PARAMS = 8385
+QS_COST_FUSED_DENSE, QS_COST_GATE1, QS_COST_DENSE, QS_COST_DIAGONAL, QS_COST_GADGET, QS_COST_PHASE = range(6)
+
+QS_PLAN_NONE = 0
+QS_PLAN_GREEDY = 1
+QS_PLAN_COST = 2
 
 NOALLOC_MAX_TERMS = 256
 for _name, (_res, _args) in SIGNATURES.items():
@@ -311,6 +339,139 @@ class State:
         t = torch.empty(1 << (2 * m), dtype=self.tensor.dtype, device=self.tensor.device)
         h = qs_partial_trace(self.handle, targs, t.data_ptr())
         return State.wrap(h, t, m, True, self.prec, self.stream)
+
+
+class Circuit:
+    """A recorded circuit (qs_circuit_*): unitary operation records from
+    workloads.py, planned into fused blocks inside the library."""
+
+    def __init__(self, num_qubits, ops=()):
+        self.handle = _P()
+        _check(_lib.qs_circuit_create(num_qubits, ctypes.byref(self.handle)), "qs_circuit_create")
+        for op in ops:
+            self.add(op)
+
+    def add(self, op):
+        kind = op["op"]
+        if kind == "unitary":
+            c, nc = _ints(op["ctrls"])
+            t, nt = _ints(op["targs"])
+            keep, mp = _doubles(op["mat"])
+            _check(_lib.qs_circuit_add_unitary(self.handle, c, nc, t, nt, mp), "qs_circuit_add_unitary")
+        elif kind == "diagonal":
+            t, nt = _ints(op["targs"])
+            keep, dp = _doubles(np.asarray(op["diag"], dtype=np.complex128))
+            _check(_lib.qs_circuit_add_diagonal(self.handle, t, nt, dp), "qs_circuit_add_diagonal")
+        elif kind == "gadget":
+            t, nt = _ints(op["targs"])
+            p, _ = _ints(op["paulis"])
+            _check(_lib.qs_circuit_add_pauli_gadget(self.handle, t, p, nt, float(op["theta"])),
+                   "qs_circuit_add_pauli_gadget")
+        else:
+            raise ValueError("circuits record unitary operations only, not " + kind)
+
+    def plan(self, kind=QS_PLAN_GREEDY, max_block_qubits=5):
+        _check(_lib.qs_circuit_plan(self.handle, int(kind), int(max_block_qubits)), "qs_circuit_plan")
+        return self.stats()
+
+    def stats(self):
+        g, b, f = _I(), _I(), _I()
+        _check(_lib.qs_circuit_get_plan(self.handle, ctypes.byref(g), ctypes.byref(b), ctypes.byref(f)),
+               "qs_circuit_get_plan")
+        return {"gates": g.value, "blocks": b.value, "fused": f.value}
+
+    def plan_cost(self, model, state_handle, max_block_qubits=5, window=24):
+        _check(_lib.qs_circuit_plan_cost(self.handle, model.handle, state_handle, int(max_block_qubits), int(window)),
+               "qs_circuit_plan_cost")
+        return self.stats()
+
+    def apply(self, state_handle):
+        _check(_lib.qs_circuit_apply(self.handle, state_handle), "qs_circuit_apply")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(_lib.qs_circuit_destroy(self.handle), "qs_circuit_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def qs_apply_dense_block(h, targs, mat):
+    t, nt = _ints(targs)
+    keep, mp = _doubles(mat)
+    _check(_lib.qs_apply_dense_block(h, t, nt, mp), "qs_apply_dense_block")
+
+
+_FP = ctypes.POINTER(ctypes.c_float)
+
+
+def _f32(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    return a, a.ctypes.data_as(_FP)
+
+
+class CostModel:
+    """Handle of the library's cost-model network (qs_costmodel_*)."""
+
+    def __init__(self, seed=2311015120):
+        self.handle = _P()
+        _check(_lib.qs_costmodel_create(ctypes.c_ulonglong(seed), ctypes.byref(self.handle)), "qs_costmodel_create")
+
+    def get_params(self):
+        out = np.empty(QS_COST_PARAMS, dtype=np.float32)
+        _check(_lib.qs_costmodel_get_params(self.handle, out.ctypes.data_as(_FP), QS_COST_PARAMS),
+               "qs_costmodel_get_params")
+        return out
+
+    def set_params(self, params):
+        keep, pp = _f32(params)
+        _check(_lib.qs_costmodel_set_params(self.handle, pp, keep.size), "qs_costmodel_set_params")
+
+    def predict(self, X):
+        keep, xp = _f32(X)
+        out = np.empty(keep.shape[0], dtype=np.float32)
+        _check(_lib.qs_costmodel_predict(self.handle, xp, keep.shape[0], out.ctypes.data_as(_FP)),
+               "qs_costmodel_predict")
+        return out
+
+    def gradient(self, X, t):
+        kx, xp = _f32(X)
+        kt, tp = _f32(t)
+        g = np.empty(QS_COST_PARAMS, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(_lib.qs_costmodel_gradient(self.handle, xp, tp, kx.shape[0], g.ctypes.data_as(_FP), ctypes.byref(loss)),
+               "qs_costmodel_gradient")
+        return g, loss.value
+
+    def train(self, X, t, epochs=200, batch=512, lr=1e-3, seed=7):
+        kx, xp = _f32(X)
+        kt, tp = _f32(t)
+        loss = ctypes.c_float()
+        _check(_lib.qs_costmodel_train(self.handle, xp, tp, kx.shape[0], int(epochs), int(batch), ctypes.c_float(lr),
+                                       ctypes.c_ulonglong(seed), ctypes.byref(loss)), "qs_costmodel_train")
+        return loss.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(_lib.qs_costmodel_destroy(self.handle), "qs_costmodel_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def qs_costmodel_encode(kind, width, qmask, nctrl, weight, state_handle):
+    out = np.empty(QS_COST_FEATURES, dtype=np.float32)
+    _check(_lib.qs_costmodel_encode(int(kind), int(width), ctypes.c_ulonglong(int(qmask)), int(nctrl), int(weight),
+                                    state_handle, out.ctypes.data_as(_FP)), "qs_costmodel_encode")
+    return out
 
 
 def apply_op(h, op):

@@ -1,0 +1,87 @@
+"""Planned circuits with gate fusion (qs_circuit_*) against the CPU oracle.
+
+Fusion regroups the same unitary operations into dense blocks composed in
+FP64, so the planned result must equal the gate-by-gate oracle result within
+the same tolerances as single operations: complex128 1e-12 per 1000 gates,
+complex64 (tensor cores, 3xTF32) FP32-level."""
+
+import numpy as np
+import pytest
+
+from oracle import qsim_oracle as orc
+from paper_2311_01512_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qs():
+    from paper_2311_01512_gb300 import qs as mod
+    return mod
+
+
+def run_plan(qs, nq, density, prec, init, ops, kind, width):
+    circ = qs.Circuit(nq, ops)
+    stats = circ.plan(kind, width)
+    st = qs.State(nq, density=density, prec=prec)
+    st.set_amps(init)
+    circ.apply(st.handle)
+    qs.qs_synchronize(st.handle)
+    out = st.get_amps().astype(np.complex128)
+    st.close()
+    circ.close()
+    return out, stats
+
+
+@pytest.mark.parametrize("width", [2, 4, 5, 6])
+def test_statevector_circuit_fused_c128(qs, width):
+    rng = wl.rng_for("fuse-sv12-%d" % width)
+    nq = 12
+    psi = wl.random_statevector(nq, rng)
+    ops = wl.statevector_circuit(nq, 160, rng, max_targs=3, max_ctrls=2)
+    want = orc.run_ops(psi, ops, is_density=False)
+    got, stats = run_plan(qs, nq, False, 1, psi, ops, qs.QS_PLAN_GREEDY, width)
+    assert stats["gates"] == 160 and stats["blocks"] < 160 and stats["fused"] > 0
+    assert float(np.max(np.abs(got - want))) <= 0.3e-12
+
+
+def test_unitary_circuit_fused_c64_tensor_cores(qs):
+    rng = wl.rng_for("fuse-c64")
+    nq = 14
+    psi = wl.random_statevector(nq, rng)
+    ops = wl.unitary_circuit(nq, 200, rng)
+    want = orc.run_ops(psi, ops, is_density=False)
+    got_fused, stats = run_plan(qs, nq, False, 0, psi.astype(np.complex64), ops, qs.QS_PLAN_GREEDY, 5)
+    got_plain, _ = run_plan(qs, nq, False, 0, psi.astype(np.complex64), ops, qs.QS_PLAN_NONE, 1)
+    scale = float(np.max(np.abs(want)))
+    err_f = float(np.max(np.abs(got_fused - want)))
+    err_p = float(np.max(np.abs(got_plain - want)))
+    assert stats["blocks"] < 120
+    # 200 gates in FP32-level arithmetic, as fused blocks or gate by gate
+    assert err_f <= 200 * scale * 2.0 ** -22, (err_f, err_p)
+    fid = abs(np.vdot(want, got_fused)) ** 2 / (np.vdot(want, want).real * np.vdot(got_fused, got_fused).real)
+    assert 1.0 - fid <= 1e-6
+
+
+def test_density_circuit_fused_c128(qs):
+    rng = wl.rng_for("fuse-dm5")
+    nq = 5
+    states, w = wl.random_mixed_state_vectors(nq, 3, rng)
+    beta = sum(wi * orc.densmatr_from_pure(s) for wi, s in zip(w, states))
+    ops = wl.unitary_circuit(nq, 60, rng)
+    want = orc.run_ops(beta, ops, is_density=True)
+    got, stats = run_plan(qs, nq, True, 1, beta, ops, qs.QS_PLAN_GREEDY, 3)
+    assert stats["fused"] > 0
+    assert float(np.max(np.abs(got - want))) <= 1e-13
+
+
+def test_plan_validation(qs):
+    circ = qs.Circuit(4)
+    with pytest.raises(qs.QSError):
+        circ.plan(qs.QS_PLAN_GREEDY, 7)          # wider than a dense gate allows
+    with pytest.raises(qs.QSError):
+        circ.add({"op": "unitary", "ctrls": [1], "targs": [1], "mat": np.eye(2)})
+    circ.add({"op": "unitary", "ctrls": [], "targs": [0], "mat": np.eye(2)})
+    st = qs.State(5)
+    with pytest.raises(qs.QSError):
+        circ.apply(st.handle)                    # qubit count differs
