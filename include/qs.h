@@ -305,6 +305,42 @@ qs_status qs_costmodel_train(qs_costmodel* model, const float* features, const f
 qs_status qs_circuit_plan_cost(qs_circuit* circuit, qs_costmodel* model, const qs_state* state,
                                int max_block_qubits, int window);
 
+/* ------------------------------------------------------------------------
+ * Batched engine (not in the paper): many independent statevectors of at
+ * most 24 qubits, each with its own circuit of dense gates (1 or 2 targets,
+ * up to 5 controls), diagonals (up to 3 targets) and Pauli gadgets, run by
+ * ONE persistent kernel launch recorded in a CUDA graph.  CTAs take states
+ * from a work counter, largest first; a state that fits in shared memory is
+ * processed there.  complex64 in FP32, complex128 in double-float
+ * arithmetic (see qs_arith).  The gate semantics are those of
+ * qs_apply_ctrl_multi_target, qs_apply_diagonal and qs_apply_pauli_gadget.
+ * ------------------------------------------------------------------------ */
+typedef struct qs_batch qs_batch;
+
+/* num_qubits[s] in 1..24 for every state s; all states share `prec` and the
+ * stream. */
+qs_status qs_batch_create(int num_states, const int* num_qubits, qs_prec prec, void* cuda_stream, qs_batch** out);
+qs_status qs_batch_destroy(qs_batch* batch);
+/* Amplitudes the caller's device pool must hold, and where state s starts
+ * (each state starts on a 256-byte boundary). */
+qs_status qs_batch_pool_amps(const qs_batch* batch, size_t* num_amps);
+qs_status qs_batch_state_offset(const qs_batch* batch, int state, size_t* offset_amps);
+/* Caller-owned device memory (256-byte aligned) holding every state. */
+qs_status qs_batch_bind_pool(qs_batch* batch, void* d_pool);
+qs_status qs_batch_add_unitary(qs_batch* batch, int state, const int* ctrls, int nctrl, const int* targs, int ntarg,
+                               const double* mat);
+qs_status qs_batch_add_diagonal(qs_batch* batch, int state, const int* targs, int ntarg, const double* diag);
+qs_status qs_batch_add_pauli_gadget(qs_batch* batch, int state, const int* targs, const int* paulis, int n,
+                                    double theta);
+/* Upload the programs and record the launch in a CUDA graph.  With
+ * autotune != 0 every candidate launch shape is timed by running the whole
+ * batch once on the bound pool: the pool's contents are unspecified
+ * afterwards, so write the initial states after compiling.  Synchronous. */
+qs_status qs_batch_compile(qs_batch* batch, int autotune);
+/* Replay the recorded launch on the batch's stream (asynchronous). */
+qs_status qs_batch_run(qs_batch* batch);
+qs_status qs_batch_info(const qs_batch* batch, int* threads, int* ctas, int* smem_qubits, long* total_ops);
+
 /* Largest number of terms qs_expec_pauli_sum_noalloc accepts. */
 #define QS_NOALLOC_MAX_TERMS 256
 

@@ -152,6 +152,28 @@ struct ComposeBlock {
   int out_off;           // offset (doubles) of its 2^k x 2^k output matrix
 };
 
+// Batched engine (qs_batch_kernels.cu): one operation of a state's program
+// and one state (at most 24 qubits: 32-bit indices).
+struct BatchOp {
+  int kind;              // 0 dense on 1 or 2 targets with controls, 1 diagonal (<= 3 targets), 2 Pauli gadget
+  int n;
+  int t[3];
+  uint32_t ctrl;         // control mask
+  uint32_t xy, yz;       // gadget masks
+  int eta, h;            // gadget: number of Y mod 4, highest bit of xy
+  int nins;              // dense: sorted target and control positions
+  int8_t ins[8];
+  double c, s;           // gadget: cos(phi), sin(phi), phi = -theta/2
+  double m[32];          // dense: 2^n x 2^n row-major; diagonal: 2^n entries (complex128 re, im)
+};
+struct BatchState {
+  uint64_t offset;       // first amplitude in the pool
+  int nq;
+  int first_op;
+  int nops;
+  int pad;
+};
+
 // Launchers.  Each returns cudaGetLastError() after the launch.  amps is the
 // state's device storage, ns its number of storage qubits.
 cudaError_t launch_gate1(qs_prec prec, void* amps, const Gate1Params& p, cudaStream_t st);
@@ -175,6 +197,10 @@ cudaError_t launch_mlp_backward(const float* params, const float* X, const float
                                 float* grad, cudaStream_t st);
 cudaError_t launch_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr,
                             cudaStream_t st);
+int num_sms();  // multiprocessors of the current device (cached)
+cudaError_t batch_set_max_smem(int bytes);
+cudaError_t launch_batch(qs_prec prec, void* pool, const BatchState* states, const int* order, int nstates,
+                         const BatchOp* ops, int* counter, int threads, int ctas, int smem_qubits, cudaStream_t st);
 cudaError_t launch_group(qs_prec prec, void* amps, int op, const GroupParams& p, cudaStream_t st);
 cudaError_t launch_ptrace(qs_prec prec, const void* in, void* out, const PtraceParams& p,
                           cudaStream_t st);

@@ -83,6 +83,17 @@ SIGNATURES = {
     "qs_costmodel_train": (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _I, _I, _I,
                                 ctypes.c_float, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_float)]),
     "qs_circuit_plan_cost": (_I, [_P, _P, _P, _I, _I]),
+    "qs_batch_create": (_I, [_I, _IP, _I, _P, ctypes.POINTER(_P)]),
+    "qs_batch_destroy": (_I, [_P]),
+    "qs_batch_pool_amps": (_I, [_P, ctypes.POINTER(_S)]),
+    "qs_batch_state_offset": (_I, [_P, _I, ctypes.POINTER(_S)]),
+    "qs_batch_bind_pool": (_I, [_P, _P]),
+    "qs_batch_add_unitary": (_I, [_P, _I, _IP, _I, _IP, _I, _DP]),
+    "qs_batch_add_diagonal": (_I, [_P, _I, _IP, _I, _DP]),
+    "qs_batch_add_pauli_gadget": (_I, [_P, _I, _IP, _IP, _I, _D]),
+    "qs_batch_compile": (_I, [_P, _I]),
+    "qs_batch_run": (_I, [_P]),
+    "qs_batch_info": (_I, [_P, _IP, _IP, _IP, ctypes.POINTER(ctypes.c_long)]),
 }
 
 QS_COST_FEATURES = 64
@@ -391,6 +402,76 @@ class Circuit:
     def close(self):
         if getattr(self, "handle", None):
             _check(_lib.qs_circuit_destroy(self.handle), "qs_circuit_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """qs_batch_*: many statevectors with their own circuits in one persistent
+    launch.  The amplitude pool is a torch tensor owned by this object."""
+
+    def __init__(self, num_qubits, prec=QS_C64, stream=None, device="cuda"):
+        import torch
+        self.num_qubits = [int(q) for q in num_qubits]
+        self.prec = prec
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        q, nq = _ints(self.num_qubits)
+        self.handle = _P()
+        _check(_lib.qs_batch_create(nq, q, prec, _P(self.stream.cuda_stream), ctypes.byref(self.handle)),
+               "qs_batch_create")
+        n = _S()
+        _check(_lib.qs_batch_pool_amps(self.handle, ctypes.byref(n)), "qs_batch_pool_amps")
+        dtype = torch.complex128 if prec == QS_C128 else torch.complex64
+        self.pool = torch.zeros(n.value, dtype=dtype, device=device)
+        _check(_lib.qs_batch_bind_pool(self.handle, _P(self.pool.data_ptr())), "qs_batch_bind_pool")
+        self.offsets = []
+        for s in range(len(self.num_qubits)):
+            off = _S()
+            _check(_lib.qs_batch_state_offset(self.handle, s, ctypes.byref(off)), "qs_batch_state_offset")
+            self.offsets.append(off.value)
+
+    def view(self, s):
+        return self.pool[self.offsets[s]:self.offsets[s] + (1 << self.num_qubits[s])]
+
+    def add(self, s, op):
+        kind = op["op"]
+        if kind == "unitary":
+            c, nc = _ints(op["ctrls"])
+            t, nt = _ints(op["targs"])
+            keep, mp = _doubles(op["mat"])
+            _check(_lib.qs_batch_add_unitary(self.handle, s, c, nc, t, nt, mp), "qs_batch_add_unitary")
+        elif kind == "diagonal":
+            t, nt = _ints(op["targs"])
+            keep, dp = _doubles(np.asarray(op["diag"], dtype=np.complex128))
+            _check(_lib.qs_batch_add_diagonal(self.handle, s, t, nt, dp), "qs_batch_add_diagonal")
+        elif kind == "gadget":
+            t, nt = _ints(op["targs"])
+            p, _ = _ints(op["paulis"])
+            _check(_lib.qs_batch_add_pauli_gadget(self.handle, s, t, p, nt, float(op["theta"])),
+                   "qs_batch_add_pauli_gadget")
+        else:
+            raise ValueError("batched circuits take unitary operations only")
+
+    def compile(self, autotune=True):
+        _check(_lib.qs_batch_compile(self.handle, 1 if autotune else 0), "qs_batch_compile")
+
+    def run(self):
+        _check(_lib.qs_batch_run(self.handle), "qs_batch_run")
+
+    def info(self):
+        a, b, c, d = _I(), _I(), _I(), ctypes.c_long()
+        _check(_lib.qs_batch_info(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)),
+               "qs_batch_info")
+        return {"threads": a.value, "ctas": b.value, "smem_qubits": c.value, "total_ops": d.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(_lib.qs_batch_destroy(self.handle), "qs_batch_destroy")
             self.handle = None
 
     def __del__(self):

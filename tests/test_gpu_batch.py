@@ -1,0 +1,61 @@
+"""The persistent batched engine (qs_batch_*): every state of a batch with its
+own random circuit, run in one recorded launch, against the CPU oracle state
+by state (complex128 in double-float: 1e-12 per 1000 gates; complex64: 1 - F
+<= 1e-6).  Sizes include states too large for shared memory, so both the
+shared-memory and the global-memory paths run."""
+
+import numpy as np
+import pytest
+
+from oracle import qsim_oracle as orc
+from paper_2311_01512_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qs():
+    from paper_2311_01512_gb300 import qs as mod
+    return mod
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_batch_matches_oracle(qs, prec):
+    import torch
+    rng = wl.rng_for("batch-test-%d" % prec)
+    sizes = [int(x) for x in rng.integers(3, 14, size=40)] + [15, 16, 17]
+    batch = qs.Batch(sizes, prec=prec)
+    circuits = []
+    for s, nq in enumerate(sizes):
+        ops = wl.unitary_circuit(nq, int(rng.integers(10, 60)), rng)
+        for op in ops:
+            batch.add(s, op)
+        circuits.append(ops)
+    batch.compile(autotune=True)
+    info = batch.info()
+    assert info["smem_qubits"] < 17            # the largest states take the global path
+    dtype = np.complex128 if prec == 1 else np.complex64
+    inits = [wl.random_statevector(nq, rng) for nq in sizes]
+    for s, psi in enumerate(inits):
+        batch.view(s).copy_(torch.from_numpy(psi.astype(dtype)))
+    batch.run()
+    batch.run()                                 # the recorded launch replays
+    torch.cuda.synchronize()
+    for s, (psi, ops) in enumerate(zip(inits, circuits)):
+        want = orc.run_ops(orc.run_ops(psi, ops, False), ops, False)
+        got = batch.view(s).cpu().numpy().astype(np.complex128)
+        if prec == 1:
+            assert float(np.max(np.abs(got - want))) <= 1e-12, s
+        else:
+            fid = abs(np.vdot(want, got)) ** 2 / (np.vdot(got, got).real * np.vdot(want, want).real)
+            assert 1.0 - fid <= 1e-6, (s, 1.0 - fid)
+
+
+def test_batch_validation(qs):
+    batch = qs.Batch([4, 5])
+    with pytest.raises(qs.QSError):
+        batch.add(0, {"op": "unitary", "ctrls": [], "targs": [0, 1, 2], "mat": np.eye(8)})
+    with pytest.raises(qs.QSError):
+        batch.add(1, {"op": "unitary", "ctrls": [], "targs": [5], "mat": np.eye(2)})
+    with pytest.raises(qs.QSError):
+        batch.add(2, {"op": "unitary", "ctrls": [], "targs": [0], "mat": np.eye(2)})
