@@ -47,6 +47,8 @@ def parse_args(argv=None):
                     help="complex128 arithmetic: double-float on the FP32 pipes (default) or native FP64")
     ap.add_argument("--f64-share", type=int, default=0,
                     help="sixteenths of one-target-gate work done in native FP64 beside double-float")
+    ap.add_argument("--no-fused", action="store_true", help="skip the fused tensor-core comparison")
+    ap.add_argument("--fused-qubits", type=int, default=30)
     ap.add_argument("--detail", default="", help="write per-kernel-family statistics to this JSON file")
     ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args(argv)
@@ -366,6 +368,13 @@ def main_ours(args):
                "note": "pinned host state uploaded through qs_set_amps, %d ops, norm read back" % NUM_OPS,
                "final_norm": out_norm.real}
 
+    fused = None
+    if not args.no_fused and rank == 0:
+        st.close()
+        del psi
+        torch.cuda.empty_cache()
+        fused = fused_comparison(args, device)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -385,6 +394,8 @@ def main_ours(args):
         }
         if e2e is not None:
             line["e2e"] = e2e
+        if fused is not None:
+            line["fused_tc"] = fused
         if cpu_res is not None:
             line["cpu_baseline"] = cpu_baseline_dict(cpu_res)
         print(json.dumps(line), flush=True)
@@ -399,10 +410,104 @@ def main_ours(args):
                                          for k in range(args.steps)],
                            "ops": [{"op": op["op"], "targs": op["targs"], "ctrls": op.get("ctrls", []),
                                     "family": fams[i]} for i, op in enumerate(ops)]}, f)
-    st.close()
+    if fused is None:
+        st.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# Fused tensor-core form vs the plain per-gate FP64 form (same GPU)
+# ---------------------------------------------------------------------------
+
+FUSED_OPS = 1000
+
+
+def fused_comparison(args, device):
+    """The 1000-gate unitary circuit of the fused workload (1q Haar; 1-2-target
+    Haar with 0-3 controls; gadgets of weight 1-6) on one random state: the
+    plain per-gate form (complex128, native FP64 and double-float) against
+    cost-model-planned fused blocks on the tensor cores (complex64, 3xTF32).
+    Reports times, speedup, max |delta amp| and 1 - fidelity of the fused
+    result against the per-gate complex128 result."""
+    import torch
+    from paper_2311_01512_gb300 import costmodel, qs
+    from paper_2311_01512_gb300 import workloads as wl
+    nq = args.fused_qubits
+    ops = wl.unitary_circuit(nq, FUSED_OPS, wl.rng_for("fused-tc-circuit"))
+    stream = torch.cuda.Stream(device=device)
+    with torch.cuda.stream(stream):
+        psi0 = device_random_state(nq, device)
+    stream.synchronize()
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    out = {"qubits": nq, "ops": FUSED_OPS}
+
+    def reset(dst, src):
+        # copies on the circuit's stream, so that they are ordered with its kernels
+        with torch.cuda.stream(stream):
+            dst.copy_(src)
+        stream.synchronize()
+
+    # per-gate complex128, native FP64 and double-float
+    with torch.cuda.stream(stream):
+        t128 = psi0.clone()
+        t64 = psi0.to(torch.complex64)
+    stream.synchronize()
+    st = qs.State(nq, prec=qs.QS_C128, stream=stream, storage=t128)
+    circ = qs.Circuit(nq, ops)
+    circ.plan(qs.QS_PLAN_NONE, 1)
+    qs.qs_set_arithmetic(st.handle, qs.QS_ARITH_F64)
+    out["per_gate_f64_ms"] = timed(lambda: circ.apply(st.handle))
+    reset(t128, psi0)
+    qs.qs_set_arithmetic(st.handle, qs.QS_ARITH_DF)
+    out["per_gate_df_ms"] = timed(lambda: circ.apply(st.handle))
+    # fused complex64 on the tensor cores, planned by the learned cost model
+    st64 = qs.State(nq, prec=qs.QS_C64, stream=stream, storage=t64)
+    model, meta = costmodel.load()
+    circ64 = qs.Circuit(nq, ops)
+    plan = circ64.plan_cost(model, st64.handle, max_block_qubits=5, window=24)
+    out["fused_ms"] = timed(lambda: circ64.apply(st64.handle))
+    out["plan"] = plan
+    out["costmodel_holdout_median_time_error"] = meta.get("holdout_median_abs_rel_time_error")
+    # unfused complex64 for reference
+    reset(t64, psi0)
+    circ64n = qs.Circuit(nq, ops)
+    circ64n.plan(qs.QS_PLAN_NONE, 1)
+    out["per_gate_c64_ms"] = timed(lambda: circ64n.apply(st64.handle))
+    reset(t64, psi0)
+    circ64.apply(st64.handle)
+    stream.synchronize()
+    with torch.cuda.stream(stream):
+        a = t128
+        b = t64.to(torch.complex128)
+        dmax = (a - b).abs().max()
+        ov = torch.vdot(a, b)
+        fid_t = ov.abs() ** 2 / (torch.vdot(a, a).real * torch.vdot(b, b).real)
+    stream.synchronize()
+    out["max_abs_delta_amp"] = float(dmax.item())
+    fid = float(fid_t.item())
+    out["one_minus_fidelity"] = 1.0 - fid
+    out["reference"] = "per-gate complex128 double-float result (oracle-checked at small sizes)"
+    out["speedup_vs_per_gate_f64"] = out["per_gate_f64_ms"] / out["fused_ms"]
+    out["speedup_vs_per_gate_df"] = out["per_gate_df_ms"] / out["fused_ms"]
+    for h in (st, st64):
+        h.close()
+    for c in (circ, circ64, circ64n):
+        c.close()
+    model.close()
+    del t128, t64, psi0
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -54,7 +54,7 @@ __device__ __forceinline__ double2 cacc_result(const cacc& a) {
 // f64_count run in native FP64 instead, so that the FP64 pipe, idle otherwise,
 // takes a share of the work; the choice is warp-uniform.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_gate1_df(double2* __restrict__ psi, const __grid_constant__ Gate1DfParams p) {
+__global__ void __launch_bounds__(256, 6) k_gate1_df(double2* __restrict__ psi, const __grid_constant__ Gate1DfParams p) {
   cdf m[4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
@@ -189,7 +189,13 @@ __global__ void __launch_bounds__(256) k_dense_df(double2* __restrict__ psi, con
 // ---------------------------------------------------------------------------
 // Diagonal: alpha_i -> d_j alpha_i.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_diag_df(double2* __restrict__ psi, const __grid_constant__ DiagParams p) {
+__device__ __forceinline__ int diag_index(uint64_t i, const DiagParams& p) {
+  int j = 0;
+  for (int q = 0; q < p.n; ++q) j |= (int)((i >> p.tpos[q]) & 1) << q;
+  return j;
+}
+
+__global__ void __launch_bounds__(256, 8) k_diag_df(double2* __restrict__ psi, const __grid_constant__ DiagParams p) {
   __shared__ cdf d[64];
   for (int j = threadIdx.x; j < (1 << p.n); j += blockDim.x) {
     cdf v;
@@ -199,11 +205,21 @@ __global__ void __launch_bounds__(256) k_diag_df(double2* __restrict__ psi, cons
   }
   __syncthreads();
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.namps; i += stride) {
-    int j = 0;
-    for (int q = 0; q < p.n; ++q) j |= (int)((i >> p.tpos[q]) & 1) << q;
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // two amplitudes per iteration, both loads issued first
+  for (; i + stride < p.namps; i += 2 * stride) {
+    const double2 v0 = psi[i], v1 = psi[i + stride];
+    cdf a;
+    a.re = qsdf::split(v0.x);
+    a.im = qsdf::split(v0.y);
+    psi[i] = cacc_result(cmul_first(d[diag_index(i, p)], a));
+    a.re = qsdf::split(v1.x);
+    a.im = qsdf::split(v1.y);
+    psi[i + stride] = cacc_result(cmul_first(d[diag_index(i + stride, p)], a));
+  }
+  for (; i < p.namps; i += stride) {
     const cdf a = load_split(psi + i);
-    psi[i] = cacc_result(cmul_first(d[j], a));
+    psi[i] = cacc_result(cmul_first(d[diag_index(i, p)], a));
   }
 }
 
@@ -231,7 +247,7 @@ __device__ __forceinline__ double2 lin2(df c, const cdf& a, df s, const cdf& b) 
   return make_double2(qsdf::finish(re), qsdf::finish(im));
 }
 
-__global__ void __launch_bounds__(256) k_gadget_df(double2* __restrict__ psi, const __grid_constant__ GadgetDfParams p) {
+__global__ void __launch_bounds__(256, 8) k_gadget_df(double2* __restrict__ psi, const __grid_constant__ GadgetDfParams p) {
   const df c{p.ch, p.cl}, s{p.sh, p.sl}, ns{-p.sh, -p.sl};
   const int q = (p.eta + 1) & 3;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -247,10 +263,21 @@ __global__ void __launch_bounds__(256) k_gadget_df(double2* __restrict__ psi, co
 }
 
 // Phase gadget: alpha_i -> (c + i s_i) alpha_i.
-__global__ void __launch_bounds__(256) k_phase_df(double2* __restrict__ psi, const __grid_constant__ GadgetDfParams p) {
+__global__ void __launch_bounds__(256, 8) k_phase_df(double2* __restrict__ psi, const __grid_constant__ GadgetDfParams p) {
   const df c{p.ch, p.cl}, s{p.sh, p.sl}, ns{-p.sh, -p.sl};
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.nwork; i += stride) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + stride < p.nwork; i += 2 * stride) {
+    const double2 v0 = psi[i], v1 = psi[i + stride];
+    cdf a;
+    a.re = qsdf::split(v0.x);
+    a.im = qsdf::split(v0.y);
+    psi[i] = lin2(c, a, parity64(i & p.yz) ? ns : s, rot_cdf(a, 1));
+    a.re = qsdf::split(v1.x);
+    a.im = qsdf::split(v1.y);
+    psi[i + stride] = lin2(c, a, parity64((i + stride) & p.yz) ? ns : s, rot_cdf(a, 1));
+  }
+  for (; i < p.nwork; i += stride) {
     const cdf a = load_split(psi + i);
     const df si = parity64(i & p.yz) ? ns : s;
     psi[i] = lin2(c, a, si, rot_cdf(a, 1));

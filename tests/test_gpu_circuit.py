@@ -85,3 +85,30 @@ def test_plan_validation(qs):
     st = qs.State(5)
     with pytest.raises(qs.QSError):
         circ.apply(st.handle)                    # qubit count differs
+
+
+def test_fused_c64_matches_per_gate_c128_at_22_qubits(qs):
+    """A size-independent property at a size beyond the oracle's comfort: the
+    cost-planned tensor-core complex64 result has 1 - F <= 1e-6 against the
+    per-gate complex128 result (itself oracle-checked at small sizes)."""
+    import torch
+    from paper_2311_01512_gb300 import costmodel
+    nq = 22
+    rng = wl.rng_for("fuse-22")
+    psi = wl.random_statevector(nq, rng)
+    ops = wl.unitary_circuit(nq, 300, rng)
+    ref, _ = run_plan(qs, nq, False, 1, psi, ops, qs.QS_PLAN_NONE, 1)
+    for plan in ("greedy", "cost"):
+        circ = qs.Circuit(nq, ops)
+        st = qs.State(nq, prec=0)
+        st.set_amps(psi.astype(np.complex64))
+        if plan == "greedy":
+            circ.plan(qs.QS_PLAN_GREEDY, 5)
+        else:
+            model, _ = costmodel.load()
+            circ.plan_cost(model, st.handle, max_block_qubits=5, window=24)
+        circ.apply(st.handle)
+        qs.qs_synchronize(st.handle)
+        got = st.get_amps().astype(np.complex128)
+        fid = abs(np.vdot(ref, got)) ** 2 / (np.vdot(ref, ref).real * np.vdot(got, got).real)
+        assert 1.0 - fid <= 1e-6, (plan, 1.0 - fid)
