@@ -176,7 +176,9 @@ qs_status gate_pass(qs_state* s, const std::vector<int>& ctrls, const std::vecto
   uint64_t fixed = cmask;
   for (int t : targs) fixed |= 1ull << t;
   const int nfree = s->ns - n - (int)ctrls.size();
-  if (s->prec == QS_C64 && s->tensor_cores && n >= 3 && n <= 5) {
+  const bool tc64 = s->prec == QS_C64 && s->tensor_cores && n >= 3 && n <= 5;
+  const bool tc128 = s->prec == QS_C128 && s->arith == QS_ARITH_DF && s->tensor_cores && n >= 3 && n <= 5;
+  if (tc64 || tc128) {
     // tensor-core tile: 128 groups, P = targets u the 7 lowest free qubits
     const int g = std::min(7, nfree);
     std::vector<int> P(targs);
@@ -205,7 +207,8 @@ qs_status gate_pass(qs_state* s, const std::vector<int>& ctrls, const std::vecto
     p.nhi = (int)hi.size();
     for (int i = 0; i < p.nhi; ++i) p.hi_ins[i] = (int8_t)hi[i];
     p.ntiles = 1ull << (s->ns - p.nhi);
-    return cuda_status(qsk::launch_dense_tc(s->amps, p, s->stream));
+    return cuda_status(tc64 ? qsk::launch_dense_tc(s->amps, p, s->stream)
+                            : qsk::launch_dense_ozaki(s->amps, p, s->stream));
   }
   // Dense tile: P = targets u the lowest free qubits, |P| = min(kTileBits, free + n).
   const int g = std::min(qsk::kTileBits - n, nfree) < 0 ? 0 : std::min(qsk::kTileBits - n, nfree);

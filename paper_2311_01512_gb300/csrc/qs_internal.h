@@ -187,6 +187,8 @@ cudaError_t launch_diag_df(void* amps, const DiagParams& p, cudaStream_t st);
 cudaError_t launch_gadget_df(void* amps, const GadgetDfParams& p, cudaStream_t st);
 // complex64 dense gates on the tensor cores, 3 <= n <= 5 (qs_tc.cu)
 cudaError_t launch_dense_tc(void* amps, const TcParams& p, cudaStream_t st);
+// complex128 dense gates on the bf16 tensor cores, exact integer slices, 3 <= n <= 5 (qs_tc_ozaki.cu)
+cudaError_t launch_dense_ozaki(void* amps, const TcParams& p, cudaStream_t st);
 cudaError_t launch_block_compose(const ComposeBlock* blocks, int nblocks, const ComposeInstr* instrs,
                                  const double* data, double* out, cudaStream_t st);
 // cost-model network (qs_mlp.cu)

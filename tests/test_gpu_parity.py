@@ -376,3 +376,39 @@ def test_tensor_core_gate_matches_cuda_cores(qs, nq, n, s):
     err_tc = float(np.max(np.abs(out[1] - want)))
     # 3xTF32 keeps FP32-level accuracy: within 2^-20 of the largest amplitude
     assert err_tc <= scale * 2.0 ** -20, (err_tc, err_cc, scale)
+
+
+# ---------------------------------------------------------------------------
+# complex128 dense gates on the bf16 tensor cores (exact integer slices)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("nq,n,s", [(5, 5, 0), (8, 3, 2), (10, 4, 1), (12, 5, 0), (13, 3, 0), (14, 4, 2)])
+@pytest.mark.parametrize("kind", ["haar", "wide", "sparse"])
+def test_complex128_tensor_core_gate(qs, nq, n, s, kind):
+    """Against the oracle and the CUDA-core double-float kernel.  'wide' uses a
+    non-unitary matrix whose entries span 1e-8..1e3 (row and column scaling),
+    'sparse' a state that is zero on most groups (all-zero tile rows)."""
+    rng = np.random.default_rng(900 + 31 * nq + 7 * n + s + len(kind))
+    qsel = [int(x) for x in rng.choice(nq, n + s, replace=False)]
+    targs, ctrls = qsel[:n], qsel[n:]
+    psi = wl.random_statevector(nq, rng)
+    mat = wl.haar_unitary(1 << n, rng)
+    if kind == "wide":
+        mat = mat * 10.0 ** rng.uniform(-8, 3, size=mat.shape)
+    if kind == "sparse":
+        psi = np.zeros_like(psi)
+        psi[rng.choice(psi.size, 5, replace=False)] = rng.standard_normal(5)
+    want = orc.apply_ctrl_multi_target(psi, ctrls, targs, mat)
+    outs = {}
+    for tc in (0, 1):
+        st = qs.State(nq, prec=1)
+        qs.qs_set_tensor_cores(st.handle, tc)
+        st.set_amps(psi)
+        qs.qs_apply_ctrl_multi_target(st.handle, ctrls, targs, mat)
+        qs.qs_synchronize(st.handle)
+        outs[tc] = st.get_amps()
+    # error bound of a dot product: a few 2^-46 of sum |m| |x| over its terms
+    bound = 2.0 ** -44 * (np.abs(mat).max() * (1 << n) * np.abs(psi).max()) + 1e-300
+    for tc in (0, 1):
+        err = float(np.max(np.abs(outs[tc] - want)))
+        assert err <= bound, (tc, err, bound)
