@@ -30,7 +30,7 @@ constexpr uint32_t kWaitLimit = 1u << 26;
 }  // namespace
 
 template <int NT>
-__global__ void __launch_bounds__(256, 1) k_dense_tc(float2* __restrict__ psi, const __grid_constant__ TcParams p) {
+__global__ void __launch_bounds__(256, 2) k_dense_tc(float2* __restrict__ psi, const __grid_constant__ TcParams p) {
   constexpr int D = 1 << NT;
   constexpr int K = 2 * D;                   // real inputs per group
   constexpr int N = 2 * D;                   // real outputs per group
@@ -126,19 +126,29 @@ __global__ void __launch_bounds__(256, 1) k_dense_tc(float2* __restrict__ psi, c
   for (uint64_t c = blockIdx.x; c < p.ntiles && !failed; c += gridDim.x) {
     const uint64_t base = insert_zeros(c, p.hi_ins, p.nhi) | p.ctrl_mask;
     // gather: tile element e (index order) -> row g (free slots), column l (target slots)
-    for (int e = tid; e < tile; e += blockDim.x) {
+    // every load of this thread first, then the shared-memory writes
+    constexpr int EPT = kRows * D / 256;
+    float2 vals[EPT];
+#pragma unroll
+    for (int r = 0; r < EPT; ++r) {
+      const int e = tid + r * 256;
+      if (e < tile) vals[r] = psi[base | sc_lo[e & ((1 << lo_bits) - 1)] | sc_hi[e >> lo_bits]];
+    }
+#pragma unroll
+    for (int r = 0; r < EPT; ++r) {
+      const int e = tid + r * 256;
+      if (e >= tile) continue;
       const int elo = e & ((1 << lo_bits) - 1), ehi = e >> lo_bits;
-      const uint64_t idx = base | sc_lo[elo] | sc_hi[ehi];
       const uint32_t gl = gl_lo[elo] | gl_hi[ehi];
       const int g = (int)(gl & 0xFFFFu), l = (int)(gl >> 16);
-      const float2 v = psi[idx];
+      const float2 v = vals[r];
       const float hx = tf32_hi(v.x), hy = tf32_hi(v.y);
       const uint32_t o0 = canon_off(g, 2 * l, K), o1 = canon_off(g, 2 * l + 1, K);
       *reinterpret_cast<float*>(a_hi + o0) = hx;
       *reinterpret_cast<float*>(a_hi + o1) = hy;
       *reinterpret_cast<float*>(a_lo + o0) = v.x - hx;
       *reinterpret_cast<float*>(a_lo + o1) = v.y - hy;
-      if (l == 0) row_base[g] = idx;
+      if (l == 0) row_base[g] = base | sc_lo[elo] | sc_hi[ehi];
     }
     fence_proxy_async();
     __syncthreads();

@@ -75,13 +75,16 @@ __device__ __forceinline__ long long level_int(float v) {
 
 }  // namespace
 
-template <int NT>
-__global__ void __launch_bounds__(256, 1) k_dense_ozaki(double2* __restrict__ psi, const __grid_constant__ TcParams p) {
+template <int NT, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) k_dense_ozaki(double2* __restrict__ psi, const __grid_constant__ TcParams p) {
   constexpr int D = 1 << NT;
   constexpr int K = 2 * D, N = 2 * D;
   constexpr int ABYTES = kOzRows * K * 2;     // one bf16 digit slice of A
   constexpr int BBYTES = N * K * 2;
-  constexpr int EPT = kOzRows * D / 256;      // tile elements per thread
+  constexpr int EPT = kOzRows * D / THREADS;  // tile elements per thread
+  constexpr int CGROUPS = THREADS / 128;      // warps sharing one lane quarter split the columns
+  constexpr int CPW = N / CGROUPS;            // accumulator columns per warp (a multiple of 8)
+  static_assert(CPW % 8 == 0, "column split");
   constexpr uint32_t TCOLS = (kOzSlices * N) <= 128 ? 128 : ((kOzSlices * N) <= 256 ? 256 : 512);
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* a_dig = smem;                                  // kOzSlices x ABYTES
@@ -180,36 +183,40 @@ __global__ void __launch_bounds__(256, 1) k_dense_ozaki(double2* __restrict__ ps
 
   for (uint64_t c = blockIdx.x; c < p.ntiles && !failed; c += gridDim.x) {
     const uint64_t base = insert_zeros(c, p.hi_ins, p.nhi) | p.ctrl_mask;
-    for (int g = tid; g < kOzRows; g += blockDim.x) row_exp[g] = 0;
+    for (int g = tid; g < kOzRows; g += THREADS) row_exp[g] = 0;
     __syncthreads();
-    // gather in index order; the row maxima of the exponents
+    // gather in index order: every load of this thread issued first, then the
+    // row maxima of the exponents
     uint32_t w[EPT][4];
-    uint32_t glv[EPT];
 #pragma unroll
     for (int r = 0; r < EPT; ++r) {
-      const int e = tid + r * 256;
-      glv[r] = 0xFFFFFFFFu;
+      const int e = tid + r * THREADS;
       if (e < tile) {
-        const int elo = e & ((1 << lo_bits) - 1), ehi = e >> lo_bits;
-        const uint64_t idx = base | sc_lo[elo] | sc_hi[ehi];
-        const uint32_t gl = gl_lo[elo] | gl_hi[ehi];
-        const double2 v = psi[idx];
+        const double2 v = psi[base | sc_lo[e & ((1 << lo_bits) - 1)] | sc_hi[e >> lo_bits]];
         w[r][0] = (uint32_t)__double2hiint(v.x);
         w[r][1] = (uint32_t)__double2loint(v.x);
         w[r][2] = (uint32_t)__double2hiint(v.y);
         w[r][3] = (uint32_t)__double2loint(v.y);
-        glv[r] = gl;
-        const int g = (int)(gl & 0xFFFFu);
-        atomicMax(row_exp + g, max((int)((w[r][0] >> 20) & 0x7FFu), (int)((w[r][2] >> 20) & 0x7FFu)));
-        if ((gl >> 16) == 0) row_base[g] = idx;
       }
+    }
+#pragma unroll
+    for (int r = 0; r < EPT; ++r) {
+      const int e = tid + r * THREADS;
+      if (e >= tile) continue;
+      const int elo = e & ((1 << lo_bits) - 1), ehi = e >> lo_bits;
+      const uint32_t gl = gl_lo[elo] | gl_hi[ehi];
+      const int g = (int)(gl & 0xFFFFu);
+      atomicMax(row_exp + g, max((int)((w[r][0] >> 20) & 0x7FFu), (int)((w[r][2] >> 20) & 0x7FFu)));
+      if ((gl >> 16) == 0) row_base[g] = base | sc_lo[elo] | sc_hi[ehi];
     }
     __syncthreads();
     // digit slices of A
 #pragma unroll
     for (int r = 0; r < EPT; ++r) {
-      if (glv[r] == 0xFFFFFFFFu) continue;
-      const int g = (int)(glv[r] & 0xFFFFu), l = (int)(glv[r] >> 16);
+      const int e = tid + r * THREADS;
+      if (e >= tile) continue;
+      const uint32_t gl = gl_lo[e & ((1 << lo_bits) - 1)] | gl_hi[e >> lo_bits];
+      const int g = (int)(gl & 0xFFFFu), l = (int)(gl >> 16);
       const int emax = row_exp[g];
       uint16_t dre[kOzSlices], dim[kOzSlices];
       digits7(w[r][0], w[r][1], emax, dre);
@@ -255,14 +262,14 @@ __global__ void __launch_bounds__(256, 1) k_dense_ozaki(double2* __restrict__ ps
       break;
     }
     fence_after_sync();
-    // epilogue: lanes 32 (w % 4) .. +31 are rows; warp half (w / 4) takes N/2 columns
+    // epilogue: lanes 32 (w % 4) .. +31 are rows; warp group (w / 4) takes CPW columns
     const int g = 32 * (warp & 3) + lane;
-    const int c0 = (warp >> 2) * (N / 2);
+    const int c0 = (warp >> 2) * CPW;
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     const int eg = row_exp[g];
     const uint64_t rb = row_base[g];
 #pragma unroll
-    for (int cc = 0; cc < N / 2; cc += 8) {
+    for (int cc = 0; cc < CPW; cc += 8) {
       float v[kOzSlices][8];
 #pragma unroll
       for (int L = 0; L < kOzSlices; ++L) tmem_ld8(lane_addr + (uint32_t)(L * N + c0 + cc), v[L]);
@@ -295,14 +302,15 @@ __global__ void __launch_bounds__(256, 1) k_dense_ozaki(double2* __restrict__ ps
   if (warp == 0) tmem_dealloc(tmem, TCOLS);
 }
 
-template <int NT>
+template <int NT, int THREADS>
 static cudaError_t dense_ozaki_nt(void* amps, const TcParams& p, cudaStream_t st) {
   constexpr int D = 1 << NT, K = 2 * D, N = 2 * D;
   const size_t smem = (size_t)kOzSlices * (kOzRows * K * 2 + N * K * 2) + 8 * (kOzRows + D + 160) + 4 * 160 +
                       4 * (kOzRows + N + 2) + 16 + 64;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_dense_ozaki<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_dense_ozaki<NT, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
@@ -312,15 +320,15 @@ static cudaError_t dense_ozaki_nt(void* amps, const TcParams& p, cudaStream_t st
   if (per_sm * tcols > 512) per_sm = 512 / tcols;
   const uint64_t maxb = (uint64_t)num_sms() * per_sm;
   const unsigned g = (unsigned)(p.ntiles < maxb ? p.ntiles : maxb);
-  k_dense_ozaki<NT><<<g, 256, smem, st>>>(static_cast<double2*>(amps), p);
+  k_dense_ozaki<NT, THREADS><<<g, THREADS, smem, st>>>(static_cast<double2*>(amps), p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dense_ozaki(void* amps, const TcParams& p, cudaStream_t st) {
   switch (p.n) {
-    case 3: return dense_ozaki_nt<3>(amps, p, st);
-    case 4: return dense_ozaki_nt<4>(amps, p, st);
-    case 5: return dense_ozaki_nt<5>(amps, p, st);
+    case 3: return dense_ozaki_nt<3, 256>(amps, p, st);
+    case 4: return dense_ozaki_nt<4, 512>(amps, p, st);
+    case 5: return dense_ozaki_nt<5, 512>(amps, p, st);
     default: return cudaErrorInvalidValue;
   }
 }
