@@ -543,3 +543,53 @@ def run_ops(state, ops, is_density):
         else:
             raise ValueError("unknown op " + kind)
     return s
+
+
+# --------------------------------------------------------------------------
+# Single-amplitude evaluation, for states too large to process whole: each
+# function returns the new amplitudes at the output indices `out_idx`, given
+# `get(indices)` that returns the OLD amplitudes at any indices.  Same
+# definitions as above, evaluated one output at a time.
+# --------------------------------------------------------------------------
+
+
+def sample_ctrl_multi_target(get, ctrls, targs, mat, out_idx):
+    """New amplitudes at out_idx after the many-control many-target gate
+    (Sec. "Many-target gate", Eq. (local many-target amplitude update); Sec.
+    "Many-control one-target gate", Eq. (control condition))."""
+    mat = np.asarray(mat, dtype=np.complex128)
+    n = len(targs)
+    cmask = get_bit_mask(ctrls)
+    tmask = get_bit_mask(targs)
+    out = np.empty(len(out_idx), dtype=np.complex128)
+    for o, i in enumerate(int(x) for x in out_idx):
+        if (i & cmask) != cmask:
+            out[o] = get(np.array([i]))[0]
+            continue
+        j = sum(get_bit(i, t) << q for q, t in enumerate(targs))
+        base = i & ~tmask
+        partners = np.array([set_bits(base, targs, l) for l in range(1 << n)], dtype=np.int64)
+        out[o] = np.dot(mat[j, :], get(partners))
+    return out
+
+
+def sample_diagonal(get, targs, diag, out_idx):
+    """New amplitudes at out_idx after the diagonal operator."""
+    diag = np.asarray(diag, dtype=np.complex128)
+    idx = np.asarray(out_idx, dtype=np.int64)
+    j = np.zeros_like(idx)
+    for q, t in enumerate(targs):
+        j |= ((idx >> t) & 1) << q
+    return diag[j] * get(idx)
+
+
+def sample_pauli_gadget(get, targs, paulis, theta, out_idx):
+    """New amplitudes at out_idx after exp(-i theta/2 P) (Sec. "Pauli
+    gadget")."""
+    phi = -0.5 * theta
+    xy, yz, num_y = _pauli_masks(targs, paulis)
+    eta = 1j ** num_y
+    idx = np.asarray(out_idx, dtype=np.int64)
+    ip = idx ^ xy
+    beta = np.where(_v_parity(ip & yz) == 1, -eta, eta)
+    return np.cos(phi) * get(idx) + 1j * np.sin(phi) * beta * get(ip)

@@ -436,3 +436,23 @@ def test_random_noisy_circuit_keeps_trace_and_hermiticity():
     assert abs(np.trace(rho) - 1.0) < 1e-12
     np.testing.assert_allclose(rho, rho.conj().T, atol=1e-13)
     assert np.min(np.linalg.eigvalsh(rho)) > -1e-12
+
+
+def test_single_amplitude_oracle_matches_whole_state():
+    rng = np.random.default_rng(321)
+    nq = 9
+    psi = wl.random_statevector(nq, rng)
+    get = lambda idx: psi[np.asarray(idx)]
+    out_idx = rng.choice(1 << nq, 40, replace=False)
+    for n, s in ((1, 0), (2, 2), (4, 1), (5, 0)):
+        qsel = [int(x) for x in rng.choice(nq, n + s, replace=False)]
+        mat = rng.standard_normal((1 << n, 1 << n)) + 1j * rng.standard_normal((1 << n, 1 << n))
+        want = orc.apply_ctrl_multi_target(psi, qsel[n:], qsel[:n], mat)[out_idx]
+        got = orc.sample_ctrl_multi_target(get, qsel[n:], qsel[:n], mat, out_idx)
+        np.testing.assert_allclose(got, want, atol=1e-13)
+    d = np.exp(1j * rng.uniform(0, 6, 8))
+    np.testing.assert_allclose(orc.sample_diagonal(get, [3, 0, 7], d, out_idx),
+                               orc.apply_diagonal(psi, [3, 0, 7], d)[out_idx], atol=1e-15)
+    targs, paulis = wl.random_pauli_string(nq, 1, nq, rng)
+    np.testing.assert_allclose(orc.sample_pauli_gadget(get, targs, paulis, 0.9, out_idx),
+                               orc.apply_pauli_gadget(psi, targs, paulis, 0.9)[out_idx], atol=1e-15)
