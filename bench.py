@@ -348,13 +348,18 @@ def main_ours(args):
         pinned.copy_(fresh)
         del fresh
         h2d = 16 * (1 << nq) + sum(op_h2d_bytes(op) for op in ops)
-        e_ms = []
+        e_ms, up_ms = [], []
+        e_clocks = ClockSampler(local)
         for k in range(1 + args.steps):            # one untimed warm-up step
             e0 = torch.cuda.Event(enable_timing=True)
+            eu = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            if k == 1:
+                e_clocks.start()
             barrier(world)
             e0.record(stream)
             qs.qs_set_amps_ptr(h, pinned.data_ptr(), 0, 1 << nq)
+            eu.record(stream)
             for op in ops:
                 qs.apply_op(h, op)
             out_norm = qs.qs_calc_norm_or_trace(h)      # device -> host read; synchronises
@@ -362,9 +367,13 @@ def main_ours(args):
             e1.synchronize()
             if k > 0:
                 e_ms.append(e0.elapsed_time(e1))
+                up_ms.append(e0.elapsed_time(eu))
+        e_clk = e_clocks.stop()
         e_total = max_over_ranks(sum(e_ms), world, device)
         e2e = {"value": world * NUM_OPS * args.steps / (e_total * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16,
+               "upload_ms_per_step": sum(up_ms) / len(up_ms), "ms_per_step": sum(e_ms) / len(e_ms),
+               "clocks": e_clk,
                "note": "pinned host state uploaded through qs_set_amps, %d ops, norm read back" % NUM_OPS,
                "final_norm": out_norm.real}
 

@@ -177,11 +177,22 @@ qs_status gate_pass(qs_state* s, const std::vector<int>& ctrls, const std::vecto
   for (int t : targs) fixed |= 1ull << t;
   const int nfree = s->ns - n - (int)ctrls.size();
   const bool tc64 = s->prec == QS_C64 && s->tensor_cores && n >= 3 && n <= 5;
-  const bool tc128 = s->prec == QS_C128 && s->arith == QS_ARITH_DF && s->tensor_cores && n >= 3 && n <= 5;
+  // complex128: two targets run on the three-target kernel with an identity on
+  // the lowest free qubit
+  const bool tc128 = s->prec == QS_C128 && s->arith == QS_ARITH_DF && s->tensor_cores && n <= 5 &&
+                     (n >= 3 || (n == 2 && nfree >= 1));
   if (tc64 || tc128) {
-    // tensor-core tile: 128 groups, P = targets u the 7 lowest free qubits
-    const int g = std::min(7, nfree);
-    std::vector<int> P(targs);
+    std::vector<int> kt(targs);
+    if (n == 2) {
+      int f = 0;
+      while (fixed >> f & 1) ++f;
+      kt.push_back(f);
+      fixed |= 1ull << f;
+    }
+    const int nk = (int)kt.size();
+    // tensor-core tile: 128 groups, P = kernel targets u the 7 lowest free qubits
+    const int g = std::min(7, s->ns - nk - (int)ctrls.size());
+    std::vector<int> P(kt);
     for (int q = 0, added = 0; q < s->ns && added < g; ++q)
       if (!(fixed >> q & 1)) {
         P.push_back(q);
@@ -192,14 +203,15 @@ qs_status gate_pass(qs_state* s, const std::vector<int>& ctrls, const std::vecto
     p.mat = static_cast<const double*>(dev_mat);
     p.err = s->d_err;
     p.ctrl_mask = cmask;
-    p.n = n;
+    p.n = nk;
+    p.nmat = n;
     p.conj = conj;
     p.tile_bits = (int)P.size();
     for (int b = 0; b < p.tile_bits; ++b) p.P[b] = (int8_t)P[b];
-    for (int q = 0; q < n; ++q) {
-      p.tslot[q] = (int8_t)(std::find(P.begin(), P.end(), targs[q]) - P.begin());
+    for (int q = 0; q < nk; ++q) {
+      p.tslot[q] = (int8_t)(std::find(P.begin(), P.end(), kt[q]) - P.begin());
       p.tslot_mask |= 1u << p.tslot[q];
-      p.tpos[q] = (int8_t)targs[q];
+      p.tpos[q] = (int8_t)kt[q];
     }
     std::vector<int> hi(P);
     hi.insert(hi.end(), ctrls.begin(), ctrls.end());

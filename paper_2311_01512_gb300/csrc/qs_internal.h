@@ -70,7 +70,8 @@ struct TcParams {
   int* err;              // device error word: set to 1 when a bounded wait runs out
   uint64_t ctrl_mask;
   uint64_t ntiles;
-  int n;
+  int n;                 // targets of the kernel
+  int nmat;              // targets of the stored matrix (< n: identity on targets nmat..n-1)
   int conj;
   int tile_bits;
   int nhi;
@@ -187,7 +188,7 @@ cudaError_t launch_diag_df(void* amps, const DiagParams& p, cudaStream_t st);
 cudaError_t launch_gadget_df(void* amps, const GadgetDfParams& p, cudaStream_t st);
 // complex64 dense gates on the tensor cores, 3 <= n <= 5 (qs_tc.cu)
 cudaError_t launch_dense_tc(void* amps, const TcParams& p, cudaStream_t st);
-// complex128 dense gates on the bf16 tensor cores, exact integer slices, 3 <= n <= 5 (qs_tc_ozaki.cu)
+// complex128 dense gates on the bf16 tensor cores, exact integer slices, 3 <= n <= 5 kernel targets (qs_tc_ozaki.cu)
 cudaError_t launch_dense_ozaki(void* amps, const TcParams& p, cudaStream_t st);
 cudaError_t launch_block_compose(const ComposeBlock* blocks, int nblocks, const ComposeInstr* instrs,
                                  const double* data, double* out, cudaStream_t st);

@@ -1,0 +1,87 @@
+// Integer slicing of FP64 operands for exact products on the bf16 tensor cores
+// (the Ozaki scheme: Ozaki, Ogita, Oishi and Rump, "Error-free transformations
+// of matrix multiplication by using fast routines of matrix multiplication and
+// its applications", Numer. Algorithms 59 (2012)).
+//
+// A double x in a row (or column) whose largest biased exponent is emax becomes
+// the integer V = x 2^(48 - Emax) rounded (|V| <= 2^49, Emax = emax - 1023),
+// written as seven balanced digits
+//   V = sum_{s=0..6} d_s 2^(42 - 7 s),   |d_0| <= 128,  -64 <= d_s <= 63 (s >= 1).
+// The digits come from one 64-bit addition: with C = 64 sum_{s=1..6} 2^(42-7s),
+// the unsigned 7-bit fields of W = V + C at bits 42 - 7s are d_s + 64 and the
+// arithmetic top part W >> 42 is d_0.  Every digit is exact in bf16.
+//
+// Slice products: for K <= 64 terms, sum_k a_s b_t is an integer below 2^20 in
+// magnitude, and a level L = s + t (at most 7 pairs) stays below 2^22
+// (2 * 64 * 128 * 64 + 5 * 64 * 64 * 64 at L = 6), so FP32 accumulation is
+// exact and adding 1.5 * 2^23 puts the level's integer in the low significand
+// bits.  The levels L = 0..6 are recombined modulo 2^64 from those bit
+// patterns; the true value fits in 63 bits, so the wrap-around is exact.
+//
+// Host and device code (the host build is checked on the CPU).
+#pragma once
+
+#include <cstdint>
+
+#include "qs_df.cuh"
+
+namespace qsoz {
+
+constexpr int kSlices = 7;
+
+// C = 64 sum_{s=1..6} 2^(42-7s)
+constexpr uint64_t kBal =
+    64ull * ((1ull << 35) + (1ull << 28) + (1ull << 21) + (1ull << 14) + (1ull << 7) + 1ull);
+
+// 0x4B400000 = bits of 1.5 * 2^23; the level offsets summed over the weights
+// 2^(7(6-L)), modulo 2^64.
+constexpr uint64_t kLevelOffset =
+    0x4B400000ull * ((1ull << 42) + (1ull << 35) + (1ull << 28) + (1ull << 21) + (1ull << 14) + (1ull << 7) + 1ull);
+
+QS_HD int biased_exp(uint32_t hw) { return (int)((hw >> 20) & 0x7FFu); }
+
+// W = V + C for the double with words (hw, lw); emax >= its biased exponent.
+// V is rounded half up (toward +infinity), so the rounding error does not
+// depend on the sign of x.  Zeros and subnormals give V = 0.
+QS_HD uint64_t fixed_w(uint32_t hw, uint32_t lw, int emax) {
+  const int eb = biased_exp(hw);
+  int sh = emax - eb + 3;                         // leaves one bit below the units
+  sh = sh > 63 ? 63 : sh;
+  const uint64_t m = eb ? ((((uint64_t)(hw & 0xFFFFFu) | 0x100000u) << 32) | lw) : 0ull;
+  const uint64_t smask = (uint64_t)(int64_t)((int32_t)hw >> 31);
+  const int64_t ms = (int64_t)((m ^ smask) - smask);      // signed significand
+  const int64_t t = ms >> sh;                              // floor(2 x 2^(48 - Emax))
+  return (uint64_t)((t + (int64_t)(2 * kBal + 1)) >> 1);   // floor(x 2^(48 - Emax) + 1/2) + C
+}
+
+// Balanced digit s of W (integer form, for checks).
+QS_HD int digit(uint64_t w, int s) {
+  if (s == 0) return (int)((int64_t)w >> 42);
+  return (int)((w >> (42 - 7 * s)) & 127u) - 64;
+}
+
+// The seven digits of W as floats (exact small integers).
+QS_HD void digit_floats(uint64_t w, float* f) {
+  const uint32_t lo = (uint32_t)w, hi = (uint32_t)(w >> 32);
+  const uint32_t d0 = (uint32_t)((int32_t)hi >> 10);
+  f[0] = qsdf::u2f(0x4B400000u + d0) - 12582912.0f;
+  f[1] = qsdf::u2f(0x4B400000u | ((hi >> 3) & 127u)) - 12582976.0f;
+  f[2] = qsdf::u2f(0x4B400000u | ((uint32_t)(w >> 28) & 127u)) - 12582976.0f;
+  f[3] = qsdf::u2f(0x4B400000u | ((lo >> 21) & 127u)) - 12582976.0f;
+  f[4] = qsdf::u2f(0x4B400000u | ((lo >> 14) & 127u)) - 12582976.0f;
+  f[5] = qsdf::u2f(0x4B400000u | ((lo >> 7) & 127u)) - 12582976.0f;
+  f[6] = qsdf::u2f(0x4B400000u | (lo & 127u)) - 12582976.0f;
+}
+
+// sum_L level_L 2^(7(6-L)) from the bit patterns b_L of (level_L + 1.5 * 2^23).
+QS_HD int64_t combine_levels(const uint32_t* b) {
+  uint64_t acc = (uint64_t)b[6] - kLevelOffset;
+  acc += (uint64_t)b[5] * 128u;
+  acc += (uint64_t)b[4] * 16384u;
+  acc += (uint64_t)b[3] * 2097152u;
+  acc += (uint64_t)b[2] * 268435456u;
+  acc += (uint64_t)(b[1] * 8u + b[0] * 1024u) << 32;
+  return (int64_t)acc;
+}
+
+}  // namespace qsoz

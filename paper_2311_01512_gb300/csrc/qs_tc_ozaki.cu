@@ -1,26 +1,35 @@
-// Dense n-target gates (3 <= n <= 5) for complex128 states on the bf16 tensor
-// cores, with error-free integer slicing (the Ozaki scheme: Ozaki, Ogita,
-// Oishi and Rump, "Error-free transformations of matrix multiplication by
-// using fast routines of matrix multiplication and its applications", Numer.
-// Algorithms 59 (2012)).
+// Dense n-target gates (2 <= n <= 5) for complex128 states on the bf16 tensor
+// cores, with error-free integer slicing (the Ozaki scheme; the slicing and
+// its bounds are in qs_slices.cuh).
 //
 // The group update alpha_kj -> sum_l m_jl alpha_kl (Sec. "Many-target gate",
 // Eq. (local many-target amplitude update)) over a tile of 128 groups is the
-// real GEMM C = A B of k_dense_tc (A: interleaved re/im amplitudes, B: the
-// realified matrix).  Every row of A and every column of B is scaled by a
-// power of two so that its largest entry lies in [2^48, 2^49], rounded to an
-// integer, and cut into seven balanced signed digits (|d_0| <= 129, others
-// |d| <= 64):
-//   a = 2^(Ea - 6) sum_s a_s 2^(-7 s),   b = 2^(Eb - 6) sum_t b_t 2^(-7 t).
-// Digits are exact in bf16; a product of two digit slices summed over
-// K <= 64 terms is an integer of at most 2^20, and the sum of the (s, t) slice
-// products of one level L = s + t (at most 7 of them) stays below 2^22, so the
-// FP32 accumulation in tensor memory is exact.  Levels L = 0..6 are kept (49
-// bits; dropped levels are below 2^-48 of the largest term); the epilogue
-// recombines them exactly in 64-bit integers, converts once to double and
-// applies the row and column scales.  The digits come straight from the FP64
-// bit patterns with integer operations (no FP64 arithmetic).
+// real GEMM C = A B, A[g, 2l + c'] the interleaved (re, im) amplitudes of group
+// g, B the realified matrix (B[2l, 2j] = Re m_jl, B[2l+1, 2j] = -Im m_jl,
+// B[2l, 2j+1] = Im m_jl, B[2l+1, 2j+1] = Re m_jl).  Each row of A (scaled by
+// its largest exponent) and each column of B is cut into seven balanced bf16
+// digit slices; the 28 slice products with s + t <= 6 run as tcgen05
+// kind::f16 MMAs whose FP32 accumulation in tensor memory is exact, one
+// accumulator per level L = s + t; the epilogue recombines the levels in
+// 64-bit integers, converts once to double and applies the two scales.  Two
+// targets run as three: the matrix is extended by an identity on one more
+// (free) qubit, which changes nothing in the result and fills the MMA's K = 16.
+//
+// Work mapping: thread (warp w, lane) owns row g = 32 (w mod 4) + lane (the
+// tensor-memory lane that warp may read) and the amplitudes l in
+// [c EPT, (c+1) EPT), c = w / 4, of that row, for the gather, the slicing and
+// the epilogue alike, so the row's exponent and base index stay in registers.
+// Pipeline per CTA (persistent, tiles c, c + grid, ...): the loads of the
+// next tile are issued right after the current tile's slices are written, and
+// with two buffers of slices and accumulators the epilogue of tile i - 1 runs
+// while the tensor cores work on tile i; the row maxima of tile i + 1 are
+// taken after that epilogue, so a tile costs two CTA barriers.  The MMAs are
+// issued by one thread in each of warps 0..3, which take the levels {6},
+// {5, 0}, {4, 1}, {3, 2}: seven slice products each.  Every wait is bounded:
+// on timeout the kernel records an error code, frees its tensor memory and
+// returns.
 #include "qs_device.cuh"
+#include "qs_slices.cuh"
 #include "qs_tc_ptx.cuh"
 
 namespace qsk {
@@ -28,143 +37,139 @@ namespace {
 
 using namespace tcptx;
 
-constexpr int kOzRows = 128;
-constexpr int kOzSlices = 7;
-constexpr uint32_t kOzWaitLimit = 1u << 26;
+constexpr int kRows = 128;
+constexpr int kS = qsoz::kSlices;
+constexpr uint32_t kWaitLimit = 1u << 26;
 
-// Seven bf16 digits of the double with words (hw, lw) relative to the biased
-// exponent emax of its row (or column) maximum: V = |x| 2^(48 - Emax) rounded
-// to nearest (V <= 2^49), written as V = sum_s d_s 2^(42 - 7s) with balanced
-// digits d_1..d_6 in [-64, 63] and d_0 in [0, 129], all multiplied by the
-// sign of x.  Balanced digits make the dropped low-order levels symmetric in
-// sign, so the truncation carries no bias toward zero.
-__device__ __forceinline__ void digits7(uint32_t hw, uint32_t lw, int emax, uint16_t* out) {
-  const int eb = (int)((hw >> 20) & 0x7FFu);
-  const uint64_t m = ((uint64_t)((hw & 0xFFFFFu) | 0x100000u) << 32) | lw;   // 53-bit significand
-  const int shift = emax - eb + 4;                                            // >= 4
-  uint64_t v = 0;
-  if (eb != 0 && shift < 64) v = (m + (1ull << (shift - 1))) >> shift;
-  const uint32_t vh = (uint32_t)(v >> 32), vl = (uint32_t)v;
-  int d[kOzSlices];
-  int carry = 0;
-#pragma unroll
-  for (int s = kOzSlices - 1; s >= 1; --s) {
-    const int pos = 42 - 7 * s;
-    const int u = (int)((pos >= 32 ? (vh >> (pos - 32)) : __funnelshift_r(vl, vh, pos)) & 127u) + carry;
-    carry = u >= 64 ? 1 : 0;
-    d[s] = u - (carry << 7);
-  }
-  d[0] = (int)(vh >> 10) + carry;
-  const uint32_t sign = hw & 0x80000000u;
-#pragma unroll
-  for (int s = 0; s < kOzSlices; ++s) {
-    const float f = __int_as_float(0x4B400000 + d[s]) - 12582912.0f;   // exact for |d| < 2^22
-    out[s] = (uint16_t)((__float_as_uint(f) ^ sign) >> 16);            // bf16 = top half (|d| <= 129)
-  }
+__host__ __device__ constexpr uint32_t tmem_cols(uint32_t n) {
+  return n <= 32 ? 32 : (n <= 64 ? 64 : (n <= 128 ? 128 : (n <= 256 ? 256 : 512)));
 }
 
-__device__ __forceinline__ int biased_exp(double x) { return (int)(((uint32_t)__double2hiint(x) >> 20) & 0x7FFu); }
+// two floats holding small integers -> packed bf16 pair (lo in bits 0..15); exact
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
 
-// Exact integer value of a level sum (a float holding an integer).  With
-// |d_0| <= 129 and |d_s| <= 64 every level is below 2^22 for K <= 64
-// (level 0: 64 * 129^2; level L >= 1: 2 * 64 * 129 * 64 + (L - 1) * 64 * 64^2),
-// where adding 1.5 * 2^23 exposes the integer in the significand bits.
-__device__ __forceinline__ long long level_int(float v) {
-  return (long long)(__float_as_int(v + 12582912.0f) - 0x4B400000);
+// seven packed (re, im) digit pairs of one amplitude (words of re and im)
+__device__ __forceinline__ void slice_amp(const uint32_t* w, int emax, uint32_t* out) {
+  float fr[kS], fi[kS];
+  qsoz::digit_floats(qsoz::fixed_w(w[0], w[1], emax), fr);
+  qsoz::digit_floats(qsoz::fixed_w(w[2], w[3], emax), fi);
+#pragma unroll
+  for (int s = 0; s < kS; ++s) out[s] = pack_bf16(fr[s], fi[s]);
+}
+
+// bounded wait on an mbarrier phase; true when it ran out
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity) {
+  uint32_t spins = 0;
+  while (!mbar_try_wait(bar, parity))
+    if (++spins > kWaitLimit) return true;
+  return false;
+}
+
+// entry (k, n) of the realified (and possibly identity-extended) matrix
+__device__ __forceinline__ double realified(const TcParams& p, int D, int k, int n) {
+  int j = n >> 1, l = k >> 1;
+  const int c = n & 1, cp = k & 1;
+  if (p.nmat < p.n) {
+    if ((j >> p.nmat) != (l >> p.nmat)) return 0.0;
+    const int mm = (1 << p.nmat) - 1;
+    j &= mm;
+    l &= mm;
+    D = 1 << p.nmat;
+  }
+  const double mr = p.mat[2 * (j * D + l)];
+  const double mi = p.conj ? -p.mat[2 * (j * D + l) + 1] : p.mat[2 * (j * D + l) + 1];
+  return c == 0 ? (cp == 0 ? mr : -mi) : (cp == 0 ? mi : mr);
+}
+
+// The MMAs of level L (slice pairs s + t = L) into the accumulator at d_tmem.
+// adesc / bdesc: descriptors of slice 0 of A and B; slices are abytes /
+// bbytes apart, 16-column K chunks 256 bytes apart (encoded address >> 4).
+template <int L, int KCH>
+__device__ __forceinline__ void mma_level(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t abytes, uint32_t bbytes) {
+#pragma unroll
+  for (int s = 0; s <= L; ++s)
+#pragma unroll
+    for (int kk = 0; kk < KCH; ++kk)
+      mma_bf16(d_tmem, adesc + ((s * abytes + kk * 256) >> 4), bdesc + (((L - s) * bbytes + kk * 256) >> 4), idesc,
+               (s | kk) != 0);
 }
 
 }  // namespace
 
-template <int NT, int THREADS>
+template <int NT, int THREADS, int NBUF>
 __global__ void __launch_bounds__(THREADS, 1) k_dense_ozaki(double2* __restrict__ psi, const __grid_constant__ TcParams p) {
   constexpr int D = 1 << NT;
   constexpr int K = 2 * D, N = 2 * D;
-  constexpr int ABYTES = kOzRows * K * 2;     // one bf16 digit slice of A
+  constexpr int CG = THREADS / kRows;         // threads per row
+  constexpr int EPT = D / CG;                 // amplitudes per thread
+  constexpr int CPW = 2 * EPT;                // accumulator columns per thread
+  static_assert(EPT % 4 == 0, "four amplitudes per 16-byte slice store");
+  constexpr int ABYTES = kRows * K * 2;       // one bf16 digit slice of A
   constexpr int BBYTES = N * K * 2;
-  constexpr int EPT = kOzRows * D / THREADS;  // tile elements per thread
-  constexpr int CGROUPS = THREADS / 128;      // warps sharing one lane quarter split the columns
-  constexpr int CPW = N / CGROUPS;            // accumulator columns per warp (a multiple of 8)
-  static_assert(CPW % 8 == 0, "column split");
-  constexpr uint32_t TCOLS = (kOzSlices * N) <= 128 ? 128 : ((kOzSlices * N) <= 256 ? 256 : 512);
+  constexpr uint32_t LCOLS = kS * N;          // accumulator columns of one buffer
+  constexpr uint32_t TCOLS = tmem_cols(NBUF * LCOLS);
+  static_assert(NBUF * LCOLS <= 512, "tensor memory");
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* a_dig = smem;                                  // kOzSlices x ABYTES
-  unsigned char* b_dig = a_dig + kOzSlices * ABYTES;            // kOzSlices x BBYTES
-  uint64_t* row_base = reinterpret_cast<uint64_t*>(b_dig + kOzSlices * BBYTES);  // 128
-  uint64_t* toff = row_base + kOzRows;                          // D
-  uint64_t* sc_lo = toff + D;                                   // 32
-  uint64_t* sc_hi = sc_lo + 32;                                 // 128
-  uint32_t* gl_lo = reinterpret_cast<uint32_t*>(sc_hi + 128);   // 32
-  uint32_t* gl_hi = gl_lo + 32;                                 // 128
-  int* row_exp = reinterpret_cast<int*>(gl_hi + 128);           // 128
-  int* col_exp = row_exp + kOzRows;                             // N
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(col_exp + N + (N & 1));
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  unsigned char* a_dig = smem;                                        // NBUF x kS x ABYTES
+  unsigned char* b_dig = a_dig + NBUF * kS * ABYTES;                  // kS x BBYTES
+  uint64_t* toff = reinterpret_cast<uint64_t*>(b_dig + kS * BBYTES);  // D
+  uint64_t* rowoff = toff + D;                                        // kRows
+  uint64_t* tile_base = rowoff + kRows;                               // 2
+  uint64_t* mbar = tile_base + 2;                                     // 2
+  int* csc = reinterpret_cast<int*>(mbar + 2);                        // N: column exponent - 2100
+  int* rowexp = csc + N;                                              // 2 x kRows (tile parity)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(rowexp + 2 * kRows);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // B: realified matrix, column maxima, digit slices (once per CTA)
-  for (int n = tid; n < N; n += blockDim.x) {
+  // B: column maxima of the exponents, then the digit slices (once per CTA)
+  for (int n = tid; n < N; n += THREADS) {
     int e = 0;
-    for (int k = 0; k < K; ++k) {
-      const int j = n >> 1, c = n & 1, l = k >> 1, cp = k & 1;
-      const double mr = p.mat[2 * (j * D + l)];
-      const double mi = p.conj ? -p.mat[2 * (j * D + l) + 1] : p.mat[2 * (j * D + l) + 1];
-      const double v = (c == 0) ? (cp == 0 ? mr : -mi) : (cp == 0 ? mi : mr);
-      e = max(e, biased_exp(v));
-    }
-    col_exp[n] = e;
+    for (int k = 0; k < K; ++k) e = max(e, qsoz::biased_exp((uint32_t)__double2hiint(realified(p, D, k, n))));
+    csc[n] = e;
   }
   __syncthreads();
-  for (int idx = tid; idx < N * K; idx += blockDim.x) {
+  for (int idx = tid; idx < N * K; idx += THREADS) {
     const int n = idx / K, k = idx % K;
-    const int j = n >> 1, c = n & 1, l = k >> 1, cp = k & 1;
-    const double mr = p.mat[2 * (j * D + l)];
-    const double mi = p.conj ? -p.mat[2 * (j * D + l) + 1] : p.mat[2 * (j * D + l) + 1];
-    const double v = (c == 0) ? (cp == 0 ? mr : -mi) : (cp == 0 ? mi : mr);
-    uint16_t d[kOzSlices];
-    digits7((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v), col_exp[n], d);
+    const double v = realified(p, D, k, n);
+    float f[kS];
+    qsoz::digit_floats(qsoz::fixed_w((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v), csc[n]), f);
     const uint32_t off = canon_off16(n, k, K);
 #pragma unroll
-    for (int s = 0; s < kOzSlices; ++s) *reinterpret_cast<uint16_t*>(b_dig + s * BBYTES + off) = d[s];
+    for (int s = 0; s < kS; ++s)
+      *reinterpret_cast<uint16_t*>(b_dig + s * BBYTES + off) = (uint16_t)(pack_bf16(f[s], 0.0f) & 0xFFFFu);
   }
-  for (int j = tid; j < D; j += blockDim.x) {
+  for (int j = tid; j < D; j += THREADS) {
     uint64_t off = 0;
 #pragma unroll
     for (int q = 0; q < NT; ++q)
       if ((j >> q) & 1) off |= 1ull << p.tpos[q];
     toff[j] = off;
   }
-  const int lo_bits = p.tile_bits < 5 ? p.tile_bits : 5;
-  int lo_free = 0;
-  for (int b = 0; b < lo_bits; ++b)
-    if (!((p.tslot_mask >> b) & 1)) ++lo_free;
-  for (int t = tid; t < 32 + 128; t += blockDim.x) {
-    const bool lo = t < 32;
-    const int v = lo ? t : t - 32;
-    const int b0 = lo ? 0 : lo_bits, b1 = lo ? lo_bits : p.tile_bits;
-    uint64_t sc = 0;
-    uint32_t g = 0, l = 0;
-    int gb = lo ? 0 : lo_free;
-    for (int b = b0; b < b1; ++b) {
-      const uint32_t bit = (uint32_t)(v >> (b - b0)) & 1u;
-      sc |= (uint64_t)bit << p.P[b];
-      if ((p.tslot_mask >> b) & 1) {
-        for (int q = 0; q < NT; ++q)
-          if (p.tslot[q] == b) l |= bit << q;
-      } else {
-        g |= bit << gb;
-        ++gb;
+  const int row_bits = p.tile_bits - NT;
+  for (int g = tid; g < kRows; g += THREADS) {
+    uint64_t off = 0;
+    for (int b = 0, r = 0; b < p.tile_bits; ++b)
+      if (!((p.tslot_mask >> b) & 1)) {
+        if ((g >> r) & 1) off |= 1ull << p.P[b];
+        ++r;
       }
-    }
-    if (lo) {
-      sc_lo[v] = sc;
-      gl_lo[v] = g | (l << 16);
-    } else {
-      sc_hi[v] = sc;
-      gl_hi[v] = g | (l << 16);
-    }
+    rowoff[g] = off;
+    rowexp[g] = 0;
+    rowexp[kRows + g] = 0;
   }
-  if (tid == 0) mbar_init(mbar, 1);
+  __syncthreads();
+  for (int n = tid; n < N; n += THREADS) csc[n] -= 2046 + 54;   // scale 2^(Ea + Eb - 54) with biased Ea, Eb
+  if (tid == 0) {
+    tile_base[0] = insert_zeros(blockIdx.x, p.hi_ins, p.nhi) | p.ctrl_mask;
+#pragma unroll
+    for (int b = 0; b < NBUF; ++b) mbar_init(mbar + b, 4);      // one commit from each MMA-issuing thread
+  }
   if (warp == 0) {
     tmem_alloc(tmem_slot, TCOLS);
     tmem_relinquish();
@@ -174,161 +179,192 @@ __global__ void __launch_bounds__(THREADS, 1) k_dense_ozaki(double2* __restrict_
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t idesc = idesc_bf16(kOzRows, N);
-  const uint32_t sbo = K * 16;
-  uint32_t phase = 0;
-  bool failed = false;
-  const int tile = 1 << p.tile_bits;
-  const int rows = tile >> NT;
+  const uint32_t idesc = idesc_bf16(kRows, N);
+  constexpr uint32_t sbo = K * 16;
 
-  for (uint64_t c = blockIdx.x; c < p.ntiles && !failed; c += gridDim.x) {
-    const uint64_t base = insert_zeros(c, p.hi_ins, p.nhi) | p.ctrl_mask;
-    for (int g = tid; g < kOzRows; g += THREADS) row_exp[g] = 0;
-    __syncthreads();
-    // gather in index order: every load of this thread issued first, then the
-    // row maxima of the exponents
-    uint32_t w[EPT][4];
+  const int g = 32 * (warp & 3) + lane;       // row (tensor-memory lane)
+  const int cg = warp >> 2;                   // amplitude / column group of the row
+  const int l0 = cg * EPT;
+  const bool row_ok = g < (1 << row_bits);
+  const uint64_t roff = rowoff[g];
+  const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+  const bool issuer = lane == 0 && warp < 4;
+  const int helper = THREADS > kRows ? kRows : 0;   // computes tile bases (not an MMA issuer)
+  // target offsets of this thread's amplitudes: registers when few
+  constexpr bool kRegOff = EPT <= 4;
+  uint64_t toffr[kRegOff ? EPT : 1];
+  if (kRegOff) {
 #pragma unroll
-    for (int r = 0; r < EPT; ++r) {
-      const int e = tid + r * THREADS;
-      if (e < tile) {
-        const double2 v = psi[base | sc_lo[e & ((1 << lo_bits) - 1)] | sc_hi[e >> lo_bits]];
-        w[r][0] = (uint32_t)__double2hiint(v.x);
-        w[r][1] = (uint32_t)__double2loint(v.x);
-        w[r][2] = (uint32_t)__double2hiint(v.y);
-        w[r][3] = (uint32_t)__double2loint(v.y);
+    for (int i = 0; i < (kRegOff ? EPT : 1); ++i) toffr[i] = toff[l0 + i];
+  }
+  auto tofs = [&](int i) -> uint64_t { return kRegOff ? toffr[kRegOff ? i : 0] : toff[l0 + i]; };
+
+  uint32_t R[EPT][4];
+  auto load_tile = [&](uint64_t base) {
+    const uint64_t rb = base | roff;
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      double2 v = make_double2(0.0, 0.0);
+      if (row_ok) v = psi[rb | tofs(i)];
+      R[i][0] = (uint32_t)__double2hiint(v.x);
+      R[i][1] = (uint32_t)__double2loint(v.x);
+      R[i][2] = (uint32_t)__double2hiint(v.y);
+      R[i][3] = (uint32_t)__double2loint(v.y);
+    }
+  };
+  // row maximum of the exponents (the CG threads of a row are in different warps)
+  auto row_max = [&](int slot) {
+    int em = 0;
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) em = max(em, max(qsoz::biased_exp(R[i][0]), qsoz::biased_exp(R[i][2])));
+    atomicMax(rowexp + slot * kRows + g, em);
+  };
+
+  // epilogue of one tile: levels -> exact integers -> doubles -> scatter
+  auto epilogue = [&](uint32_t tbuf, int eg, uint64_t rb) {
+#pragma unroll
+    for (int cc = 0; cc < CPW; cc += 8) {
+      float v[kS][8];
+#pragma unroll
+      for (int L = 0; L < kS; ++L) tmem_ld8(tmem + tbuf + lane_addr + (uint32_t)(L * N + cg * CPW + cc), v[L]);
+      tmem_wait_ld();
+      if (row_ok) {
+        const int4 s0 = *reinterpret_cast<const int4*>(csc + cg * CPW + cc);
+        const int4 s1 = *reinterpret_cast<const int4*>(csc + cg * CPW + cc + 4);
+        const int scl[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+        double o[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          uint32_t bits[kS];
+#pragma unroll
+          for (int L = 0; L < kS; ++L) bits[L] = __float_as_uint(v[L][q] + 12582912.0f);
+          const long long acc = qsoz::combine_levels(bits);
+          const double r = __ll2double_rn(acc);
+          const int hi = __double2hiint(r) + (int)((unsigned)(eg + scl[q]) << 20);
+          o[q] = acc != 0 ? __hiloint2double(hi, __double2loint(r)) : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) psi[rb | tofs((cc + q) >> 1)] = make_double2(o[q], o[q + 1]);
       }
     }
+  };
+
+  // prologue: the first tile's amplitudes and row maxima, the second tile's base
+  load_tile(tile_base[0]);
+  row_max(0);
+  if (tid == helper && blockIdx.x + gridDim.x < p.ntiles)
+    tile_base[1] = insert_zeros(blockIdx.x + gridDim.x, p.hi_ins, p.nhi) | p.ctrl_mask;
+  __syncthreads();
+
+  uint32_t phases = 0;
+  bool failed = false;
+  int it = 0;
+  int eg_prev = 0;
+  uint64_t rb_prev = 0;
+  for (uint64_t c = blockIdx.x; c < p.ntiles; c += gridDim.x, ++it) {
+    const int b = NBUF == 2 ? (it & 1) : 0;
+    const int par = it & 1;                   // tile parity: row-maximum and base slots
+    const uint64_t rb = tile_base[par] | roff;
+    const bool has_next = c + gridDim.x < p.ntiles;
+    const int eg = rowexp[par * kRows + g];
+    // digit slices of this thread's amplitudes, 16 bytes per slice and 4 amplitudes
+    unsigned char* A = a_dig + b * (kS * ABYTES);
 #pragma unroll
-    for (int r = 0; r < EPT; ++r) {
-      const int e = tid + r * THREADS;
-      if (e >= tile) continue;
-      const int elo = e & ((1 << lo_bits) - 1), ehi = e >> lo_bits;
-      const uint32_t gl = gl_lo[elo] | gl_hi[ehi];
-      const int g = (int)(gl & 0xFFFFu);
-      atomicMax(row_exp + g, max((int)((w[r][0] >> 20) & 0x7FFu), (int)((w[r][2] >> 20) & 0x7FFu)));
-      if ((gl >> 16) == 0) row_base[g] = base | sc_lo[elo] | sc_hi[ehi];
-    }
-    __syncthreads();
-    // digit slices of A
+    for (int i = 0; i < EPT; i += 4) {
+      uint32_t pk[4][kS];
 #pragma unroll
-    for (int r = 0; r < EPT; ++r) {
-      const int e = tid + r * THREADS;
-      if (e >= tile) continue;
-      const uint32_t gl = gl_lo[e & ((1 << lo_bits) - 1)] | gl_hi[e >> lo_bits];
-      const int g = (int)(gl & 0xFFFFu), l = (int)(gl >> 16);
-      const int emax = row_exp[g];
-      uint16_t dre[kOzSlices], dim[kOzSlices];
-      digits7(w[r][0], w[r][1], emax, dre);
-      digits7(w[r][2], w[r][3], emax, dim);
-      const uint32_t off = canon_off16(g, 2 * l, K);     // 2l and 2l + 1 share one 4-byte word
+      for (int e = 0; e < 4; ++e) slice_amp(R[i + e], eg, pk[e]);
+      const uint32_t off = canon_off16(g, 2 * (l0 + i), K);
 #pragma unroll
-      for (int s = 0; s < kOzSlices; ++s)
-        *reinterpret_cast<uint32_t*>(a_dig + s * ABYTES + off) = (uint32_t)dre[s] | ((uint32_t)dim[s] << 16);
+      for (int s = 0; s < kS; ++s)
+        *reinterpret_cast<uint4*>(A + s * ABYTES + off) = make_uint4(pk[0][s], pk[1][s], pk[2][s], pk[3][s]);
     }
     fence_proxy_async();
     __syncthreads();
-    if (tid == 0) {
+    if (issuer) {
       fence_after_sync();
-      const uint32_t sa = smem_u32(a_dig), sb = smem_u32(b_dig);
-#pragma unroll
-      for (int L = 0; L < kOzSlices; ++L) {
-        const uint32_t d_tmem = tmem + (uint32_t)(L * N);
-        uint32_t acc = 0;
-        for (int s = 0; s <= L; ++s) {
-          const int t = L - s;
-#pragma unroll
-          for (int kk = 0; kk < K / 16; ++kk) {
-            mma_bf16(d_tmem, smem_desc(sa + s * ABYTES + kk * 256, 128, sbo),
-                     smem_desc(sb + t * BBYTES + kk * 256, 128, sbo), idesc, acc);
-            acc = 1;
-          }
-        }
+      const uint64_t ad = smem_desc(smem_u32(A), 128, sbo), bd = smem_desc(smem_u32(b_dig), 128, sbo);
+      const uint32_t d = tmem + (uint32_t)(b * LCOLS);
+      constexpr int KCH = K / 16;
+      if (warp == 0) {
+        mma_level<6, KCH>(d + 6 * N, ad, bd, idesc, ABYTES, BBYTES);
+      } else if (warp == 1) {
+        mma_level<5, KCH>(d + 5 * N, ad, bd, idesc, ABYTES, BBYTES);
+        mma_level<0, KCH>(d, ad, bd, idesc, ABYTES, BBYTES);
+      } else if (warp == 2) {
+        mma_level<4, KCH>(d + 4 * N, ad, bd, idesc, ABYTES, BBYTES);
+        mma_level<1, KCH>(d + N, ad, bd, idesc, ABYTES, BBYTES);
+      } else {
+        mma_level<3, KCH>(d + 3 * N, ad, bd, idesc, ABYTES, BBYTES);
+        mma_level<2, KCH>(d + 2 * N, ad, bd, idesc, ABYTES, BBYTES);
       }
-      mma_commit(mbar);
+      mma_commit(mbar + b);
     }
-    uint32_t spins = 0;
+    if (cg == 0) rowexp[par * kRows + g] = 0;   // read by every thread of the row before the barrier
+    // loads of the next tile, in flight during the MMAs and the epilogue
+    if (has_next) load_tile(tile_base[par ^ 1]);
     bool timed_out = false;
-    while (!mbar_try_wait(mbar, phase)) {
-      if (++spins > kOzWaitLimit) {
-        timed_out = true;
-        break;
+    if (NBUF == 2) {
+      if (it > 0) {
+        const int pb = b ^ 1;
+        timed_out = wait_phase(mbar + pb, (phases >> pb) & 1u);
+        phases ^= 1u << pb;
+        fence_after_sync();
+        epilogue((uint32_t)(pb * LCOLS), eg_prev, rb_prev);
       }
+    } else {
+      timed_out = wait_phase(mbar, phases & 1u);
+      phases ^= 1u;
+      fence_after_sync();
+      epilogue(0u, eg, rb);
     }
-    phase ^= 1;
-    failed = __syncthreads_or(timed_out) != 0;
-    if (failed) {
-      if (tid == 0) atomicExch(p.err, 1);
-      break;
-    }
-    fence_after_sync();
-    // epilogue: lanes 32 (w % 4) .. +31 are rows; warp group (w / 4) takes CPW columns
-    const int g = 32 * (warp & 3) + lane;
-    const int c0 = (warp >> 2) * CPW;
-    const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-    const int eg = row_exp[g];
-    const uint64_t rb = row_base[g];
-#pragma unroll
-    for (int cc = 0; cc < CPW; cc += 8) {
-      float v[kOzSlices][8];
-#pragma unroll
-      for (int L = 0; L < kOzSlices; ++L) tmem_ld8(lane_addr + (uint32_t)(L * N + c0 + cc), v[L]);
-      tmem_wait_ld();
-      if (g < rows) {
-        double outv[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          long long acc = level_int(v[0][q]);
-#pragma unroll
-          for (int L = 1; L < kOzSlices; ++L) acc = acc * 128 + level_int(v[L][q]);
-          double r = __ll2double_rn(acc);
-          // scale 2^(Ea + Eb - 54), Ea, Eb unbiased row / column maximum exponents
-          const int scale = eg + col_exp[c0 + cc + q] - 2046 - 54;
-          if (acc != 0) r = __hiloint2double(__double2hiint(r) + (int)((unsigned)scale << 20), __double2loint(r));
-          outv[q] = r;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; q += 2) {
-          const int j = (c0 + cc + q) >> 1;
-          psi[rb | toff[j]] = make_double2(outv[q], outv[q + 1]);
-        }
-      }
-    }
+    eg_prev = eg;
+    rb_prev = rb;
+    if (has_next) row_max(par ^ 1);
+    if (tid == helper && c + 2 * (uint64_t)gridDim.x < p.ntiles)
+      tile_base[par] = insert_zeros(c + 2 * (uint64_t)gridDim.x, p.hi_ins, p.nhi) | p.ctrl_mask;
     fence_before_sync();
-    __syncthreads();
+    failed = __syncthreads_or(timed_out) != 0;
     fence_after_sync();
+    if (failed) break;
   }
+  if (NBUF == 2 && !failed && it > 0) {
+    const int pb = (it - 1) & 1;
+    const bool timed_out = wait_phase(mbar + pb, (phases >> pb) & 1u);
+    fence_after_sync();
+    epilogue((uint32_t)(pb * LCOLS), eg_prev, rb_prev);
+    fence_before_sync();
+    failed = __syncthreads_or(timed_out) != 0;
+  }
+  if (failed && tid == 0) atomicExch(p.err, 1);
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, TCOLS);
 }
 
-template <int NT, int THREADS>
+template <int NT, int THREADS, int NBUF, int CTAS>
 static cudaError_t dense_ozaki_nt(void* amps, const TcParams& p, cudaStream_t st) {
   constexpr int D = 1 << NT, K = 2 * D, N = 2 * D;
-  const size_t smem = (size_t)kOzSlices * (kOzRows * K * 2 + N * K * 2) + 8 * (kOzRows + D + 160) + 4 * 160 +
-                      4 * (kOzRows + N + 2) + 16 + 64;
+  constexpr size_t smem = (size_t)NBUF * kS * (kRows * K * 2) + (size_t)kS * (N * K * 2) + 8 * (D + kRows + 4) +
+                          4 * (N + 2 * kRows) + 16;
+  static_assert(smem <= 227 * 1024, "shared memory");
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_dense_ozaki<NT, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_dense_ozaki<NT, THREADS, NBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  constexpr int tcols = (kOzSlices * N) <= 128 ? 128 : ((kOzSlices * N) <= 256 ? 256 : 512);
-  int per_sm = (int)((200 * 1024) / smem);
-  per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
-  if (per_sm * tcols > 512) per_sm = 512 / tcols;
-  const uint64_t maxb = (uint64_t)num_sms() * per_sm;
+  const uint64_t maxb = (uint64_t)num_sms() * CTAS;
   const unsigned g = (unsigned)(p.ntiles < maxb ? p.ntiles : maxb);
-  k_dense_ozaki<NT, THREADS><<<g, THREADS, smem, st>>>(static_cast<double2*>(amps), p);
+  k_dense_ozaki<NT, THREADS, NBUF><<<g, THREADS, smem, st>>>(static_cast<double2*>(amps), p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dense_ozaki(void* amps, const TcParams& p, cudaStream_t st) {
   switch (p.n) {
-    case 3: return dense_ozaki_nt<3, 256>(amps, p, st);
-    case 4: return dense_ozaki_nt<4, 512>(amps, p, st);
-    case 5: return dense_ozaki_nt<5, 512>(amps, p, st);
+    case 3: return dense_ozaki_nt<3, 256, 2, 2>(amps, p, st);
+    case 4: return dense_ozaki_nt<4, 512, 2, 1>(amps, p, st);
+    case 5: return dense_ozaki_nt<5, 512, 1, 1>(amps, p, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1,0 +1,165 @@
+// Host check of the integer slicing used by the complex128 tensor-core kernel
+// (qs_slices.cuh): digits reconstruct the rounded fixed-point value exactly,
+// stay within their bounds and are exact in bf16; slice-product levels stay
+// exact in FP32; the level recombination is exact; a full dot product of K
+// terms stays within (K + 1) 2^-47 of the row-max x column-max scale.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <random>
+
+#include "qs_slices.cuh"
+
+static int failures = 0;
+#define CHECK(cond, ...)                   \
+  do {                                     \
+    if (!(cond)) {                         \
+      if (failures < 20) {                 \
+        std::printf("FAIL: " __VA_ARGS__); \
+        std::printf("\n");                 \
+      }                                    \
+      ++failures;                          \
+    }                                      \
+  } while (0)
+
+static void words(double x, uint32_t& hw, uint32_t& lw) {
+  uint64_t u;
+  std::memcpy(&u, &x, 8);
+  hw = (uint32_t)(u >> 32);
+  lw = (uint32_t)u;
+}
+
+static int bexp(double x) {
+  uint32_t hw, lw;
+  words(x, hw, lw);
+  return qsoz::biased_exp(hw);
+}
+
+// x 2^(48 - Emax) rounded half up, from long double arithmetic (exact here:
+// the scaled value has at most 53 significant bits).
+static long long ref_fixed(double x, int emax) {
+  const long double y = std::ldexp((long double)x, 48 - (emax - 1023));
+  return (long long)std::floor(y + 0.5L);
+}
+
+int main() {
+  std::mt19937_64 rng(2311015120ULL);
+  std::uniform_real_distribution<double> u(-1.0, 1.0);
+  std::uniform_int_distribution<int> ex(-60, 10);
+  std::uniform_int_distribution<int> gap(0, 70);
+
+  // 1. digits: exact reconstruction, bounds, float form exact in bf16
+  for (int it = 0; it < 3000000; ++it) {
+    double x = std::ldexp(u(rng), ex(rng));
+    if (it % 97 == 0) x = 0.0;
+    if (it % 101 == 0) x = -0.0;
+    int emax = (x == 0.0 ? 1000 : bexp(x)) + (it % 3 == 0 ? 0 : gap(rng) % (it % 5 == 0 ? 70 : 4));
+    if (it % 7 == 0) emax = bexp(x) > 0 ? bexp(x) : 1;  // value at the row maximum
+    uint32_t hw, lw;
+    words(x, hw, lw);
+    const uint64_t w = qsoz::fixed_w(hw, lw, emax);
+    long long v = 0;
+    for (int s = 0; s < qsoz::kSlices; ++s) {
+      const int d = qsoz::digit(w, s);
+      if (s == 0)
+        CHECK(d >= -128 && d <= 128, "d0 = %d", d);
+      else
+        CHECK(d >= -64 && d <= 63, "d%d = %d", s, d);
+      v += (long long)d * (1ll << (42 - 7 * s));
+    }
+    const long long ref = ref_fixed(x, emax);
+    CHECK(v == ref, "x = %.17g emax = %d: V = %lld, expected %lld", x, emax, v, ref);
+    float f[qsoz::kSlices];
+    qsoz::digit_floats(w, f);
+    for (int s = 0; s < qsoz::kSlices; ++s) {
+      CHECK(f[s] == (float)qsoz::digit(w, s), "float digit %d", s);
+      CHECK((qsdf::f2u(f[s]) & 0xFFFFu) == 0u, "digit %d not exact in bf16", s);
+    }
+  }
+
+  // 2. level sums of extreme digits stay below 2^22 and accumulate exactly in FP32
+  for (int it = 0; it < 20000; ++it) {
+    const int K = 64;
+    int a[qsoz::kSlices][64], b[qsoz::kSlices][64];
+    for (int s = 0; s < qsoz::kSlices; ++s)
+      for (int k = 0; k < K; ++k) {
+        const int mag = s == 0 ? 128 : 64;
+        const bool sgn = it < 4 ? ((it >> (s == 0)) & 1) : (rng() & 1);
+        a[s][k] = sgn ? -mag : (s == 0 ? mag : 63);
+        b[s][k] = (it < 4 ? (it & 1) : (rng() & 1)) ? -mag : (s == 0 ? mag : 63);
+      }
+    for (int L = 0; L < qsoz::kSlices; ++L) {
+      long long exact = 0;
+      float acc = 0.0f;
+      for (int s = 0; s <= L; ++s)
+        for (int k = 0; k < K; ++k) {
+          const long long p = (long long)a[s][k] * b[L - s][k];
+          exact += p;
+          acc += (float)p;
+        }
+      CHECK(std::llabs(exact) < (1ll << 22), "level %d = %lld", L, exact);
+      CHECK((long long)acc == exact, "level %d not exact in FP32", L);
+    }
+  }
+
+  // 3. recombination of the level bit patterns
+  // (level 0 is below 2^20: K * 128 * 128 with K <= 64)
+  std::uniform_int_distribution<int> lev(-(1 << 22) + 1, (1 << 22) - 1);
+  std::uniform_int_distribution<int> lev0(-(1 << 20), 1 << 20);
+  for (int it = 0; it < 2000000; ++it) {
+    uint32_t bits[qsoz::kSlices];
+    __int128 ref = 0;
+    for (int L = 0; L < qsoz::kSlices; ++L) {
+      const int top = L == 0 ? (1 << 20) : (1 << 22) - 1;
+      const int v = it < 3 ? (it == 0 ? top : (it == 1 ? -top : 0)) : (L == 0 ? lev0(rng) : lev(rng));
+      bits[L] = qsdf::f2u((float)v + 12582912.0f);
+      ref += (__int128)v * ((__int128)1 << (7 * (6 - L)));
+    }
+    const long long got = qsoz::combine_levels(bits);
+    CHECK((__int128)got == ref, "combine %lld", got);
+  }
+
+  // 4. full complex dot products through digits, levels and recombination
+  std::normal_distribution<double> gauss(0.0, 1.0);
+  double worst = 0.0;
+  for (int it = 0; it < 20000; ++it) {
+    const int K = 2 << (it % 5 + 1);  // 4 .. 64
+    double a[64], b[64];
+    const int spread = it % 4 == 0 ? 40 : 3;
+    std::uniform_int_distribution<int> es(-spread, 0);
+    for (int k = 0; k < K; ++k) {
+      a[k] = std::ldexp(gauss(rng), es(rng) - 15);
+      b[k] = std::ldexp(gauss(rng), es(rng));
+    }
+    int ea = 0, eb = 0;
+    for (int k = 0; k < K; ++k) {
+      ea = std::max(ea, bexp(a[k]));
+      eb = std::max(eb, bexp(b[k]));
+    }
+    long long lv[qsoz::kSlices] = {0, 0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < K; ++k) {
+      uint32_t h1, l1, h2, l2;
+      words(a[k], h1, l1);
+      words(b[k], h2, l2);
+      const uint64_t wa = qsoz::fixed_w(h1, l1, ea), wb = qsoz::fixed_w(h2, l2, eb);
+      for (int s = 0; s < qsoz::kSlices; ++s)
+        for (int t = 0; s + t < qsoz::kSlices; ++t) lv[s + t] += (long long)qsoz::digit(wa, s) * qsoz::digit(wb, t);
+    }
+    uint32_t bits[qsoz::kSlices];
+    for (int L = 0; L < qsoz::kSlices; ++L) bits[L] = qsdf::f2u((float)lv[L] + 12582912.0f);
+    const long long acc = qsoz::combine_levels(bits);
+    const long double got = std::ldexp((long double)acc, (ea - 1023) + (eb - 1023) - 54);
+    long double exact = 0;
+    for (int k = 0; k < K; ++k) exact += (long double)a[k] * b[k];
+    const long double scale = std::ldexp(1.0L, (ea - 1023) + (eb - 1023) + 1);
+    const double rel = (double)(std::fabs(got - exact) / scale);
+    worst = std::max(worst, rel);
+    // each term carries at most 2^-47 of the scale (two operand roundings of
+    // 2^-49 relative to the maxima), and the dropped levels add below 2^-47
+    CHECK(rel < (K + 1) * std::ldexp(1.0, -47), "dot product error %.3g of the scale (K = %d)", rel, K);
+  }
+  std::printf("worst dot-product error / (row max * column max) = %.3g (2^%.1f)\n", worst, std::log2(worst));
+
+  std::printf("ok (%d failures)\n", failures);
+  return failures ? 1 : 0;
+}

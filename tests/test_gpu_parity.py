@@ -382,14 +382,22 @@ def test_tensor_core_gate_matches_cuda_cores(qs, nq, n, s):
 # complex128 dense gates on the bf16 tensor cores (exact integer slices)
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("nq,n,s", [(5, 5, 0), (8, 3, 2), (10, 4, 1), (12, 5, 0), (13, 3, 0), (14, 4, 2)])
+@pytest.mark.parametrize("nq,n,s", [(5, 5, 0), (8, 3, 2), (10, 4, 1), (12, 5, 0), (13, 3, 0), (14, 4, 2),
+                                     (3, 2, 0), (4, 2, 1), (9, 2, 3), (13, 2, 0), (16, 5, 1), (17, 3, 1)])
 @pytest.mark.parametrize("kind", ["haar", "wide", "sparse"])
-def test_complex128_tensor_core_gate(qs, nq, n, s, kind):
+@pytest.mark.parametrize("place", ["random", "lowest", "highest"])
+def test_complex128_tensor_core_gate(qs, nq, n, s, kind, place):
     """Against the oracle and the CUDA-core double-float kernel.  'wide' uses a
     non-unitary matrix whose entries span 1e-8..1e3 (row and column scaling),
-    'sparse' a state that is zero on most groups (all-zero tile rows)."""
-    rng = np.random.default_rng(900 + 31 * nq + 7 * n + s + len(kind))
+    'sparse' a state that is zero on most groups (all-zero tile rows).  Two
+    targets run on the three-target kernel with an identity on a free qubit;
+    (3, 2, 0) and (4, 2, 1) leave a single free qubit, so the tile has one row."""
+    rng = np.random.default_rng(900 + 31 * nq + 7 * n + s + len(kind) + 3 * len(place))
     qsel = [int(x) for x in rng.choice(nq, n + s, replace=False)]
+    if place == "lowest":
+        qsel = list(range(n + s))
+    elif place == "highest":
+        qsel = list(range(nq - 1, nq - 1 - n - s, -1))
     targs, ctrls = qsel[:n], qsel[n:]
     psi = wl.random_statevector(nq, rng)
     mat = wl.haar_unitary(1 << n, rng)
