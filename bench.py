@@ -49,6 +49,8 @@ def parse_args(argv=None):
                     help="sixteenths of one-target-gate work done in native FP64 beside double-float")
     ap.add_argument("--no-fused", action="store_true", help="skip the fused tensor-core comparison")
     ap.add_argument("--fused-qubits", type=int, default=30)
+    ap.add_argument("--fused-prec", choices=("c64", "c128"), default="c64",
+                    help="precision of the fused form: complex64 (3xTF32 blocks) or complex128 (bf16 integer slices)")
     ap.add_argument("--detail", default="", help="write per-kernel-family statistics to this JSON file")
     ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args(argv)
@@ -255,11 +257,7 @@ def load_traffic(family):
     try:
         rec = json.load(open(path))
         from paper_2311_01512_gb300 import build as b
-        import hashlib
-        h = hashlib.sha256()
-        for src in b.SOURCES:
-            h.update(open(os.path.join(b.CSRC, src), "rb").read())
-        if rec.get("sources_sha256") != h.hexdigest():
+        if rec.get("sources_sha256") != b.sources_digest():
             return None
         return rec.get("families", {}).get(family)
     except Exception:
@@ -437,18 +435,19 @@ def fused_comparison(args, device):
     """The 1000-gate unitary circuit of the fused workload (1q Haar; 1-2-target
     Haar with 0-3 controls; gadgets of weight 1-6) on one random state: the
     plain per-gate form (complex128, native FP64 and double-float) against
-    cost-model-planned fused blocks on the tensor cores (complex64, 3xTF32).
-    Reports times, speedup, max |delta amp| and 1 - fidelity of the fused
-    result against the per-gate complex128 result."""
+    cost-model-planned fused blocks on the tensor cores (complex64 with 3xTF32
+    blocks, or complex128 with bf16 integer-slice blocks).  Reports times,
+    speedup, max |delta amp| and 1 - fidelity of the fused result against the
+    per-gate complex128 result.  States are regenerated from their seed instead
+    of kept as copies, and the comparison runs in slices, so that the 32-qubit
+    case needs three state-sized buffers at most."""
     import torch
     from paper_2311_01512_gb300 import costmodel, qs
     from paper_2311_01512_gb300 import workloads as wl
     nq = args.fused_qubits
+    c64 = args.fused_prec == "c64"
     ops = wl.unitary_circuit(nq, FUSED_OPS, wl.rng_for("fused-tc-circuit"))
     stream = torch.cuda.Stream(device=device)
-    with torch.cuda.stream(stream):
-        psi0 = device_random_state(nq, device)
-    stream.synchronize()
 
     def timed(fn):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -459,62 +458,71 @@ def fused_comparison(args, device):
         e1.synchronize()
         return e0.elapsed_time(e1)
 
-    out = {"qubits": nq, "ops": FUSED_OPS}
-
-    def reset(dst, src):
-        # copies on the circuit's stream, so that they are ordered with its kernels
+    def reset(dst):
+        # the seeded initial state, written on the circuit's stream
         with torch.cuda.stream(stream):
+            src = device_random_state(nq, device)
             dst.copy_(src)
+            del src
         stream.synchronize()
 
+    out = {"qubits": nq, "ops": FUSED_OPS, "fused_amp": "complex64" if c64 else "complex128"}
     # per-gate complex128, native FP64 and double-float
     with torch.cuda.stream(stream):
-        t128 = psi0.clone()
-        t64 = psi0.to(torch.complex64)
+        t128 = device_random_state(nq, device)
     stream.synchronize()
     st = qs.State(nq, prec=qs.QS_C128, stream=stream, storage=t128)
     circ = qs.Circuit(nq, ops)
     circ.plan(qs.QS_PLAN_NONE, 1)
     qs.qs_set_arithmetic(st.handle, qs.QS_ARITH_F64)
     out["per_gate_f64_ms"] = timed(lambda: circ.apply(st.handle))
-    reset(t128, psi0)
+    reset(t128)
     qs.qs_set_arithmetic(st.handle, qs.QS_ARITH_DF)
     out["per_gate_df_ms"] = timed(lambda: circ.apply(st.handle))
-    # fused complex64 on the tensor cores, planned by the learned cost model
-    st64 = qs.State(nq, prec=qs.QS_C64, stream=stream, storage=t64)
+    # fused form, planned by the learned cost model
+    with torch.cuda.stream(stream):
+        src = device_random_state(nq, device)
+        tf = src.to(torch.complex64) if c64 else src
+        del src
+    stream.synchronize()
+    sf = qs.State(nq, prec=qs.QS_C64 if c64 else qs.QS_C128, stream=stream, storage=tf)
     model, meta = costmodel.load()
-    circ64 = qs.Circuit(nq, ops)
-    plan = circ64.plan_cost(model, st64.handle, max_block_qubits=5, window=24)
-    out["fused_ms"] = timed(lambda: circ64.apply(st64.handle))
+    circf = qs.Circuit(nq, ops)
+    plan = circf.plan_cost(model, sf.handle, max_block_qubits=5, window=24)
+    out["fused_ms"] = timed(lambda: circf.apply(sf.handle))
     out["plan"] = plan
     out["costmodel_holdout_median_time_error"] = meta.get("holdout_median_abs_rel_time_error")
-    # unfused complex64 for reference
-    reset(t64, psi0)
-    circ64n = qs.Circuit(nq, ops)
-    circ64n.plan(qs.QS_PLAN_NONE, 1)
-    out["per_gate_c64_ms"] = timed(lambda: circ64n.apply(st64.handle))
-    reset(t64, psi0)
-    circ64.apply(st64.handle)
+    # unfused, same precision as the fused form
+    reset(tf)
+    circn = qs.Circuit(nq, ops)
+    circn.plan(qs.QS_PLAN_NONE, 1)
+    out["per_gate_same_prec_ms"] = timed(lambda: circn.apply(sf.handle))
+    reset(tf)
+    circf.apply(sf.handle)
     stream.synchronize()
+    # max |delta amp| and fidelity, in slices of 2^26 amplitudes
+    dmax, ov, na, nb = 0.0, 0.0 + 0.0j, 0.0, 0.0
+    step = 1 << min(26, nq)
     with torch.cuda.stream(stream):
-        a = t128
-        b = t64.to(torch.complex128)
-        dmax = (a - b).abs().max()
-        ov = torch.vdot(a, b)
-        fid_t = ov.abs() ** 2 / (torch.vdot(a, a).real * torch.vdot(b, b).real)
+        for i in range(0, 1 << nq, step):
+            a = t128[i:i + step]
+            b = tf[i:i + step].to(torch.complex128)
+            dmax = max(dmax, float((a - b).abs().max().item()))
+            ov += complex(torch.vdot(a, b).item())
+            na += float(torch.vdot(a, a).real.item())
+            nb += float(torch.vdot(b, b).real.item())
     stream.synchronize()
-    out["max_abs_delta_amp"] = float(dmax.item())
-    fid = float(fid_t.item())
-    out["one_minus_fidelity"] = 1.0 - fid
+    out["max_abs_delta_amp"] = dmax
+    out["one_minus_fidelity"] = 1.0 - abs(ov) ** 2 / (na * nb)
     out["reference"] = "per-gate complex128 double-float result (oracle-checked at small sizes)"
     out["speedup_vs_per_gate_f64"] = out["per_gate_f64_ms"] / out["fused_ms"]
     out["speedup_vs_per_gate_df"] = out["per_gate_df_ms"] / out["fused_ms"]
-    for h in (st, st64):
+    for h in (st, sf):
         h.close()
-    for c in (circ, circ64, circ64n):
+    for c in (circ, circf, circn):
         c.close()
     model.close()
-    del t128, t64, psi0
+    del t128, tf
     torch.cuda.empty_cache()
     return out
 

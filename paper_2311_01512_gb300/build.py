@@ -21,6 +21,19 @@ SOURCES = ["qs_gates.cu", "qs_gates_df.cu", "qs_tc.cu", "qs_tc_ozaki.cu", "qs_de
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
+def sources_digest():
+    """SHA-256 over every kernel source and header (sorted by name): the key
+    that ties a recorded ncu measurement to the code it measured."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(CSRC)):
+        if name.endswith((".cu", ".cuh", ".cpp", ".h")):
+            h.update(name.encode())
+            with open(os.path.join(CSRC, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
 def _nvcc():
     cand = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
     if os.path.exists(cand):

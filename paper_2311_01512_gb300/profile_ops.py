@@ -5,18 +5,68 @@ bf16 tensor cores), and a 5-target dense gate on a complex64 state (tf32
 tensor cores), each repeated.
 
     python -m paper_2311_01512_gb300.profile_ops --qubits 28 --reps 3
+
+With --traffic-csv it instead turns an ncu CSV of dram__bytes_read.sum and
+dram__bytes_write.sum over one repetition of that sequence into DRAM bytes
+per launch, scaled to a full pass over --scale-to qubits (traffic grows with
+the amplitudes processed), keyed by the bench's kernel families and stamped
+with the kernel sources' digest:
+
+    python -m paper_2311_01512_gb300.profile_ops --qubits 28 --traffic-csv traffic28.csv \
+        --scale-to 30 --out profiles/dram_traffic.json
 """
 
 import argparse
+import csv
+import json
 
 import numpy as np
+
+# launch order of one repetition -> the bench's kernel family names
+_FAMILIES = {"k_gate1_df": ["k_gate1"], "k_diag_df": ["k_diag"], "k_gadget_df": ["k_gadget"],
+             "k_dense_ozaki<3": ["k_dense<2>", "k_dense<3>"], "k_dense_ozaki<4": ["k_dense<4>"],
+             "k_dense_ozaki<5": ["k_dense<5>"], "k_dense_tc<5>": ["c64 k_dense<5>"]}
+
+
+def summarize_traffic(path, qubits, scale_to, out):
+    from . import build
+    rows = list(csv.reader(open(path)))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    hdr = rows[hi]
+    ki, mi, vi, ii = hdr.index("Kernel Name"), hdr.index("Metric Name"), hdr.index("Metric Value"), hdr.index("ID")
+    launches = {}
+    for r in rows[hi + 1:]:
+        if len(r) <= vi:
+            continue
+        d = launches.setdefault(r[ii], {"name": r[ki].split("(")[0].replace("void ", "").replace("qsk::", "")})
+        d[r[mi]] = float(r[vi].replace(",", ""))
+    scale = 2.0 ** (scale_to - qubits)
+    fam, pending = {}, {k: list(v) for k, v in _FAMILIES.items()}
+    for d in launches.values():
+        for prefix, names in pending.items():
+            if d["name"].startswith(prefix) and names:
+                b = d.get("dram__bytes_read.sum", 0.0) + d.get("dram__bytes_write.sum", 0.0)
+                fam[names.pop(0)] = b * scale
+                break
+    rec = {"sources_sha256": build.sources_digest(), "measured_qubits": qubits, "scaled_to_qubits": scale_to,
+           "unit": "bytes per full-pass launch (dram__bytes_read.sum + dram__bytes_write.sum)",
+           "families": fam}
+    with open(out, "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec, indent=1))
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--qubits", type=int, default=28)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--traffic-csv")
+    ap.add_argument("--scale-to", type=int, default=30)
+    ap.add_argument("--out", default="profiles/dram_traffic.json")
     args = ap.parse_args(argv)
+    if args.traffic_csv:
+        summarize_traffic(args.traffic_csv, args.qubits, args.scale_to, args.out)
+        return
     import torch
     from . import qs
     from . import workloads as wl
