@@ -176,11 +176,11 @@ qs_status gate_pass(qs_state* s, const std::vector<int>& ctrls, const std::vecto
   uint64_t fixed = cmask;
   for (int t : targs) fixed |= 1ull << t;
   const int nfree = s->ns - n - (int)ctrls.size();
-  const bool tc64 = s->prec == QS_C64 && s->tensor_cores && n >= 3 && n <= 5;
-  // complex128: two targets run on the three-target kernel with an identity on
-  // the lowest free qubit
-  const bool tc128 = s->prec == QS_C128 && s->arith == QS_ARITH_DF && s->tensor_cores && n <= 5 &&
-                     (n >= 3 || (n == 2 && nfree >= 1));
+  // two targets run on the three-target tensor-core kernels with an identity
+  // on the lowest free qubit
+  const bool tc_n = n <= 5 && (n >= 3 || (n == 2 && nfree >= 1));
+  const bool tc64 = s->prec == QS_C64 && s->tensor_cores && tc_n;
+  const bool tc128 = s->prec == QS_C128 && s->arith == QS_ARITH_DF && s->tensor_cores && tc_n;
   if (tc64 || tc128) {
     std::vector<int> kt(targs);
     if (n == 2) {

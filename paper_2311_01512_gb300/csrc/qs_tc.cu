@@ -9,13 +9,16 @@
 // Ah, Bh exact TF32 values, C = Ah Bh + Ah Bl + Al Bh accumulated in FP32 in
 // tensor memory, which keeps FP32-level accuracy.
 //
-// One CTA: 256 threads gather a tile through the same bit-insertion
-// enumeration as the CUDA-core kernels, split it into TF32 halves and write
-// both into shared memory in the UMMA canonical K-major layout (8-row x 16-byte
-// core matrices, no swizzle); one thread issues the MMAs and commits them to an
-// mbarrier; all eight warps read the accumulator back with tcgen05.ld and
-// scatter the results.  Every wait is bounded: on timeout the kernel records
-// an error code, frees its tensor memory and returns.
+// Work mapping and pipeline as in the complex128 kernel (qs_tc_ozaki.cu):
+// thread (warp w, lane) owns tile row g = 32 (w mod 4) + lane (its
+// tensor-memory lane) and amplitudes [c EPT, (c+1) EPT), c = w / 4, for the
+// gather, the split and the epilogue; operands are written in the canonical
+// K-major no-swizzle layout (8-row x 16-byte core matrices) as 16-byte
+// vectors; with two operand and accumulator buffers, the loads of tile i + 1
+// are issued before the epilogue of tile i - 1, which runs while the tensor
+// cores work on tile i.  One thread issues the MMAs and commits them to an
+// mbarrier.  Every wait is bounded: on timeout the kernel records an error
+// code, frees its tensor memory and returns.
 #include "qs_device.cuh"
 #include "qs_tc_ptx.cuh"
 
@@ -27,86 +30,90 @@ using namespace tcptx;
 constexpr int kRows = 128;
 constexpr uint32_t kWaitLimit = 1u << 26;
 
+__host__ __device__ constexpr uint32_t tc_cols(uint32_t n) {
+  return n <= 32 ? 32 : (n <= 64 ? 64 : (n <= 128 ? 128 : (n <= 256 ? 256 : 512)));
+}
+
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t spins = 0;
+  while (!mbar_try_wait(bar, parity))
+    if (++spins > kWaitLimit) return true;
+  return false;
+}
+
 }  // namespace
 
-template <int NT>
-__global__ void __launch_bounds__(256, 2) k_dense_tc(float2* __restrict__ psi, const __grid_constant__ TcParams p) {
+template <int NT, int THREADS, int NBUF>
+__global__ void __launch_bounds__(THREADS, 1) k_dense_tc(float2* __restrict__ psi, const __grid_constant__ TcParams p) {
   constexpr int D = 1 << NT;
   constexpr int K = 2 * D;                   // real inputs per group
   constexpr int N = 2 * D;                   // real outputs per group
-  constexpr int OPB = kRows * K * 4;         // bytes of one A operand
+  constexpr int CG = THREADS / kRows;        // threads per row
+  constexpr int EPT = D / CG;                // amplitudes per thread
+  constexpr int CPW = 2 * EPT;               // accumulator columns per thread
+  static_assert(EPT % 4 == 0, "eight accumulator columns per epilogue step");
+  constexpr int OPB = kRows * K * 4;         // bytes of one A operand (hi or lo)
   constexpr int BPB = N * K * 4;             // bytes of one B operand
-  constexpr uint32_t TCOLS = N < 32 ? 32 : N;
+  constexpr uint32_t TCOLS = tc_cols(NBUF * N);
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* a_hi = smem;
-  unsigned char* a_lo = a_hi + OPB;
-  unsigned char* b_hi = a_lo + OPB;
+  unsigned char* a_op = smem;                                         // NBUF x (hi, lo)
+  unsigned char* b_hi = a_op + NBUF * 2 * OPB;
   unsigned char* b_lo = b_hi + BPB;
-  uint64_t* row_base = reinterpret_cast<uint64_t*>(b_lo + BPB);   // kRows
-  uint64_t* toff = row_base + kRows;                               // D
-  uint64_t* sc_lo = toff + D;                                      // 32: index bits of e & 31
-  uint64_t* sc_hi = sc_lo + 32;                                    // 128: index bits of e >> 5
-  uint32_t* gl_lo = reinterpret_cast<uint32_t*>(sc_hi + 128);      // 32: (row | col << 16) bits
-  uint32_t* gl_hi = gl_lo + 32;                                    // 128
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(gl_hi + 128);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  uint64_t* toff = reinterpret_cast<uint64_t*>(b_lo + BPB);          // D
+  uint64_t* rowoff = toff + D;                                        // kRows
+  uint64_t* tile_base = rowoff + kRows;                               // 2
+  uint64_t* mbar = tile_base + 2;                                     // 2
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   // B = realified matrix, split into TF32 halves, once per CTA.
-  for (int e = tid; e < N * K; e += blockDim.x) {
+  for (int e = tid; e < N * K; e += THREADS) {
     const int n = e / K, k = e % K;
-    const int j = n >> 1, c = n & 1, l = k >> 1, cp = k & 1;
-    const double mr = p.mat[2 * (j * D + l)];
-    const double mi = p.conj ? -p.mat[2 * (j * D + l) + 1] : p.mat[2 * (j * D + l) + 1];
-    const double v = (c == 0) ? (cp == 0 ? mr : -mi) : (cp == 0 ? mi : mr);
+    int j = n >> 1, l = k >> 1, Dm = D;
+    const int c = n & 1, cp = k & 1;
+    double v = 0.0;
+    if (p.nmat < p.n) {                       // identity on the extra targets
+      Dm = 1 << p.nmat;
+      if ((j >> p.nmat) != (l >> p.nmat)) Dm = 0;
+      j &= (1 << p.nmat) - 1;
+      l &= (1 << p.nmat) - 1;
+    }
+    if (Dm) {
+      const double mr = p.mat[2 * (j * Dm + l)];
+      const double mi = p.conj ? -p.mat[2 * (j * Dm + l) + 1] : p.mat[2 * (j * Dm + l) + 1];
+      v = (c == 0) ? (cp == 0 ? mr : -mi) : (cp == 0 ? mi : mr);
+    }
     const float f = (float)v;
     const float h = tf32_hi(f);
     const uint32_t off = canon_off(n, k, K);
     *reinterpret_cast<float*>(b_hi + off) = h;
     *reinterpret_cast<float*>(b_lo + off) = f - h;
   }
-  for (int j = tid; j < D; j += blockDim.x) {
+  for (int j = tid; j < D; j += THREADS) {
     uint64_t off = 0;
 #pragma unroll
     for (int q = 0; q < NT; ++q)
       if ((j >> q) & 1) off |= 1ull << p.tpos[q];
     toff[j] = off;
   }
-  // Tables splitting a tile element e (index order) into its global index
-  // bits and its (row, column): row = bits at the free slots of P in order,
-  // column l = bits at the target slots (bit q of l at tslot[q]).
-  const int lo_bits = p.tile_bits < 5 ? p.tile_bits : 5;
-  int lo_free = 0;
-  for (int b = 0; b < lo_bits; ++b)
-    if (!((p.tslot_mask >> b) & 1)) ++lo_free;
-  for (int t = tid; t < 32 + 128; t += blockDim.x) {
-    const bool lo = t < 32;
-    const int v = lo ? t : t - 32;
-    const int b0 = lo ? 0 : lo_bits, b1 = lo ? lo_bits : p.tile_bits;
-    uint64_t sc = 0;
-    uint32_t g = 0, l = 0;
-    int gb = lo ? 0 : lo_free;
-    for (int b = b0; b < b1; ++b) {
-      const uint32_t bit = (uint32_t)(v >> (b - b0)) & 1u;
-      sc |= (uint64_t)bit << p.P[b];
-      if ((p.tslot_mask >> b) & 1) {
-        for (int q = 0; q < NT; ++q)
-          if (p.tslot[q] == b) l |= bit << q;
-      } else {
-        g |= bit << gb;
-        ++gb;
+  const int row_bits = p.tile_bits - NT;
+  for (int g = tid; g < kRows; g += THREADS) {
+    uint64_t off = 0;
+    for (int b = 0, r = 0; b < p.tile_bits; ++b)
+      if (!((p.tslot_mask >> b) & 1)) {
+        if ((g >> r) & 1) off |= 1ull << p.P[b];
+        ++r;
       }
-    }
-    if (lo) {
-      sc_lo[v] = sc;
-      gl_lo[v] = g | (l << 16);
-    } else {
-      sc_hi[v] = sc;
-      gl_hi[v] = g | (l << 16);
-    }
+    rowoff[g] = off;
   }
-  if (tid == 0) mbar_init(mbar, 1);
+  if (tid == 0) {
+    tile_base[0] = insert_zeros(blockIdx.x, p.hi_ins, p.nhi) | p.ctrl_mask;
+    if (blockIdx.x + gridDim.x < p.ntiles)
+      tile_base[1] = insert_zeros(blockIdx.x + gridDim.x, p.hi_ins, p.nhi) | p.ctrl_mask;
+#pragma unroll
+    for (int b = 0; b < NBUF; ++b) mbar_init(mbar + b, 1);
+  }
   if (warp == 0) {
     tmem_alloc(tmem_slot, TCOLS);
     tmem_relinquish();
@@ -117,126 +124,163 @@ __global__ void __launch_bounds__(256, 2) k_dense_tc(float2* __restrict__ psi, c
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc = idesc_tf32(kRows, N);
-  const uint32_t sbo = K * 32;
-  uint32_t phase = 0;
-  bool failed = false;
+  constexpr uint32_t sbo = K * 32;
 
-  const int tile = 1 << p.tile_bits;
-  const int rows = tile >> NT;
-  for (uint64_t c = blockIdx.x; c < p.ntiles && !failed; c += gridDim.x) {
-    const uint64_t base = insert_zeros(c, p.hi_ins, p.nhi) | p.ctrl_mask;
-    // gather: tile element e (index order) -> row g (free slots), column l (target slots)
-    // every load of this thread first, then the shared-memory writes
-    constexpr int EPT = kRows * D / 256;
-    float2 vals[EPT];
+  const int g = 32 * (warp & 3) + lane;       // row (tensor-memory lane)
+  const int cg = warp >> 2;
+  const int l0 = cg * EPT;
+  const bool row_ok = g < (1 << row_bits);
+  const uint64_t roff = rowoff[g];
+  const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+  const int helper = THREADS > kRows ? kRows : 0;
+  uint64_t toffr[EPT];
 #pragma unroll
-    for (int r = 0; r < EPT; ++r) {
-      const int e = tid + r * 256;
-      if (e < tile) vals[r] = psi[base | sc_lo[e & ((1 << lo_bits) - 1)] | sc_hi[e >> lo_bits]];
+  for (int i = 0; i < EPT; ++i) toffr[i] = toff[l0 + i];
+  // When the lowest target bits are the lowest qubits in order, a thread's
+  // amplitudes are consecutive in memory (and start on an even index): move
+  // them two at a time (16 bytes).  The test depends on l mod EPT only, so it
+  // is the same in every thread.
+  bool vec = true;
+#pragma unroll
+  for (int i = 1; i < EPT; ++i) vec = vec && toffr[i] == toffr[0] + (uint64_t)i;
+
+  float2 R[EPT];
+  auto load_tile = [&](uint64_t base) {
+    const uint64_t rb = base | roff;
+    if (vec) {
+#pragma unroll
+      for (int i = 0; i < EPT; i += 2) {
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (row_ok) v = *reinterpret_cast<const float4*>(psi + (rb | toffr[i]));
+        R[i] = make_float2(v.x, v.y);
+        R[i + 1] = make_float2(v.z, v.w);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < EPT; ++i) R[i] = row_ok ? psi[rb | toffr[i]] : make_float2(0.0f, 0.0f);
     }
+  };
+  auto epilogue = [&](uint32_t tbuf, uint64_t rb) {
 #pragma unroll
-    for (int r = 0; r < EPT; ++r) {
-      const int e = tid + r * 256;
-      if (e >= tile) continue;
-      const int elo = e & ((1 << lo_bits) - 1), ehi = e >> lo_bits;
-      const uint32_t gl = gl_lo[elo] | gl_hi[ehi];
-      const int g = (int)(gl & 0xFFFFu), l = (int)(gl >> 16);
-      const float2 v = vals[r];
-      const float hx = tf32_hi(v.x), hy = tf32_hi(v.y);
-      const uint32_t o0 = canon_off(g, 2 * l, K), o1 = canon_off(g, 2 * l + 1, K);
-      *reinterpret_cast<float*>(a_hi + o0) = hx;
-      *reinterpret_cast<float*>(a_hi + o1) = hy;
-      *reinterpret_cast<float*>(a_lo + o0) = v.x - hx;
-      *reinterpret_cast<float*>(a_lo + o1) = v.y - hy;
-      if (l == 0) row_base[g] = base | sc_lo[elo] | sc_hi[ehi];
+    for (int cc = 0; cc < CPW; cc += 8) {
+      float v[8];
+      tmem_ld8(tmem + tbuf + lane_addr + (uint32_t)(cg * CPW + cc), v);
+      tmem_wait_ld();
+      if (row_ok) {
+        if (vec) {
+#pragma unroll
+          for (int q = 0; q < 8; q += 4)
+            *reinterpret_cast<float4*>(psi + (rb | toffr[(cc + q) >> 1])) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; q += 2) psi[rb | toffr[(cc + q) >> 1]] = make_float2(v[q], v[q + 1]);
+        }
+      }
+    }
+  };
+
+  load_tile(tile_base[0]);
+  uint32_t phases = 0;
+  bool failed = false;
+  int it = 0;
+  uint64_t rb_prev = 0;
+  for (uint64_t c = blockIdx.x; c < p.ntiles; c += gridDim.x, ++it) {
+    const int b = NBUF == 2 ? (it & 1) : 0;
+    const int par = it & 1;
+    const uint64_t rb = tile_base[par] | roff;
+    const bool has_next = c + gridDim.x < p.ntiles;
+    // TF32 halves of this thread's amplitudes, 16 bytes (two amplitudes) per store
+    unsigned char* ahi = a_op + b * (2 * OPB);
+    unsigned char* alo = ahi + OPB;
+#pragma unroll
+    for (int i = 0; i < EPT; i += 2) {
+      const float hx0 = tf32_hi(R[i].x), hy0 = tf32_hi(R[i].y);
+      const float hx1 = tf32_hi(R[i + 1].x), hy1 = tf32_hi(R[i + 1].y);
+      const uint32_t off = canon_off(g, 2 * (l0 + i), K);
+      *reinterpret_cast<float4*>(ahi + off) = make_float4(hx0, hy0, hx1, hy1);
+      *reinterpret_cast<float4*>(alo + off) =
+          make_float4(R[i].x - hx0, R[i].y - hy0, R[i + 1].x - hx1, R[i + 1].y - hy1);
     }
     fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
       fence_after_sync();
-      const uint32_t sa_hi = smem_u32(a_hi), sa_lo = smem_u32(a_lo);
-      const uint32_t sb_hi = smem_u32(b_hi), sb_lo = smem_u32(b_lo);
-      uint32_t acc = 0;
+      const uint64_t dah = smem_desc(smem_u32(ahi), 128, sbo), dal = smem_desc(smem_u32(alo), 128, sbo);
+      const uint64_t dbh = smem_desc(smem_u32(b_hi), 128, sbo), dbl = smem_desc(smem_u32(b_lo), 128, sbo);
+      const uint32_t d = tmem + (uint32_t)(b * N);
 #pragma unroll
-      for (int kk = 0; kk < K / 8; ++kk) {     // Al Bh
-        mma_tf32(tmem, smem_desc(sa_lo + kk * 256, 128, sbo), smem_desc(sb_hi + kk * 256, 128, sbo), idesc, acc);
-        acc = 1;
-      }
+      for (int kk = 0; kk < K / 8; ++kk)     // Al Bh
+        mma_tf32(d, dal + (kk * 256 >> 4), dbh + (kk * 256 >> 4), idesc, kk != 0);
 #pragma unroll
-      for (int kk = 0; kk < K / 8; ++kk)       // Ah Bl
-        mma_tf32(tmem, smem_desc(sa_hi + kk * 256, 128, sbo), smem_desc(sb_lo + kk * 256, 128, sbo), idesc, 1);
+      for (int kk = 0; kk < K / 8; ++kk)     // Ah Bl
+        mma_tf32(d, dah + (kk * 256 >> 4), dbl + (kk * 256 >> 4), idesc, 1);
 #pragma unroll
-      for (int kk = 0; kk < K / 8; ++kk)       // Ah Bh
-        mma_tf32(tmem, smem_desc(sa_hi + kk * 256, 128, sbo), smem_desc(sb_hi + kk * 256, 128, sbo), idesc, 1);
-      mma_commit(mbar);
+      for (int kk = 0; kk < K / 8; ++kk)     // Ah Bh
+        mma_tf32(d, dah + (kk * 256 >> 4), dbh + (kk * 256 >> 4), idesc, 1);
+      mma_commit(mbar + b);
     }
-    // bounded wait for the MMAs of this tile
-    uint32_t spins = 0;
+    // loads of the next tile, in flight during the MMAs and the epilogue
+    if (has_next) load_tile(tile_base[par ^ 1]);
     bool timed_out = false;
-    while (!mbar_try_wait(mbar, phase)) {
-      if (++spins > kWaitLimit) {
-        timed_out = true;
-        break;
+    if (NBUF == 2) {
+      if (it > 0) {
+        const int pb = b ^ 1;
+        timed_out = tc_wait(mbar + pb, (phases >> pb) & 1u);
+        phases ^= 1u << pb;
+        fence_after_sync();
+        epilogue((uint32_t)(pb * N), rb_prev);
       }
+    } else {
+      timed_out = tc_wait(mbar, phases & 1u);
+      phases ^= 1u;
+      fence_after_sync();
+      epilogue(0u, rb);
     }
-    phase ^= 1;
-    failed = __syncthreads_or(timed_out) != 0;    // the same decision in every thread
-    if (failed) {
-      if (tid == 0) atomicExch(p.err, 1);
-      break;
-    }
-    fence_after_sync();
-    // epilogue: warp w reads lanes 32 (w % 4) .. +31, columns of half (w / 4)
-    const int g = 32 * (warp & 3) + lane;
-    const int c0 = (warp >> 2) * (N / 2);
-    float v[N / 2];
-#pragma unroll
-    for (int cc = 0; cc < N / 2; cc += 8)
-      tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + cc), v + cc);
-    tmem_wait_ld();
-    if (g < rows) {
-      const uint64_t rb = row_base[g];
-#pragma unroll
-      for (int cc = 0; cc < N / 2; cc += 2) {
-        const int j = (c0 + cc) >> 1;
-        psi[rb | toff[j]] = make_float2(v[cc], v[cc + 1]);
-      }
-    }
+    rb_prev = rb;
+    if (tid == helper && c + 2 * (uint64_t)gridDim.x < p.ntiles)
+      tile_base[par] = insert_zeros(c + 2 * (uint64_t)gridDim.x, p.hi_ins, p.nhi) | p.ctrl_mask;
     fence_before_sync();
-    __syncthreads();
+    failed = __syncthreads_or(timed_out) != 0;
     fence_after_sync();
+    if (failed) break;
   }
+  if (NBUF == 2 && !failed && it > 0) {
+    const int pb = (it - 1) & 1;
+    const bool timed_out = tc_wait(mbar + pb, (phases >> pb) & 1u);
+    fence_after_sync();
+    epilogue((uint32_t)(pb * N), rb_prev);
+    fence_before_sync();
+    failed = __syncthreads_or(timed_out) != 0;
+  }
+  if (failed && tid == 0) atomicExch(p.err, 1);
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, TCOLS);
 }
 
-template <int NT>
+template <int NT, int THREADS, int NBUF, int CTAS>
 static cudaError_t dense_tc_nt(void* amps, const TcParams& p, cudaStream_t st) {
   constexpr int D = 1 << NT, K = 2 * D, N = 2 * D;
-  const size_t smem = 2 * (size_t)kRows * K * 4 + 2 * (size_t)N * K * 4 + 8 * (kRows + D + 160 + 1) + 4 * 160 + 16;
+  constexpr size_t smem = (size_t)NBUF * 2 * kRows * K * 4 + 2 * (size_t)N * K * 4 + 8 * (D + kRows + 4) + 16;
+  static_assert(smem * CTAS <= 227 * 1024, "shared memory");
+  static_assert(CTAS * tc_cols(NBUF * N) <= 512, "tensor memory");
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_dense_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_dense_tc<NT, THREADS, NBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  // CTAs per SM: shared memory (about 200 KiB usable), 8 x 256 threads, and
-  // tensor memory (512 columns) all bound it
-  int per_sm = (int)((200 * 1024) / smem);
-  per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
-  const int tcols = N < 32 ? 32 : N;
-  if (per_sm * tcols > 512) per_sm = 512 / tcols;
-  const uint64_t maxb = (uint64_t)num_sms() * per_sm;
+  const uint64_t maxb = (uint64_t)num_sms() * CTAS;
   const unsigned g = (unsigned)(p.ntiles < maxb ? p.ntiles : maxb);
-  k_dense_tc<NT><<<g, 256, smem, st>>>(static_cast<float2*>(amps), p);
+  k_dense_tc<NT, THREADS, NBUF><<<g, THREADS, smem, st>>>(static_cast<float2*>(amps), p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dense_tc(void* amps, const TcParams& p, cudaStream_t st) {
   switch (p.n) {
-    case 3: return dense_tc_nt<3>(amps, p, st);
-    case 4: return dense_tc_nt<4>(amps, p, st);
-    case 5: return dense_tc_nt<5>(amps, p, st);
+    case 3: return dense_tc_nt<3, 256, 2, 3>(amps, p, st);
+    case 4: return dense_tc_nt<4, 512, 2, 2>(amps, p, st);
+    case 5: return dense_tc_nt<5, 512, 2, 1>(amps, p, st);
     default: return cudaErrorInvalidValue;
   }
 }

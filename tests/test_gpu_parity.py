@@ -352,13 +352,19 @@ def test_validation_errors(qs):
 
 
 # ---------------------------------------------------------------------------
-# tensor-core path (complex64 dense gates, 3..5 targets) against the CUDA cores
+# tensor-core path (complex64 dense gates, 2..5 targets) against the CUDA cores
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("nq,n,s", [(5, 5, 0), (8, 3, 2), (10, 4, 0), (13, 5, 2), (16, 3, 0), (16, 5, 1)])
-def test_tensor_core_gate_matches_cuda_cores(qs, nq, n, s):
-    rng = np.random.default_rng(600 + 10 * nq + n + s)
+@pytest.mark.parametrize("nq,n,s", [(5, 5, 0), (8, 3, 2), (10, 4, 0), (13, 5, 2), (16, 3, 0), (16, 5, 1),
+                                     (3, 2, 0), (4, 2, 1), (11, 2, 2), (17, 4, 1)])
+@pytest.mark.parametrize("place", ["random", "lowest", "highest"])
+def test_tensor_core_gate_matches_cuda_cores(qs, nq, n, s, place):
+    rng = np.random.default_rng(600 + 10 * nq + n + s + 7 * len(place))
     qsel = [int(x) for x in rng.choice(nq, n + s, replace=False)]
+    if place == "lowest":
+        qsel = list(range(n + s))
+    elif place == "highest":
+        qsel = list(range(nq - 1, nq - 1 - n - s, -1))
     targs, ctrls = qsel[:n], qsel[n:]
     psi = wl.random_statevector(nq, rng).astype(np.complex64)
     mat = wl.haar_unitary(1 << n, rng)
