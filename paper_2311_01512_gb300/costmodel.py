@@ -145,13 +145,32 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--samples", type=int, default=20000)
     ap.add_argument("--out", default=WEIGHTS_PATH)
-    ap.add_argument("--epochs", type=int, default=300)
+    ap.add_argument("--epochs", type=int, nargs="+", default=[300],
+                    help="train once per value; the model with the lowest hold-out error is saved")
+    ap.add_argument("--data-out", help="also save the timed rows (X, log ms) here")
+    ap.add_argument("--data-in", help="train on rows saved by --data-out instead of timing new ones")
     args = ap.parse_args()
-    configs = [(0, 24), (0, 27), (0, 30), (0, 32), (1, 24), (1, 27), (1, 30), (1, 31)]
-    X, y, meta = collect(args.samples, configs)
-    model, metrics = train(X, y, epochs=args.epochs)
-    meta.update(metrics)
-    save(model, args.out, meta)
+    if args.data_in:
+        d = np.load(args.data_in)
+        X, y, meta = d["X"], d["y"], json.loads(str(d["meta"]))
+    else:
+        configs = [(0, 24), (0, 27), (0, 30), (0, 32), (1, 24), (1, 27), (1, 30), (1, 31)]
+        X, y, meta = collect(args.samples, configs)
+        if args.data_out:
+            np.savez(args.data_out, X=X, y=y, meta=json.dumps(meta))
+    best = None
+    for ep in args.epochs:
+        model, metrics = train(X, y, epochs=ep)
+        metrics["epochs"] = ep
+        print(json.dumps(metrics), flush=True)
+        if best is None or metrics["holdout_rmse_log"] < best[1]["holdout_rmse_log"]:
+            if best is not None:
+                best[0].close()
+            best = (model, metrics)
+        else:
+            model.close()
+    meta.update(best[1])
+    save(best[0], args.out, meta)
     print(json.dumps(meta))
 
 

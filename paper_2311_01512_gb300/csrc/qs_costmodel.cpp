@@ -138,8 +138,10 @@ qs_status qs_costmodel_encode(int kind, int width, unsigned long long qmask, int
   out[48] = s->prec == QS_C128 ? 1.0f : 0.0f;
   out[49] = s->is_density ? 1.0f : 0.0f;
   out[50] = (s->prec == QS_C128 && s->arith == QS_ARITH_DF) ? 1.0f : 0.0f;
-  out[51] = (s->prec == QS_C64 && s->tensor_cores && (kind == QS_COST_FUSED_DENSE || kind == QS_COST_DENSE) &&
-             width >= 3 && width <= 5)
+  // dense launches that run on the tensor-core kernels (2..5 targets; complex128 with double-float)
+  const bool tc_prec = s->prec == QS_C64 || s->arith == QS_ARITH_DF;
+  out[51] = (tc_prec && s->tensor_cores && (kind == QS_COST_FUSED_DENSE || kind == QS_COST_DENSE) && width >= 2 &&
+             width <= 5)
                 ? 1.0f
                 : 0.0f;
   out[52] = (float)weight / 34.0f;
