@@ -48,7 +48,8 @@ def parse_args(argv=None):
     ap.add_argument("--f64-share", type=int, default=0,
                     help="sixteenths of one-target-gate work done in native FP64 beside double-float")
     ap.add_argument("--no-fused", action="store_true", help="skip the fused tensor-core comparison")
-    ap.add_argument("--fused-qubits", type=int, default=30)
+    ap.add_argument("--fused-qubits", type=int, default=32,
+                    help="qubits of the fused comparison (32: the complex64 fused workload's size)")
     ap.add_argument("--fused-prec", choices=("c64", "c128"), default="c64",
                     help="precision of the fused form: complex64 (3xTF32 blocks) or complex128 (bf16 integer slices)")
     ap.add_argument("--detail", default="", help="write per-kernel-family statistics to this JSON file")
