@@ -196,6 +196,16 @@ qs_status qs_apply_two_qubit_depolarising(qs_state* state, int t1, int t2, doubl
  * update)). */
 qs_status qs_apply_damping(qs_state* state, int t, double p);
 
+/* One-qubit Pauli channel, rho -> (1 - px - py - pz) rho + px X rho X
+ * + py Y rho Y + pz Z rho Z on qubit t: the general form of the depolarising
+ * channel (Sec. "Depolarising channel"; the paper notes the extension), and
+ * dephasing at (0, 0, p).  On the Choi vector, where bits t and t + N agree,
+ * beta_i -> (1 - px - py) beta_i + (px + py) beta_{i flip t, t+N}; where they
+ * differ, beta_i -> (1 - px - py - 2 pz) beta_i + (px - py) beta_{i flip t, t+N}.
+ * Density matrices only; each probability in [0, 1] (their sum is not
+ * checked, as the paper checks no CPTP condition). */
+qs_status qs_apply_pauli_channel(qs_state* state, int t, double px, double py, double pz);
+
 /* Partial trace over n targets, 1 <= n < N (Sec. "Partial trace", Eqs.
  * (reduced amplitude definition) and (index function)):
  * beta'_i = sum_v beta_{g(i, v)}.  The input is not modified.  The result is a

@@ -439,6 +439,22 @@ def densmatr_apply_damping(rho, t, p):
     return out
 
 
+def densmatr_apply_pauli_channel(rho, t, px, py, pz):
+    """One-qubit Pauli channel rho -> (1 - px - py - pz) rho + px X rho X +
+    py Y rho Y + pz Z rho Z on qubit t: the general form of the depolarising
+    channel (Sec. "Depolarising channel", which notes the extension).  Each
+    sigma rho sigma is the unitary sigma applied to the Choi vector (Sec.
+    "Unitary gates": sigma on t, conj(sigma) on t + N)."""
+    rho = np.asarray(rho, dtype=np.complex128)
+    sx = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+    sy = np.array([[0, -1j], [1j, 0]], dtype=np.complex128)
+    sz = np.array([[1, 0], [0, -1]], dtype=np.complex128)
+    out = (1.0 - px - py - pz) * rho
+    for p, sig in ((px, sx), (py, sy), (pz, sz)):
+        out = out + p * densmatr_apply_ctrl_multi_target(rho, [], [t], sig)
+    return out
+
+
 def partial_trace(rho, targs):
     """Partial trace over targs (Sec. "Partial trace", Eqs. (reduced amplitude
     definition) and (index function)): beta'_i = sum_v beta_{g(i, v)}, where
@@ -540,6 +556,8 @@ def run_ops(state, ops, is_density):
             s = densmatr_apply_two_qubit_depolarising(s, op["targs"][0], op["targs"][1], op["p"])
         elif kind == "damping":
             s = densmatr_apply_damping(s, op["targs"][0], op["p"])
+        elif kind == "pauli_channel":
+            s = densmatr_apply_pauli_channel(s, op["targs"][0], *op["probs"])
         else:
             raise ValueError("unknown op " + kind)
     return s

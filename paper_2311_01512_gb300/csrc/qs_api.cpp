@@ -528,7 +528,7 @@ qs_status qs_apply_kraus(qs_state* s, const int* targs, int n, const double* kra
 
 namespace {
 
-qs_status group_channel(qs_state* s, int op, int t1, int t2, const double f[3]) {
+qs_status group_channel(qs_state* s, int op, int t1, int t2, const double* f) {
   if (!s) return QS_ERR_ARG;
   if (!s->is_density) return QS_ERR_NOT_DENSMATR;
   const bool two = (op == qsk::G_DEPHASE2 || op == qsk::G_DEPOL2);
@@ -546,9 +546,7 @@ qs_status group_channel(qs_state* s, int op, int t1, int t2, const double f[3]) 
   std::sort(pos.begin(), pos.end());
   for (int b = 0; b < p.nbits; ++b) p.ins[b] = (int8_t)pos[b];
   p.ngroups = 1ull << (s->ns - p.nbits);
-  p.f[0] = f[0];
-  p.f[1] = f[1];
-  p.f[2] = f[2];
+  for (int k = 0; k < 4; ++k) p.f[k] = f[k];
   return cuda_status(qsk::launch_group(s->prec, s->amps, op, p, s->stream));
 }
 
@@ -556,32 +554,38 @@ qs_status group_channel(qs_state* s, int op, int t1, int t2, const double f[3]) 
 
 qs_status qs_apply_dephasing(qs_state* s, int t, double p) {
   if (check_prob(p) != QS_OK) return QS_ERR_ARG;
-  const double f[3] = {1.0 - 2.0 * p, 0.0, 0.0};
+  const double f[4] = {1.0 - 2.0 * p, 0.0, 0.0, 0.0};
   return group_channel(s, qsk::G_DEPHASE1, t, t, f);
 }
 
 qs_status qs_apply_two_qubit_dephasing(qs_state* s, int t1, int t2, double p) {
   if (check_prob(p) != QS_OK) return QS_ERR_ARG;
-  const double f[3] = {1.0 - 4.0 * p / 3.0, 0.0, 0.0};
+  const double f[4] = {1.0 - 4.0 * p / 3.0, 0.0, 0.0, 0.0};
   return group_channel(s, qsk::G_DEPHASE2, t1, t2, f);
 }
 
 qs_status qs_apply_depolarising(qs_state* s, int t, double p) {
   if (check_prob(p) != QS_OK) return QS_ERR_ARG;
-  const double f[3] = {1.0 - 2.0 * p / 3.0, 2.0 * p / 3.0, 1.0 - 4.0 * p / 3.0};
+  const double f[4] = {1.0 - 2.0 * p / 3.0, 2.0 * p / 3.0, 1.0 - 4.0 * p / 3.0, 0.0};
   return group_channel(s, qsk::G_DEPOL1, t, t, f);
 }
 
 qs_status qs_apply_two_qubit_depolarising(qs_state* s, int t1, int t2, double p) {
   if (check_prob(p) != QS_OK) return QS_ERR_ARG;
-  const double f[3] = {1.0 - 4.0 * p / 5.0, 4.0 * p / 15.0, 1.0 - 16.0 * p / 15.0};
+  const double f[4] = {1.0 - 4.0 * p / 5.0, 4.0 * p / 15.0, 1.0 - 16.0 * p / 15.0, 0.0};
   return group_channel(s, qsk::G_DEPOL2, t1, t2, f);
 }
 
 qs_status qs_apply_damping(qs_state* s, int t, double p) {
   if (check_prob(p) != QS_OK) return QS_ERR_ARG;
-  const double f[3] = {1.0 - p, p, std::sqrt(1.0 - p)};
+  const double f[4] = {1.0 - p, p, std::sqrt(1.0 - p), 0.0};
   return group_channel(s, qsk::G_DAMP, t, t, f);
+}
+
+qs_status qs_apply_pauli_channel(qs_state* s, int t, double px, double py, double pz) {
+  if (check_prob(px) != QS_OK || check_prob(py) != QS_OK || check_prob(pz) != QS_OK) return QS_ERR_ARG;
+  const double f[4] = {1.0 - px - py, px + py, 1.0 - px - py - 2.0 * pz, px - py};
+  return group_channel(s, qsk::G_PAULI1, t, t, f);
 }
 
 qs_status qs_partial_trace(const qs_state* in, const int* targs, int n, void* d_out_amps, qs_state** out) {

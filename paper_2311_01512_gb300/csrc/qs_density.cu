@@ -22,16 +22,23 @@ namespace qsk {
 //     new = f0 self + f1 (sum of the other three) (f0 = 1 - 4p/5, f1 = 4p/15);
 //     the 12 others scale by f2 = 1 - 16p/15;
 //   damping (Eq. damping update): 00 -> 00 + f1 11 (f1 = p); 01, 10 scale by
-//     f2 = sqrt(1 - p); 11 scales by f0 = 1 - p.
+//     f2 = sqrt(1 - p); 11 scales by f0 = 1 - p;
+//   Pauli channel, one qubit (the general form of the depolarising channel,
+//     rho -> (1 - px - py - pz) rho + px X rho X + py Y rho Y + pz Z rho Z):
+//     00 and 11 mix as new = f0 self + f1 other (f0 = 1 - px - py,
+//     f1 = px + py); 01 and 10 mix as new = f2 self + f3 other
+//     (f2 = 1 - px - py - 2 pz, f3 = px - py), since on the Choi vector
+//     X rho X and Y rho Y both swap the pair and Y rho Y, Z rho Z carry the
+//     sign (-1)^(bit t + bit t+N).
 // ---------------------------------------------------------------------------
 template <typename R, int OP>
 __global__ void __launch_bounds__(256) k_group(typename Cplx<R>::T* __restrict__ rho, const __grid_constant__ GroupParams p) {
   using T2 = typename Cplx<R>::T;
-  const R f0 = (R)p.f[0], f1 = (R)p.f[1], f2 = (R)p.f[2];
+  const R f0 = (R)p.f[0], f1 = (R)p.f[1], f2 = (R)p.f[2], f3 = (R)p.f[3];
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < p.ngroups; k += stride) {
     const uint64_t base = insert_zeros(k, p.ins, p.nbits);
-    if (OP == G_DEPHASE1 || OP == G_DEPOL1 || OP == G_DAMP) {
+    if (OP == G_DEPHASE1 || OP == G_DEPOL1 || OP == G_DAMP || OP == G_PAULI1) {
       const uint64_t b0 = 1ull << p.mpos[0], b1 = 1ull << p.mpos[1];
       const uint64_t i00 = base, i01 = base | b0, i10 = base | b1, i11 = base | b0 | b1;
       if (OP == G_DEPHASE1) {
@@ -45,6 +52,11 @@ __global__ void __launch_bounds__(256) k_group(typename Cplx<R>::T* __restrict__
           rho[i11] = mk<R>(f0 * d.x + f1 * a.x, f0 * d.y + f1 * a.y);
           rho[i01] = mk<R>(f2 * b.x, f2 * b.y);
           rho[i10] = mk<R>(f2 * c.x, f2 * c.y);
+        } else if (OP == G_PAULI1) {
+          rho[i00] = mk<R>(f0 * a.x + f1 * d.x, f0 * a.y + f1 * d.y);
+          rho[i11] = mk<R>(f0 * d.x + f1 * a.x, f0 * d.y + f1 * a.y);
+          rho[i01] = mk<R>(f2 * b.x + f3 * c.x, f2 * b.y + f3 * c.y);
+          rho[i10] = mk<R>(f2 * c.x + f3 * b.x, f2 * c.y + f3 * b.y);
         } else {  // damping
           rho[i00] = mk<R>(a.x + f1 * d.x, a.y + f1 * d.y);
           rho[i01] = mk<R>(f2 * b.x, f2 * b.y);
@@ -184,6 +196,7 @@ static cudaError_t group_t(void* amps, int op, const GroupParams& p, cudaStream_
     case G_DEPOL1: k_group<R, G_DEPOL1><<<g, 256, 0, st>>>(a, p); break;
     case G_DEPOL2: k_group<R, G_DEPOL2><<<g, 256, 0, st>>>(a, p); break;
     case G_DAMP: k_group<R, G_DAMP><<<g, 256, 0, st>>>(a, p); break;
+    case G_PAULI1: k_group<R, G_PAULI1><<<g, 256, 0, st>>>(a, p); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

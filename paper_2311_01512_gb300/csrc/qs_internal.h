@@ -110,13 +110,13 @@ struct GadgetDfParams {
 
 // Density-matrix channels acting on groups of 4 (one qubit: bits t, t+N) or 16
 // (two qubits: t1, t2, t1+N, t2+N) Choi amplitudes.
-enum GroupOp { G_DEPHASE1 = 0, G_DEPHASE2 = 1, G_DEPOL1 = 2, G_DEPOL2 = 3, G_DAMP = 4 };
+enum GroupOp { G_DEPHASE1 = 0, G_DEPHASE2 = 1, G_DEPOL1 = 2, G_DEPOL2 = 3, G_DAMP = 4, G_PAULI1 = 5 };
 struct GroupParams {
   uint64_t ngroups;
   int nbits;             // 2 or 4
   int8_t ins[4];         // sorted member positions
   int8_t mpos[4];        // member bit b -> qubit position
-  double f[3];           // channel coefficients (see the kernel)
+  double f[4];           // channel coefficients (see the kernel)
 };
 
 // Partial trace (Sec. "Partial trace").

@@ -58,6 +58,7 @@ SIGNATURES = {
     "qs_apply_depolarising": (_I, [_P, _I, _D]),
     "qs_apply_two_qubit_depolarising": (_I, [_P, _I, _I, _D]),
     "qs_apply_damping": (_I, [_P, _I, _D]),
+    "qs_apply_pauli_channel": (_I, [_P, _I, _D, _D, _D]),
     "qs_partial_trace": (_I, [_P, _IP, _I, _P, ctypes.POINTER(_P)]),
     "qs_expec_pauli_sum": (_I, [_P, _IP, _DP, _I, _DP]),
     "qs_calc_norm_or_trace": (_I, [_P, _DP]),
@@ -241,6 +242,10 @@ def qs_apply_two_qubit_depolarising(h, t1, t2, p):
 
 def qs_apply_damping(h, t, p):
     _check(_lib.qs_apply_damping(h, int(t), float(p)), "qs_apply_damping")
+
+
+def qs_apply_pauli_channel(h, t, px, py, pz):
+    _check(_lib.qs_apply_pauli_channel(h, int(t), float(px), float(py), float(pz)), "qs_apply_pauli_channel")
 
 
 def qs_partial_trace(h, targs, d_out):
@@ -576,5 +581,7 @@ def apply_op(h, op):
         qs_apply_two_qubit_depolarising(h, op["targs"][0], op["targs"][1], op["p"])
     elif kind == "damping":
         qs_apply_damping(h, op["targs"][0], op["p"])
+    elif kind == "pauli_channel":
+        qs_apply_pauli_channel(h, op["targs"][0], *op["probs"])
     else:
         raise ValueError("unknown op " + kind)

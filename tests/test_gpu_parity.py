@@ -238,6 +238,12 @@ CHANNELS = [
      lambda b, t, p: orc.densmatr_apply_two_qubit_depolarising(b, t[0], t[1], p), 2),
     ("damping", lambda qs, h, t, p: qs.qs_apply_damping(h, t[0], p),
      lambda b, t, p: orc.densmatr_apply_damping(b, t[0], p), 1),
+    # Pauli channel with (px, py, pz) = (p/2, p/3, p/6) and, for the asymmetric
+    # part, (p/5, 0, 3p/5)
+    ("pauli", lambda qs, h, t, p: qs.qs_apply_pauli_channel(h, t[0], p / 2, p / 3, p / 6),
+     lambda b, t, p: orc.densmatr_apply_pauli_channel(b, t[0], p / 2, p / 3, p / 6), 1),
+    ("pauli_xz", lambda qs, h, t, p: qs.qs_apply_pauli_channel(h, t[0], p / 5, 0.0, 3 * p / 5),
+     lambda b, t, p: orc.densmatr_apply_pauli_channel(b, t[0], p / 5, 0.0, 3 * p / 5), 1),
 ]
 
 
@@ -343,6 +349,13 @@ def test_validation_errors(qs):
     with pytest.raises(qs.QSError) as ei:
         qs.qs_apply_depolarising(dm.handle, 0, 1.5)
     assert "QS_ERR_ARG" in str(ei.value)
+    for probs in ((-0.1, 0.0, 0.0), (0.0, 1.2, 0.0), (0.0, 0.0, float("nan"))):
+        with pytest.raises(qs.QSError) as ei:
+            qs.qs_apply_pauli_channel(dm.handle, 0, *probs)
+        assert "QS_ERR_ARG" in str(ei.value)
+    with pytest.raises(qs.QSError) as ei:
+        qs.qs_apply_pauli_channel(sv.handle, 0, 0.1, 0.1, 0.1)
+    assert "QS_ERR_NOT_DENSMATR" in str(ei.value)
     with pytest.raises(qs.QSError) as ei:
         qs.qs_apply_kraus(dm.handle, [0, 1, 2, 0], [np.eye(16)])
     # nothing changed after the rejected calls

@@ -362,6 +362,38 @@ def test_channels_match_explicit(seed):
     np.testing.assert_allclose(choi_to_mat(orc.densmatr_apply_damping(beta, t, p)), want, atol=1e-14)
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_pauli_channel_matches_explicit_and_special_cases(seed):
+    """General one-qubit Pauli channel: explicit Pauli conjugations of the
+    density matrix, its Kraus form, and its depolarising (p/3 each) and
+    dephasing (0, 0, p) special cases, which come from other equations."""
+    rng = np.random.default_rng(300 + seed)
+    nq = 4
+    rho = random_density(nq, 4, rng)
+    beta = mat_to_choi(rho)
+    t = int(rng.integers(nq))
+    px, py, pz = (float(x) for x in rng.uniform(0, 0.3, 3))
+    want = (1 - px - py - pz) * rho
+    for p, k in ((px, 1), (py, 2), (pz, 3)):
+        s = _paulis_on(nq, t, k)
+        want = want + p * s @ rho @ s.conj().T
+    got = orc.densmatr_apply_pauli_channel(beta, t, px, py, pz)
+    np.testing.assert_allclose(choi_to_mat(got), want, atol=1e-14)
+    kraus = [np.sqrt(1 - px - py - pz) * I2, np.sqrt(px) * np.array([[0, 1], [1, 0]]),
+             np.sqrt(py) * np.array([[0, -1j], [1j, 0]]), np.sqrt(pz) * np.array([[1, 0], [0, -1]])]
+    np.testing.assert_allclose(got, orc.densmatr_apply_kraus(beta, [t], kraus), atol=1e-14)
+    p = float(rng.uniform(0, 0.5))
+    np.testing.assert_allclose(orc.densmatr_apply_pauli_channel(beta, t, p / 3, p / 3, p / 3),
+                               orc.densmatr_apply_depolarising(beta, t, p), atol=1e-15)
+    np.testing.assert_allclose(orc.densmatr_apply_pauli_channel(beta, t, 0, 0, p),
+                               orc.densmatr_apply_dephasing(beta, t, p), atol=1e-15)
+    # bit flip with px = 1/2 and phase flip with pz = 1/2 remove the X / Z coherences:
+    # together they replace qubit t by I/2 (an independent fixed point)
+    twice = orc.densmatr_apply_pauli_channel(orc.densmatr_apply_pauli_channel(beta, t, 0.5, 0, 0), t, 0, 0, 0.5)
+    np.testing.assert_allclose(choi_to_mat(twice), choi_to_mat(orc.densmatr_apply_depolarising(beta, t, 0.75)),
+                               atol=1e-14)
+
+
 def test_channel_fixed_points_and_special_cases():
     rng = np.random.default_rng(77)
     nq = 3
