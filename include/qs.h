@@ -152,6 +152,12 @@ qs_status qs_init_pure_densmatr(qs_state* rho, const qs_state* psi, double weigh
 qs_status qs_apply_ctrl_multi_target(qs_state* state, const int* ctrls, int nctrl, const int* targs,
                                      int ntarg, const double* mat);
 
+/* SWAP of qubits t1 != t2 (Sec. "Swap gate"): alpha_i -> alpha_{i with bits
+ * t1 and t2 flipped} where bits t1 and t2 of i differ; the rest unchanged.
+ * Exact (amplitudes are moved, not computed).  Density matrix: SWAP on
+ * (t1, t2), then on (t1 + N, t2 + N). */
+qs_status qs_apply_swap(qs_state* state, int t1, int t2);
+
 /* Diagonal operator on ntarg <= QS_MAX_DENSE_TARGETS targets:
  * alpha_i -> diag[j] alpha_i with j the value of the target bits of i (bit q
  * of j on targs[q]); diag: 2^ntarg complex128 (re, im).  The diagonal case of

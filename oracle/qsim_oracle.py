@@ -173,6 +173,22 @@ def apply_ctrl_multi_target(psi, ctrls, targs, mat):
     return psi
 
 
+def apply_swap(psi, t1, t2):
+    """SWAP of qubits t1, t2 (Sec. "Swap gate"): alpha_i -> alpha_{i with
+    bits t1 and t2 flipped} where bits t1 and t2 of i differ, else alpha_i."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    i = np.arange(psi.shape[0], dtype=np.int64)
+    differ = ((i >> t1) & 1) != ((i >> t2) & 1)
+    return np.where(differ, psi[i ^ ((1 << t1) | (1 << t2))], psi)
+
+
+def densmatr_apply_swap(rho, t1, t2):
+    """SWAP on a Choi vector (Sec. "Unitary gates"): SWAP on (t1, t2) and,
+    SWAP being real, SWAP again on (t1 + N, t2 + N)."""
+    nq = _dm_qubits(rho)
+    return apply_swap(apply_swap(rho, t1, t2), t1 + nq, t2 + nq)
+
+
 def apply_diagonal(psi, targs, diag):
     """Diagonal n-target operator: alpha_i -> d_j alpha_i, with j the value of
     the target bits of i (bit q of j on qubit targs[q]).  This is the
@@ -558,6 +574,9 @@ def run_ops(state, ops, is_density):
             s = densmatr_apply_damping(s, op["targs"][0], op["p"])
         elif kind == "pauli_channel":
             s = densmatr_apply_pauli_channel(s, op["targs"][0], *op["probs"])
+        elif kind == "swap":
+            f = densmatr_apply_swap if is_density else apply_swap
+            s = f(s, op["targs"][0], op["targs"][1])
         else:
             raise ValueError("unknown op " + kind)
     return s

@@ -451,6 +451,19 @@ qs_status qs_apply_dense_block(qs_state* s, const int* targs, int ntarg, const d
   return st != QS_OK ? st : st2;
 }
 
+qs_status qs_apply_swap(qs_state* s, int t1, int t2) {
+  if (!s) return QS_ERR_ARG;
+  const int tt[2] = {t1, t2};
+  qs_status st = check_qubits(s->nq, tt, 2, nullptr, 0);
+  if (st != QS_OK) return st;
+  if (t1 > t2) std::swap(t1, t2);
+  st = cuda_status(qsk::launch_swap(s->prec, s->amps, s->ns, t1, t2, s->stream));
+  // density matrix: SWAP is real, so SWAP^* on (t1 + N, t2 + N) is SWAP again
+  if (st == QS_OK && s->is_density)
+    st = cuda_status(qsk::launch_swap(s->prec, s->amps, s->ns, t1 + s->nq, t2 + s->nq, s->stream));
+  return st;
+}
+
 qs_status qs_apply_diagonal(qs_state* s, const int* targs, int ntarg, const double* diag) {
   if (!s || !diag) return QS_ERR_ARG;
   if (ntarg < 1) return QS_ERR_ARG;
@@ -640,6 +653,11 @@ qs_status qs_expec_pauli_sum(const qs_state* cs, const int* paulis, const double
     t.eta = num_y & 3;
     terms[(size_t)n] = t;
   }
+  // statevectors: terms sharing their flip mask become neighbours, so the kernel
+  // loads each partner amplitude once per mask (the sum's order changes only)
+  if (!s->is_density)
+    std::stable_sort(terms.begin(), terms.end(),
+                     [](const qsk::PauliTerm& x, const qsk::PauliTerm& y) { return x.xy < y.xy; });
   for (int first = 0; first < num_terms; first += qsk::kTermChunk) {
     const int cnt = std::min(qsk::kTermChunk, num_terms - first);
     const void* dterms = nullptr;

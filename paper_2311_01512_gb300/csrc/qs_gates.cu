@@ -194,6 +194,35 @@ static cudaError_t gate1_t(void* amps, const Gate1Params& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// SWAP (Sec. "Swap gate"): alpha_i -> alpha_{i with bits t1 and t2 flipped}
+// where those bits differ.  One thread per pair: the group index k takes zero
+// bits at t1 < t2, then the pair is (k | 2^t1, k | 2^t2).  No arithmetic, so
+// the same kernel serves complex64 and complex128 (moved as 8- or 16-byte
+// words).
+// ---------------------------------------------------------------------------
+template <typename T2>
+__global__ void __launch_bounds__(256) k_swap(T2* __restrict__ psi, uint64_t npairs, int t1, int t2) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t b1 = 1ull << t1, b2 = 1ull << t2;
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < npairs; k += stride) {
+    const uint64_t base = insert_zero(insert_zero(k, t1), t2);
+    const T2 x = psi[base | b1], y = psi[base | b2];
+    psi[base | b1] = y;
+    psi[base | b2] = x;
+  }
+}
+
+cudaError_t launch_swap(qs_prec prec, void* amps, int ns, int t1, int t2, cudaStream_t st) {
+  const uint64_t npairs = 1ull << (ns - 2);
+  const unsigned g = grid_for(npairs, 256, num_sms() * 8);
+  if (prec == QS_C128)
+    k_swap<double2><<<g, 256, 0, st>>>(static_cast<double2*>(amps), npairs, t1, t2);
+  else
+    k_swap<float2><<<g, 256, 0, st>>>(static_cast<float2*>(amps), npairs, t1, t2);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gate1(qs_prec prec, void* amps, const Gate1Params& p, cudaStream_t st) {
   return prec == QS_C128 ? gate1_t<double>(amps, p, st) : gate1_t<float>(amps, p, st);
 }

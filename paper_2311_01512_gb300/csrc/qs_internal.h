@@ -178,6 +178,8 @@ struct BatchState {
 // Launchers.  Each returns cudaGetLastError() after the launch.  amps is the
 // state's device storage, ns its number of storage qubits.
 cudaError_t launch_gate1(qs_prec prec, void* amps, const Gate1Params& p, cudaStream_t st);
+// SWAP of storage qubits t1 < t2 (qs_gates.cu)
+cudaError_t launch_swap(qs_prec prec, void* amps, int ns, int t1, int t2, cudaStream_t st);
 cudaError_t launch_dense(qs_prec prec, void* amps, const DenseParams& p, cudaStream_t st);
 cudaError_t launch_diag(qs_prec prec, void* amps, const DiagParams& p, cudaStream_t st);
 cudaError_t launch_gadget(qs_prec prec, void* amps, const GadgetParams& p, cudaStream_t st);

@@ -67,29 +67,60 @@ __global__ void __launch_bounds__(256) k_expec_dm(const typename Cplx<R>::T* __r
 
 // <psi|H|psi> = sum_n h_n sum_i conj(alpha_i) (P_n psi)_i with
 // (P psi)_i = beta_{i'} alpha_{i'}, i' = i xor xy (Sec. "Pauli tensor",
-// Eq. (Pauli tensor amplitude update)).
+// Eq. (Pauli tensor amplitude update)), in one pass over the amplitudes with
+// every term evaluated at each amplitude read:
+//  * terms with xy = 0 (I/Z strings) are diagonal: their sum over the run of
+//    such terms is sum_i |alpha_i|^2 sum_n h_n (-1)^{popc(i & yz_n)};
+//  * terms that share xy (consecutive after the host's sort) share the
+//    partner load alpha_{i xor xy};
+//  * each Pauli string is Hermitian and h is real, so the contributions of i
+//    and i xor xy are complex conjugates: only indices with the highest bit
+//    of xy clear are visited, each counting 2 Re(...).  The imaginary part of
+//    the result is exactly zero.
 template <typename R>
 __global__ void __launch_bounds__(256) k_expec_sv(const typename Cplx<R>::T* __restrict__ psi, int nq,
                                                   const PauliTerm* __restrict__ terms, int nterms,
                                                   double2* __restrict__ partials) {
-  double sr = 0.0, si = 0.0;
+  double sr = 0.0;
   const uint64_t dim = 1ull << nq;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride) {
     const auto a = psi[i];
     const double ar = (double)a.x, ai = (double)a.y;
-    for (int n = 0; n < nterms; ++n) {
-      const PauliTerm t = terms[n];
-      const uint64_t ip = i ^ t.xy;
+    int n = 0;
+    while (n < nterms) {
+      const uint64_t xy = terms[n].xy;
+      if (xy == 0) {
+        double d = 0.0;
+        for (; n < nterms && terms[n].xy == 0; ++n) d += parity64(i & terms[n].yz) ? -terms[n].h : terms[n].h;
+        sr += d * (ar * ar + ai * ai);
+        continue;
+      }
+      const uint64_t hb = 1ull << (63 - __clzll((long long)xy));
+      if (i & hb) {
+        for (; n < nterms && terms[n].xy == xy; ++n) {
+        }
+        continue;
+      }
+      const uint64_t ip = i ^ xy;
       const auto b = psi[ip];
-      double2 v = rot_i(make_double2((double)b.x, (double)b.y), t.eta);
-      const double h = parity64(ip & t.yz) ? -t.h : t.h;
-      // conj(a) * v * h
-      sr += h * (ar * v.x + ai * v.y);
-      si += h * (ar * v.y - ai * v.x);
+      const double br = (double)b.x, bi = (double)b.y;
+      double cr = 0.0, ci = 0.0;                        // sum_n h_n eta_n (-1)^{popc(ip & yz_n)}
+      for (; n < nterms && terms[n].xy == xy; ++n) {
+        const double h = parity64(ip & terms[n].yz) ? -terms[n].h : terms[n].h;
+        switch (terms[n].eta) {
+          case 0: cr += h; break;
+          case 1: ci += h; break;
+          case 2: cr -= h; break;
+          default: ci -= h; break;
+        }
+      }
+      // 2 Re(conj(a) (c b))
+      const double qr = ar * br + ai * bi, qi = ar * bi - ai * br;
+      sr += 2.0 * (qr * cr - qi * ci);
     }
   }
-  const double2 s = block_sum(make_double2(sr, si));
+  const double2 s = block_sum(make_double2(sr, 0.0));
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 

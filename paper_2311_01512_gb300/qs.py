@@ -59,6 +59,7 @@ SIGNATURES = {
     "qs_apply_two_qubit_depolarising": (_I, [_P, _I, _I, _D]),
     "qs_apply_damping": (_I, [_P, _I, _D]),
     "qs_apply_pauli_channel": (_I, [_P, _I, _D, _D, _D]),
+    "qs_apply_swap": (_I, [_P, _I, _I]),
     "qs_partial_trace": (_I, [_P, _IP, _I, _P, ctypes.POINTER(_P)]),
     "qs_expec_pauli_sum": (_I, [_P, _IP, _DP, _I, _DP]),
     "qs_calc_norm_or_trace": (_I, [_P, _DP]),
@@ -242,6 +243,10 @@ def qs_apply_two_qubit_depolarising(h, t1, t2, p):
 
 def qs_apply_damping(h, t, p):
     _check(_lib.qs_apply_damping(h, int(t), float(p)), "qs_apply_damping")
+
+
+def qs_apply_swap(h, t1, t2):
+    _check(_lib.qs_apply_swap(h, int(t1), int(t2)), "qs_apply_swap")
 
 
 def qs_apply_pauli_channel(h, t, px, py, pz):
@@ -583,5 +588,7 @@ def apply_op(h, op):
         qs_apply_damping(h, op["targs"][0], op["p"])
     elif kind == "pauli_channel":
         qs_apply_pauli_channel(h, op["targs"][0], *op["probs"])
+    elif kind == "swap":
+        qs_apply_swap(h, op["targs"][0], op["targs"][1])
     else:
         raise ValueError("unknown op " + kind)

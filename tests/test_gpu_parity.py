@@ -97,6 +97,38 @@ def test_ctrl_multi_target_gate(qs, prec, nq, n, s):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("nq", [2, 7, 12])
+def test_swap(qs, prec, nq):
+    rng = np.random.default_rng(700 + nq)
+    psi = wl.random_statevector(nq, rng)
+    st = new_sv(qs, nq, prec, psi)
+    want = psi
+    pairs = [(0, nq - 1), (nq - 1, 0)] + [tuple(int(x) for x in rng.choice(nq, 2, replace=False)) for _ in range(4)]
+    for t1, t2 in pairs:
+        qs.qs_apply_swap(st.handle, t1, t2)
+        want = orc.apply_swap(want, t1, t2)
+    got = st.get_amps()
+    if prec == 0:
+        np.testing.assert_array_equal(got, want.astype(np.complex64))   # moved, not computed: exact
+    else:
+        np.testing.assert_array_equal(got, want)
+    if nq <= 7:
+        beta = rand_dm(nq, 3, rng)
+        dm = new_dm(qs, nq, prec, beta)
+        wantd = beta
+        for t1, t2 in pairs:
+            qs.qs_apply_swap(dm.handle, t1, t2)
+            wantd = orc.densmatr_apply_swap(wantd, t1, t2)
+        close(dm.get_amps(), wantd, prec)
+    with pytest.raises(qs.QSError) as ei:
+        qs.qs_apply_swap(st.handle, 1, 1)
+    assert "QS_ERR_DUP_QUBIT" in str(ei.value)
+    with pytest.raises(qs.QSError) as ei:
+        qs.qs_apply_swap(st.handle, 0, nq)
+    assert "QS_ERR_QUBIT_RANGE" in str(ei.value)
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("n", range(1, 7))
 def test_diagonal(qs, prec, n):
     rng = np.random.default_rng(50 + n)
@@ -141,6 +173,21 @@ def test_norm_and_statevector_expectation(qs, prec):
     got = qs.qs_expec_pauli_sum(st.handle, paulis, coeffs)
     want = orc.expec_pauli_sum_statevector(psi, paulis, coeffs)
     assert abs(got - want) < (1e-12 if prec else 1e-5)
+    # terms that share flip masks (grouped by the kernel), diagonal runs, masks whose
+    # highest bit is below and above a warp's index span, and repeated strings
+    base = wl.random_pauli_sum(nq, 6, rng)[0]
+    rows = [base[k % 6].copy() for k in range(30)]
+    for k, r in enumerate(rows):
+        flips = (r == 1) | (r == 2)
+        r[flips] = rng.choice([1, 2], size=int(flips.sum()))   # same X/Y pattern, other Y/X choice
+        r[~flips] = rng.choice([0, 3], size=int((~flips).sum()))
+    rows += [np.where(np.arange(nq) == q, 1, 0) for q in (0, 3, 4, 5, nq - 1)]
+    rows += [np.zeros(nq, dtype=np.int64), np.full(nq, 3)]
+    paulis2 = np.array(rows, dtype=np.int32)
+    coeffs2 = rng.standard_normal(len(rows))
+    got = qs.qs_expec_pauli_sum(st.handle, paulis2, coeffs2)
+    want = orc.expec_pauli_sum_statevector(psi, paulis2, coeffs2)
+    assert abs(got - want) < (1e-12 if prec else 1e-5) * np.abs(coeffs2).sum()
 
 
 @pytest.mark.parametrize("prec", PRECS)

@@ -302,6 +302,37 @@ def test_densmatr_unitary_and_gadget(seed):
     np.testing.assert_allclose(got, df @ rho @ df.conj().T, atol=1e-13)
 
 
+SWAP4 = np.array([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]], dtype=np.complex128)
+XMAT = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+
+
+def test_swap_pins():
+    """SWAP (Sec. "Swap gate") against its 4x4 matrix as a two-target gate, three
+    CNOTs, an explicit basis-state example, the Kronecker operator, and S rho S
+    on a density matrix."""
+    rng = np.random.default_rng(61)
+    nq = 5
+    # worked example: |0b00001> with t1 = 0, t2 = 4 becomes |0b10000>
+    e = np.zeros(1 << nq, dtype=np.complex128)
+    e[0b00001] = 1.0
+    out = orc.apply_swap(e, 0, 4)
+    assert out[0b10000] == 1.0 and np.count_nonzero(out) == 1
+    psi = wl.random_statevector(nq, rng)
+    for t1, t2 in ((0, 4), (3, 1), (2, 3)):
+        got = orc.apply_swap(psi, t1, t2)
+        np.testing.assert_allclose(got, orc.apply_ctrl_multi_target(psi, [], [t1, t2], SWAP4), atol=0)
+        cn = orc.apply_ctrl_multi_target(psi, [t1], [t2], XMAT)
+        cn = orc.apply_ctrl_multi_target(cn, [t2], [t1], XMAT)
+        cn = orc.apply_ctrl_multi_target(cn, [t1], [t2], XMAT)
+        np.testing.assert_allclose(got, cn, atol=0)
+        np.testing.assert_allclose(got, full_operator(nq, [], [t1, t2], SWAP4) @ psi, atol=1e-15)
+        np.testing.assert_allclose(orc.apply_swap(got, t2, t1), psi, atol=0)
+    rho = random_density(4, 3, rng)
+    sw = full_operator(4, [], [0, 2], SWAP4)
+    np.testing.assert_allclose(choi_to_mat(orc.densmatr_apply_swap(mat_to_choi(rho), 0, 2)), sw @ rho @ sw,
+                               atol=1e-15)
+
+
 def test_superoperator_of_one_unitary_is_two_pass_unitary():
     rng = np.random.default_rng(5)
     nq = 3
