@@ -630,3 +630,12 @@ def sample_pauli_gadget(get, targs, paulis, theta, out_idx):
     ip = idx ^ xy
     beta = np.where(_v_parity(ip & yz) == 1, -eta, eta)
     return np.cos(phi) * get(idx) + 1j * np.sin(phi) * beta * get(ip)
+
+
+def sample_swap(get, t1, t2, out_idx):
+    """New amplitudes at out_idx after SWAP of qubits t1, t2 (Sec. "Swap
+    gate"): alpha_{i with both bits flipped} where the two bits differ."""
+    idx = np.asarray(out_idx, dtype=np.int64)
+    differ = ((idx >> t1) & 1) != ((idx >> t2) & 1)
+    src = np.where(differ, idx ^ ((1 << t1) | (1 << t2)), idx)
+    return get(src)

@@ -118,3 +118,64 @@ def test_large_density_matrix_properties_at_15_qubits():
     assert abs(e.imag) < 1e-12
     red.close()
     rho.close()
+
+
+def test_indices_beyond_32_bits_complex64_33_qubits():
+    """A 33-qubit complex64 state (64 GiB), so that amplitude indices pass
+    2^32: one-target, dense (tensor-core) and 2-target gates, a diagonal, a
+    gadget and a SWAP, each touching qubit 32, with outputs sampled at random
+    indices and at 0, 2^32 - 1, 2^32, 2^32 + 1 and 2^33 - 1, against the
+    oracle evaluated one amplitude at a time."""
+    import torch
+    from paper_2311_01512_gb300 import qs
+    from paper_2311_01512_gb300 import workloads as wl
+    nq = 33
+    device = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=device)
+    g = torch.Generator(device=device)
+    g.manual_seed(2311015133)
+    with torch.cuda.stream(stream):
+        psi = torch.randn(1 << nq, dtype=torch.complex64, device=device, generator=g)
+        psi /= torch.linalg.vector_norm(psi)
+    stream.synchronize()
+    st = qs.State(nq, prec=qs.QS_C64, stream=stream, storage=psi)
+    rng = np.random.default_rng(33)
+    ops = [
+        {"op": "unitary", "ctrls": [], "targs": [32], "mat": wl.haar_unitary(2, rng)},
+        {"op": "unitary", "ctrls": [31], "targs": [32, 5, 17], "mat": wl.haar_unitary(8, rng)},
+        {"op": "unitary", "ctrls": [], "targs": [0, 32], "mat": wl.haar_unitary(4, rng)},
+        {"op": "diagonal", "targs": [32, 0, 20], "diag": np.exp(1j * rng.uniform(0, 2 * np.pi, 8))},
+        {"op": "gadget", "targs": [32, 1, 31], "paulis": [1, 2, 3], "theta": 0.7},
+        {"op": "swap", "targs": [32, 3]},
+    ]
+    extremes = np.array([0, (1 << 32) - 1, 1 << 32, (1 << 32) + 1, (1 << nq) - 1], dtype=np.int64)
+    for op in ops:
+        out_idx = np.concatenate([extremes, rng.choice(1 << nq, 96, replace=False)])
+        if op["op"] == "swap":
+            t1, t2 = op["targs"]
+            need = np.array(sorted(set(out_idx.tolist()) | {int(i) ^ ((1 << t1) | (1 << t2)) for i in out_idx}),
+                            dtype=np.int64)
+        else:
+            need = np.array(_partners(op, out_idx), dtype=np.int64)
+        with torch.cuda.stream(stream):
+            old = psi[torch.from_numpy(need).to(device)].cpu().numpy().astype(np.complex128)
+        lookup = dict(zip(need.tolist(), old))
+        get = lambda ix: np.array([lookup[int(i)] for i in ix], dtype=np.complex128)
+        qs.apply_op(st.handle, op)
+        qs.qs_synchronize(st.handle)
+        with torch.cuda.stream(stream):
+            new = psi[torch.from_numpy(out_idx).to(device)].cpu().numpy().astype(np.complex128)
+        if op["op"] == "unitary":
+            want = orc.sample_ctrl_multi_target(get, op["ctrls"], op["targs"], op["mat"], out_idx)
+        elif op["op"] == "diagonal":
+            want = orc.sample_diagonal(get, op["targs"], op["diag"], out_idx)
+        elif op["op"] == "gadget":
+            want = orc.sample_pauli_gadget(get, op["targs"], op["paulis"], op["theta"], out_idx)
+        else:
+            want = orc.sample_swap(get, op["targs"][0], op["targs"][1], out_idx)
+        err = float(np.max(np.abs(new - want)))
+        # complex64 storage; 3xTF32 and FP32 arithmetic keep ~2^-21 of the amplitudes
+        assert err <= 2.0 ** -19 * float(np.max(np.abs(old))), (op["op"], op["targs"], err)
+    st.close()
+    del psi
+    torch.cuda.empty_cache()

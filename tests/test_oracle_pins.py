@@ -327,6 +327,9 @@ def test_swap_pins():
         np.testing.assert_allclose(got, cn, atol=0)
         np.testing.assert_allclose(got, full_operator(nq, [], [t1, t2], SWAP4) @ psi, atol=1e-15)
         np.testing.assert_allclose(orc.apply_swap(got, t2, t1), psi, atol=0)
+    got = orc.apply_swap(psi, 1, 4)
+    idx = np.arange(1 << nq)
+    np.testing.assert_array_equal(orc.sample_swap(lambda ix: psi[np.asarray(ix)], 1, 4, idx), got)
     rho = random_density(4, 3, rng)
     sw = full_operator(4, [], [0, 2], SWAP4)
     np.testing.assert_allclose(choi_to_mat(orc.densmatr_apply_swap(mat_to_choi(rho), 0, 2)), sw @ rho @ sw,
