@@ -160,17 +160,18 @@ QS_HD double join(df v) {
   return w2d(dh, dl);
 }
 
-// Exact float -> double by bit construction (no FP64 conversion instruction):
-// zeros and FP32 subnormals (|f| < 2^-126) become zero.
+// Exact float -> double by bit construction (no FP64 conversion instruction).
+// The arithmetic shift keeps the sign in bit 31 and clears bits 28..30, so
+// the high word is sign | (exponent - 127 + 1023) << 20 | significand >> 3
+// once the exponent bias 896 << 20 is added; zeros (exponent field 0) get no
+// bias and stay signed zeros.  FP32 subnormals (|f| < 2^-126) come out as
+// double subnormals below 2^-1022 instead of their value: an absolute error
+// under 2^-126.
 QS_HD double to_double(float f) {
   const uint32_t b = f2u(f);
-  uint32_t dh = (((b & 0x7FFFFFFFu) >> 3) + (896u << 20)) | (b & 0x80000000u);
-  uint32_t dl = b << 29;
-  if ((b & 0x7F800000u) == 0) {
-    dh = b & 0x80000000u;
-    dl = 0;
-  }
-  return w2d(dh, dl);
+  const uint32_t bias = (b & 0x7F800000u) ? (896u << 20) : 0u;
+  const uint32_t dh = ((uint32_t)((int32_t)b >> 3) & 0x8FFFFFFFu) + bias;
+  return w2d(dh, b << 29);
 }
 
 // Constants (gate-matrix entries) are split exactly on the host: h = (float)x,

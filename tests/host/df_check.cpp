@@ -68,13 +68,26 @@ int main() {
     const df at = qsdf::split(std::ldexp(1.5, -102));
     if ((double)at.h + (double)at.l != std::ldexp(1.5, -102)) fail("split 2^-102", at.h, 0);
   }
-  // 3b. to_double is exact for normal floats, zero for zeros and subnormals
+  // 3b. to_double is exact for normal floats and signed zeros; FP32 subnormals
+  // land within 2^-126 (below the documented range)
   for (int i = 0; i < 1000000; ++i) {
     const float f = (float)std::ldexp(u(rng), ex(rng));
-    const double want = std::fabs(f) < std::ldexp(1.0f, -126) ? 0.0 : (double)f;
-    if (qsdf::to_double(f) != want) fail("to_double", qsdf::to_double(f), want);
+    const double got = qsdf::to_double(f);
+    if (std::fabs(f) >= std::ldexp(1.0f, -126)) {
+      if (got != (double)f) fail("to_double", got, (double)f);
+    } else if (std::fabs(got - (double)f) > std::ldexp(1.0, -126)) {
+      fail("to_double subnormal", got, (double)f);
+    }
   }
+  for (uint32_t bits : {0x00000001u, 0x007FFFFFu, 0x80000001u, 0x807FFFFFu, 0x00400000u}) {
+    float f;
+    std::memcpy(&f, &bits, 4);
+    if (std::fabs(qsdf::to_double(f)) > std::ldexp(1.0, -126)) fail("to_double subnormal edge", qsdf::to_double(f), 0);
+  }
+  if (qsdf::to_double(0.0f) != 0.0 || std::signbit(qsdf::to_double(0.0f))) fail("to_double +0", 0, 0);
   if (qsdf::to_double(-0.0f) != 0.0 || !std::signbit(qsdf::to_double(-0.0f))) fail("to_double -0", 0, 0);
+  for (float f : {1.0f, -1.0f, 3.4028235e38f, -3.4028235e38f, 1.17549435e-38f, -1.17549435e-38f})
+    if (qsdf::to_double(f) != (double)f) fail("to_double edge", qsdf::to_double(f), (double)f);
   // 4. dot products of length 2..64 against long double: error <= 16 * 2^-46 * sum |c v|
   for (int i = 0; i < 300000; ++i) {
     const int len = 2 + (i % 63);
