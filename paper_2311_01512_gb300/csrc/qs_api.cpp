@@ -416,6 +416,28 @@ qs_status qs_apply_ctrl_multi_target(qs_state* s, const int* ctrls, int nctrl, c
     st = ring_put(s, mat, mat_bytes, &dmat, &slot);
     if (st != QS_OK) return st;
   }
+  // Density matrix, uncontrolled two-target unitary on the tensor-core path:
+  // U on t and U^* on t + N in one 4-target pass of conj(U) (x) U, the
+  // superoperator of the one-operator Kraus map {U} (Sec. "Kraus map"), which
+  // reads and writes the Choi vector once instead of twice.
+  const bool tc = s->tensor_cores && (s->prec == QS_C64 || s->arith == QS_ARITH_DF);
+  if (s->is_density && nctrl == 0 && ntarg == 2 && tc) {
+    void* dsup = nullptr;
+    int slot_s = -1;
+    st = ring_take(s, &dsup, &slot_s);
+    if (st == QS_OK)
+      st = cuda_status(qsk::launch_superop(static_cast<const double*>(dmat), 1, 2, static_cast<double*>(dsup),
+                                           s->stream));
+    if (st == QS_OK) {
+      std::vector<int> t4(t);
+      for (int q = 0; q < 2; ++q) t4.push_back(t[q] + s->nq);
+      st = gate_pass(s, {}, t4, nullptr, dsup, 0);
+    }
+    const qs_status a = slot_s >= 0 ? ring_done(s, slot_s) : QS_OK;
+    const qs_status b = ring_done(s, slot);
+    if (st == QS_OK) st = a != QS_OK ? a : b;
+    return st;
+  }
   st = gate_pass(s, c, t, mat, dmat, 0);
   if (st == QS_OK && s->is_density) {
     // U^* on the same qubits shifted by N (Eq. (unitary on a vectorised density matrix))
