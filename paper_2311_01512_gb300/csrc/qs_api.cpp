@@ -680,16 +680,29 @@ qs_status qs_expec_pauli_sum(const qs_state* cs, const int* paulis, const double
   if (!s->is_density)
     std::stable_sort(terms.begin(), terms.end(),
                      [](const qsk::PauliTerm& x, const qsk::PauliTerm& y) { return x.xy < y.xy; });
-  for (int first = 0; first < num_terms; first += qsk::kTermChunk) {
-    const int cnt = std::min(qsk::kTermChunk, num_terms - first);
+  // statevector: the leading run of diagonal terms (xy = 0 sorts first) goes to
+  // the Walsh-Hadamard kernel when it is long enough to pay for the transform
+  int ndiag = 0;
+  if (!s->is_density)
+    while (ndiag < num_terms && terms[(size_t)ndiag].xy == 0) ++ndiag;
+  if (s->nq < 5 || ndiag < 8) ndiag = 0;
+  for (int first = 0; first < num_terms;) {
+    const int lim = first < ndiag ? ndiag : num_terms;
+    const int cnt = std::min(qsk::kTermChunk, lim - first);
     const void* dterms = nullptr;
     int slot = -1;
     qs_status st = ring_put(s, terms.data() + first, sizeof(qsk::PauliTerm) * (size_t)cnt, &dterms, &slot);
     if (st != QS_OK) return st;
     const auto* dt = static_cast<const qsk::PauliTerm*>(dterms);
-    cudaError_t e = s->is_density ? qsk::launch_expec_dm(s->prec, s->amps, s->nq, dt, cnt, s->d_partials, s->stream)
-                                  : qsk::launch_expec_sv(s->prec, s->amps, s->nq, dt, cnt, s->d_partials, s->stream);
+    cudaError_t e;
+    if (s->is_density)
+      e = qsk::launch_expec_dm(s->prec, s->amps, s->nq, dt, cnt, s->d_partials, s->stream);
+    else if (first < ndiag)
+      e = qsk::launch_expec_sv_diag(s->prec, s->amps, s->nq, dt, cnt, s->d_partials, s->stream);
+    else
+      e = qsk::launch_expec_sv(s->prec, s->amps, s->nq, dt, cnt, s->d_partials, s->stream);
     if (e == cudaSuccess) e = qsk::launch_reduce_final(s->d_partials, s->d_result, first > 0, s->stream);
+    first += cnt;
     st = ring_done(s, slot);
     if (e != cudaSuccess) return QS_ERR_CUDA;
     if (st != QS_OK) return st;

@@ -222,6 +222,9 @@ cudaError_t launch_expec_dm(qs_prec prec, const void* amps, int nq, const PauliT
                             int nterms, double2* partials, cudaStream_t st);
 cudaError_t launch_expec_sv(qs_prec prec, const void* amps, int nq, const PauliTerm* terms,
                             int nterms, double2* partials, cudaStream_t st);
+// the diagonal (I/Z) terms of a statevector Pauli sum by warp Walsh-Hadamard transforms; N >= 5
+cudaError_t launch_expec_sv_diag(qs_prec prec, const void* amps, int nq, const PauliTerm* terms, int nterms,
+                                 double2* partials, cudaStream_t st);
 cudaError_t launch_reduce_final(const double2* partials, double2* result, int accumulate,
                                 cudaStream_t st);
 

@@ -124,6 +124,59 @@ __global__ void __launch_bounds__(256) k_expec_sv(const typename Cplx<R>::T* __r
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// The diagonal (I/Z) terms of a statevector Pauli sum, many at a time:
+// sum_n h_n sum_i |alpha_i|^2 (-1)^{popc(i & z_n)}.  A warp holds 32
+// consecutive amplitudes i = base + m; a Walsh-Hadamard transform over its
+// lanes gives W_j = sum_m |alpha_{base+m}|^2 (-1)^{popc(j & m)} in lane j, so
+// the tile's share of term n is (-1)^{popc(base & z_n)} W_{z_n mod 32}: five
+// butterfly steps per amplitude and one multiply-add per 32 terms replace one
+// add per term.  Needs N >= 5 (whole warps of amplitudes).
+template <typename R>
+__global__ void __launch_bounds__(256) k_expec_sv_diag(const typename Cplx<R>::T* __restrict__ psi, int nq,
+                                                       const PauliTerm* __restrict__ terms, int nterms,
+                                                       double2* __restrict__ partials) {
+  const int lane = threadIdx.x & 31;
+  double acc = 0.0;
+  const uint64_t dim = 1ull << nq;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  // dim and stride are multiples of 32: every lane of a warp runs the same iterations
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride) {
+    const auto a = psi[i];
+    double w = (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+#pragma unroll
+    for (int b = 1; b < 32; b <<= 1) {
+      const double o = __shfl_xor_sync(0xFFFFFFFFu, w, b);
+      w = (lane & b) ? (o - w) : (w + o);
+    }
+    const uint64_t base = i & ~31ull;
+    for (int n0 = 0; n0 < nterms; n0 += 32) {
+      const int n = n0 + lane;
+      uint64_t z = 0;
+      double h = 0.0;
+      if (n < nterms) {
+        z = terms[n].yz;
+        h = terms[n].h;
+      }
+      const double wz = __shfl_sync(0xFFFFFFFFu, w, (int)(z & 31u));
+      acc += (parity64(base & z) ? -h : h) * wz;
+    }
+  }
+  const double2 s = block_sum(make_double2(acc, 0.0));
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+cudaError_t launch_expec_sv_diag(qs_prec prec, const void* amps, int nq, const PauliTerm* terms, int nterms,
+                                 double2* partials, cudaStream_t st) {
+  if (nq < 5) return cudaErrorInvalidValue;
+  if (prec == QS_C128)
+    k_expec_sv_diag<double><<<kReduceBlocks, 256, 0, st>>>(static_cast<const double2*>(amps), nq, terms, nterms,
+                                                           partials);
+  else
+    k_expec_sv_diag<float><<<kReduceBlocks, 256, 0, st>>>(static_cast<const float2*>(amps), nq, terms, nterms,
+                                                          partials);
+  return cudaGetLastError();
+}
+
 // Stage two: one block of 1024 threads; thread j adds partials j, j + 1024, ...
 __global__ void __launch_bounds__(1024) k_reduce_final(const double2* __restrict__ partials, int n,
                                                        double2* __restrict__ result, int accumulate) {

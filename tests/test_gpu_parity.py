@@ -191,6 +191,30 @@ def test_norm_and_statevector_expectation(qs, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("nq", [4, 5, 6, 11])
+def test_statevector_expectation_many_diagonal_terms(qs, prec, nq):
+    """Runs of 40 I/Z strings take the warp Walsh-Hadamard path (N >= 5), with
+    masks on every bit including the highest; mixed in are 10 other strings."""
+    rng = np.random.default_rng(90 + nq)
+    psi = wl.random_statevector(nq, rng)
+    st = new_sv(qs, nq, prec, psi)
+    zs = np.where(rng.random((40, nq)) < 0.4, 3, 0).astype(np.int32)
+    zs[0, :] = 0
+    zs[1, :] = 3
+    zs[2, :] = 0
+    zs[2, nq - 1] = 3
+    others = wl.random_pauli_sum(nq, 10, rng)[0]
+    paulis = np.concatenate([zs, others])
+    coeffs = rng.standard_normal(len(paulis))
+    got = qs.qs_expec_pauli_sum(st.handle, paulis, coeffs)
+    want = orc.expec_pauli_sum_statevector(psi, paulis, coeffs)
+    assert abs(got - want) < (1e-12 if prec else 1e-5) * np.abs(coeffs).sum()
+    got_d = qs.qs_expec_pauli_sum(st.handle, zs, coeffs[:40])
+    want_d = orc.expec_pauli_sum_statevector(psi, zs, coeffs[:40])
+    assert abs(got_d - want_d) < (1e-12 if prec else 1e-5) * np.abs(coeffs[:40]).sum()
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_statevector_circuit(qs, prec):
     """500 seeded operations of the 30-qubit workload's mix at 14 qubits."""
     rng = wl.rng_for("sv-circuit-14")
