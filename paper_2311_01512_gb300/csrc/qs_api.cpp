@@ -179,7 +179,7 @@ qs_status gate_pass(qs_state* s, const std::vector<int>& ctrls, const std::vecto
   // two targets run on the three-target tensor-core kernels with an identity
   // on the lowest free qubit
   const bool tc_n = n <= 5 && (n >= 3 || (n == 2 && nfree >= 1));
-  const bool tc64 = s->prec == QS_C64 && s->tensor_cores && tc_n;
+  const bool tc64 = s->prec == QS_C64 && s->tensor_cores && (tc_n || n == 6);   // 6: bf16x3 slices
   const bool tc128 = s->prec == QS_C128 && s->arith == QS_ARITH_DF && s->tensor_cores && tc_n;
   if (tc64 || tc128) {
     std::vector<int> kt(targs);

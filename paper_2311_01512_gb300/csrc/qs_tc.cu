@@ -257,6 +257,196 @@ __global__ void __launch_bounds__(THREADS, 1) k_dense_tc(float2* __restrict__ ps
   if (warp == 0) tmem_dealloc(tmem, TCOLS);
 }
 
+// ---------------------------------------------------------------------------
+// Six targets (K = N = 128).  3xTF32 operands would need 256 KB of shared
+// memory, so A and B are cut into three bf16 slices each instead: x = x0 + x1
+// + x2, each slice the bf16 rounding of what the previous ones left (8
+// significant bits each, exact remainders in FP32).  The six products with
+// s + t <= 2 accumulate in FP32 in tensor memory (kind::f16, bf16 inputs); the
+// dropped products are below 2^-26 of |A| |B|.  The leading product x0 y0 has
+// an accumulator of its own and the five corrections share a second one, 2^-8
+// smaller, so the tensor cores' accumulation rounding acts mostly on eight
+// steps of the leading sum; the epilogue adds the two.  Same mapping and
+// bounded waits as above; one buffer of slices (192 KB), one CTA of 512
+// threads per SM.
+// ---------------------------------------------------------------------------
+namespace {
+__device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+// three packed (re, im) bf16 slices of one amplitude
+__device__ __forceinline__ void bf16_slices(float2 v, uint32_t* out) {
+  float r = v.x, i = v.y;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    const uint32_t w = bf16x2_rn(r, i);
+    out[s] = w;
+    r -= __uint_as_float(w << 16);
+    i -= __uint_as_float(w & 0xFFFF0000u);
+  }
+}
+}  // namespace
+
+__global__ void __launch_bounds__(512, 1) k_dense_tc6(float2* __restrict__ psi, const __grid_constant__ TcParams p) {
+  constexpr int NT = 6, D = 64, K = 128, N = 128, THREADS = 512;
+  constexpr int CG = THREADS / kRows;        // 4
+  constexpr int EPT = D / CG;                // 16 amplitudes per thread
+  constexpr int CPW = 2 * EPT;               // 32 accumulator columns per thread
+  constexpr int SL = kRows * K * 2;          // one bf16 slice of A (32 KB)
+  constexpr int SB = N * K * 2;              // one bf16 slice of B (32 KB)
+  constexpr uint32_t TCOLS = 256;             // leading product | corrections
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* a_sl = smem;                                           // 3 x SL
+  unsigned char* b_sl = a_sl + 3 * SL;                                  // 3 x SB
+  uint64_t* toff = reinterpret_cast<uint64_t*>(b_sl + 3 * SB);          // D
+  uint64_t* rowoff = toff + D;                                          // kRows
+  uint64_t* tile_base = rowoff + kRows;                                 // 2
+  uint64_t* mbar = tile_base + 2;                                       // 1 (+1 pad)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < N * K; e += THREADS) {
+    const int n = e / K, k = e % K;
+    const int j = n >> 1, c = n & 1, l = k >> 1, cp = k & 1;
+    const double mr = p.mat[2 * (j * D + l)];
+    const double mi = p.conj ? -p.mat[2 * (j * D + l) + 1] : p.mat[2 * (j * D + l) + 1];
+    float v = (float)((c == 0) ? (cp == 0 ? mr : -mi) : (cp == 0 ? mi : mr));
+    const uint32_t off = canon_off16(n, k, K);
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) {
+      const uint32_t w = bf16x2_rn(v, 0.0f);
+      *reinterpret_cast<uint16_t*>(b_sl + sl * SB + off) = (uint16_t)(w & 0xFFFFu);
+      v -= __uint_as_float(w << 16);
+    }
+  }
+  for (int j = tid; j < D; j += THREADS) {
+    uint64_t off = 0;
+#pragma unroll
+    for (int q = 0; q < NT; ++q)
+      if ((j >> q) & 1) off |= 1ull << p.tpos[q];
+    toff[j] = off;
+  }
+  const int row_bits = p.tile_bits - NT;
+  for (int g = tid; g < kRows; g += THREADS) {
+    uint64_t off = 0;
+    for (int b = 0, r = 0; b < p.tile_bits; ++b)
+      if (!((p.tslot_mask >> b) & 1)) {
+        if ((g >> r) & 1) off |= 1ull << p.P[b];
+        ++r;
+      }
+    rowoff[g] = off;
+  }
+  if (tid == 0) {
+    tile_base[0] = insert_zeros(blockIdx.x, p.hi_ins, p.nhi) | p.ctrl_mask;
+    if (blockIdx.x + gridDim.x < p.ntiles)
+      tile_base[1] = insert_zeros(blockIdx.x + gridDim.x, p.hi_ins, p.nhi) | p.ctrl_mask;
+    mbar_init(mbar, 1);
+  }
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, TCOLS);
+    tmem_relinquish();
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = idesc_bf16(kRows, N);
+  constexpr uint32_t sbo = K * 16;
+
+  const int g = 32 * (warp & 3) + lane;
+  const int cg = warp >> 2;
+  const int l0 = cg * EPT;
+  const bool row_ok = g < (1 << row_bits);
+  const uint64_t roff = rowoff[g];
+  const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
+  const int helper = kRows;
+
+  float2 R[EPT];
+  auto load_tile = [&](uint64_t base) {
+    const uint64_t rb = base | roff;
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) R[i] = row_ok ? psi[rb | toff[l0 + i]] : make_float2(0.0f, 0.0f);
+  };
+
+  load_tile(tile_base[0]);
+  uint32_t phase = 0;
+  bool failed = false;
+  int it = 0;
+  for (uint64_t c = blockIdx.x; c < p.ntiles; c += gridDim.x, ++it) {
+    const int par = it & 1;
+    const uint64_t rb = tile_base[par] | roff;
+    const bool has_next = c + gridDim.x < p.ntiles;
+#pragma unroll
+    for (int i = 0; i < EPT; i += 4) {
+      uint32_t w[4][3];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) bf16_slices(R[i + e], w[e]);
+      const uint32_t off = canon_off16(g, 2 * (l0 + i), K);
+#pragma unroll
+      for (int sl = 0; sl < 3; ++sl)
+        *reinterpret_cast<uint4*>(a_sl + sl * SL + off) = make_uint4(w[0][sl], w[1][sl], w[2][sl], w[3][sl]);
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      fence_after_sync();
+      const uint64_t da = smem_desc(smem_u32(a_sl), 128, sbo), db = smem_desc(smem_u32(b_sl), 128, sbo);
+      // products (s, t) with s + t <= 2: (0, 0) into columns 0..127, the rest into 128..255
+      constexpr int PS[6] = {0, 0, 1, 0, 1, 2}, PT[6] = {0, 1, 0, 2, 1, 0};
+#pragma unroll
+      for (int pr = 0; pr < 6; ++pr)
+#pragma unroll
+        for (int kk = 0; kk < K / 16; ++kk)
+          mma_bf16(tmem + (pr == 0 ? 0u : (uint32_t)N), da + ((PS[pr] * SL + kk * 256) >> 4),
+                   db + ((PT[pr] * SB + kk * 256) >> 4), idesc, (pr > 1 || kk != 0) ? 1u : 0u);
+      mma_commit(mbar);
+    }
+    if (has_next) load_tile(tile_base[par ^ 1]);
+    const bool timed_out = tc_wait(mbar, phase);
+    phase ^= 1u;
+    fence_after_sync();
+#pragma unroll
+    for (int cc = 0; cc < CPW; cc += 8) {
+      float v[8], w[8];
+      tmem_ld8(tmem + lane_addr + (uint32_t)(cg * CPW + cc), v);
+      tmem_ld8(tmem + lane_addr + (uint32_t)(N + cg * CPW + cc), w);
+      tmem_wait_ld();
+      if (row_ok) {
+#pragma unroll
+        for (int q = 0; q < 8; q += 2)
+          psi[rb | toff[l0 + ((cc + q) >> 1)]] = make_float2(v[q] + w[q], v[q + 1] + w[q + 1]);
+      }
+    }
+    if (tid == helper && c + 2 * (uint64_t)gridDim.x < p.ntiles)
+      tile_base[par] = insert_zeros(c + 2 * (uint64_t)gridDim.x, p.hi_ins, p.nhi) | p.ctrl_mask;
+    fence_before_sync();
+    failed = __syncthreads_or(timed_out) != 0;
+    fence_after_sync();
+    if (failed) break;
+  }
+  if (failed && tid == 0) atomicExch(p.err, 1);
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, TCOLS);
+}
+
+static cudaError_t dense_tc6(void* amps, const TcParams& p, cudaStream_t st) {
+  constexpr size_t smem = 3 * (size_t)kRows * 128 * 2 + 3 * (size_t)128 * 128 * 2 + 8 * (64 + kRows + 4) + 16;
+  static_assert(smem <= 227 * 1024, "shared memory");
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(k_dense_tc6, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  const uint64_t maxb = (uint64_t)num_sms();
+  const unsigned g = (unsigned)(p.ntiles < maxb ? p.ntiles : maxb);
+  k_dense_tc6<<<g, 512, smem, st>>>(static_cast<float2*>(amps), p);
+  return cudaGetLastError();
+}
+
 template <int NT, int THREADS, int NBUF, int CTAS>
 static cudaError_t dense_tc_nt(void* amps, const TcParams& p, cudaStream_t st) {
   constexpr int D = 1 << NT, K = 2 * D, N = 2 * D;
@@ -281,6 +471,7 @@ cudaError_t launch_dense_tc(void* amps, const TcParams& p, cudaStream_t st) {
     case 3: return dense_tc_nt<3, 256, 2, 3>(amps, p, st);
     case 4: return dense_tc_nt<4, 512, 2, 2>(amps, p, st);
     case 5: return dense_tc_nt<5, 512, 2, 1>(amps, p, st);
+    case 6: return dense_tc6(amps, p, st);
     default: return cudaErrorInvalidValue;
   }
 }

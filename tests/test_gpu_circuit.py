@@ -45,13 +45,15 @@ def test_statevector_circuit_fused_c128(qs, width):
     assert float(np.max(np.abs(got - want))) <= 0.3e-12
 
 
-def test_unitary_circuit_fused_c64_tensor_cores(qs):
+@pytest.mark.parametrize("width", [5, 6])
+def test_unitary_circuit_fused_c64_tensor_cores(qs, width):
+    """Width 6 puts the 6-target blocks on the bf16-slice kernel."""
     rng = wl.rng_for("fuse-c64")
     nq = 14
     psi = wl.random_statevector(nq, rng)
     ops = wl.unitary_circuit(nq, 200, rng)
     want = orc.run_ops(psi, ops, is_density=False)
-    got_fused, stats = run_plan(qs, nq, False, 0, psi.astype(np.complex64), ops, qs.QS_PLAN_GREEDY, 5)
+    got_fused, stats = run_plan(qs, nq, False, 0, psi.astype(np.complex64), ops, qs.QS_PLAN_GREEDY, width)
     got_plain, _ = run_plan(qs, nq, False, 0, psi.astype(np.complex64), ops, qs.QS_PLAN_NONE, 1)
     scale = float(np.max(np.abs(want)))
     err_f = float(np.max(np.abs(got_fused - want)))
@@ -98,17 +100,17 @@ def test_fused_c64_matches_per_gate_c128_at_22_qubits(qs):
     psi = wl.random_statevector(nq, rng)
     ops = wl.unitary_circuit(nq, 300, rng)
     ref, _ = run_plan(qs, nq, False, 1, psi, ops, qs.QS_PLAN_NONE, 1)
-    for plan in ("greedy", "cost"):
+    for plan, width in (("greedy", 5), ("greedy", 6), ("cost", 5), ("cost", 6)):
         circ = qs.Circuit(nq, ops)
         st = qs.State(nq, prec=0)
         st.set_amps(psi.astype(np.complex64))
         if plan == "greedy":
-            circ.plan(qs.QS_PLAN_GREEDY, 5)
+            circ.plan(qs.QS_PLAN_GREEDY, width)
         else:
             model, _ = costmodel.load()
-            circ.plan_cost(model, st.handle, max_block_qubits=5, window=24)
+            circ.plan_cost(model, st.handle, max_block_qubits=width, window=24)
         circ.apply(st.handle)
         qs.qs_synchronize(st.handle)
         got = st.get_amps().astype(np.complex128)
         fid = abs(np.vdot(ref, got)) ** 2 / (np.vdot(ref, ref).real * np.vdot(got, got).real)
-        assert 1.0 - fid <= 1e-6, (plan, 1.0 - fid)
+        assert 1.0 - fid <= 1e-6, (plan, width, 1.0 - fid)

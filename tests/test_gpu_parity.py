@@ -440,7 +440,8 @@ def test_validation_errors(qs):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("nq,n,s", [(5, 5, 0), (8, 3, 2), (10, 4, 0), (13, 5, 2), (16, 3, 0), (16, 5, 1),
-                                     (3, 2, 0), (4, 2, 1), (11, 2, 2), (17, 4, 1)])
+                                     (3, 2, 0), (4, 2, 1), (11, 2, 2), (17, 4, 1),
+                                     (6, 6, 0), (9, 6, 1), (14, 6, 0), (18, 6, 2)])
 @pytest.mark.parametrize("place", ["random", "lowest", "highest"])
 def test_tensor_core_gate_matches_cuda_cores(qs, nq, n, s, place):
     rng = np.random.default_rng(600 + 10 * nq + n + s + 7 * len(place))
