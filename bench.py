@@ -50,6 +50,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-fused", action="store_true", help="skip the fused tensor-core comparison")
     ap.add_argument("--fused-qubits", type=int, default=32,
                     help="qubits of the fused comparison (32: the complex64 fused workload's size)")
+    ap.add_argument("--fused-max-block", type=int, default=6,
+                    help="widest fused block the cost-model planner may form (6 on complex64; complex128 stops at 5)")
     ap.add_argument("--fused-prec", choices=("c64", "c128"), default="c64",
                     help="precision of the fused form: complex64 (3xTF32 blocks) or complex128 (bf16 integer slices)")
     ap.add_argument("--detail", default="", help="write per-kernel-family statistics to this JSON file")
@@ -489,7 +491,9 @@ def fused_comparison(args, device):
     sf = qs.State(nq, prec=qs.QS_C64 if c64 else qs.QS_C128, stream=stream, storage=tf)
     model, meta = costmodel.load()
     circf = qs.Circuit(nq, ops)
-    plan = circf.plan_cost(model, sf.handle, max_block_qubits=5, window=24)
+    width = min(args.fused_max_block, 6 if c64 else 5)
+    plan = circf.plan_cost(model, sf.handle, max_block_qubits=width, window=24)
+    plan["max_block_qubits"] = width
     out["fused_ms"] = timed(lambda: circf.apply(sf.handle))
     out["plan"] = plan
     out["costmodel_holdout_median_time_error"] = meta.get("holdout_median_abs_rel_time_error")
