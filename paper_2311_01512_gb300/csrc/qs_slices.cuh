@@ -9,7 +9,9 @@
 //   V = sum_{s=0..6} d_s 2^(42 - 7 s),   |d_0| <= 128,  -64 <= d_s <= 63 (s >= 1).
 // The digits come from one 64-bit addition: with C = 64 sum_{s=1..6} 2^(42-7s),
 // the unsigned 7-bit fields of W = V + C at bits 42 - 7s are d_s + 64 and the
-// arithmetic top part W >> 42 is d_0.  Every digit is exact in bf16.
+// arithmetic top part W >> 42 is d_0.  Every digit is exact in bf16.  (The
+// code keeps 2W + (0 or 1), whose fields are one bit higher, to save the
+// final halving of the rounding step.)
 //
 // Slice products: for K <= 64 terms, sum_k a_s b_t is an integer below 2^20 in
 // magnitude, and a level L = s + t (at most 7 pairs) stays below 2^22
@@ -40,37 +42,54 @@ constexpr uint64_t kLevelOffset =
 
 QS_HD int biased_exp(uint32_t hw) { return (int)((hw >> 20) & 0x7FFu); }
 
-// W = V + C for the double with words (hw, lw); emax >= its biased exponent.
-// V is rounded half up (toward +infinity), so the rounding error does not
-// depend on the sign of x.  Zeros and subnormals give V = 0.
-QS_HD uint64_t fixed_w(uint32_t hw, uint32_t lw, int emax) {
-  const int eb = biased_exp(hw);
-  int sh = emax - eb + 3;                         // leaves one bit below the units
-  sh = sh > 63 ? 63 : sh;
-  const uint64_t m = eb ? ((((uint64_t)(hw & 0xFFFFFu) | 0x100000u) << 32) | lw) : 0ull;
+// Lower bound of the exponent maximum (biased) of a row or column: entries
+// below 2^(54 - 1023) = 2^-969 are sliced on that grid, and zeros and
+// subnormals (whose implicit bit is wrongly set below) always shift out
+// entirely, since their shift is then at least 57.
+constexpr int kEmaxFloor = 54;
+
+// Arithmetic right shift of a 64-bit value; amounts above 63 give the sign
+// fill (PTX shr clamps the amount), which the host version matches.
+QS_HD int64_t shr_s64(int64_t x, int sh) {
+#if defined(__CUDA_ARCH__)
+  int64_t r;
+  asm("shr.s64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(sh));
+  return r;
+#else
+  return x >> (sh > 63 ? 63 : sh);
+#endif
+}
+
+// T = floor(2 x 2^(48 - Emax)) + 2C + 1 for the double with words (hw, lw),
+// with emax >= max(its biased exponent, kEmaxFloor).  T is 2W or 2W + 1 for
+// W = V + C, V = x 2^(48 - Emax) rounded half up (toward +infinity, so the
+// rounding error does not depend on the sign of x); the digit fields of W
+// sit one bit higher in T.  Zeros and subnormals give V = 0.
+QS_HD uint64_t fixed_t(uint32_t hw, uint32_t lw, int emax) {
+  const int sh = emax - biased_exp(hw) + 3;      // leaves one bit below the units
+  const uint64_t m = (((uint64_t)(hw & 0xFFFFFu) | 0x100000u) << 32) | lw;
   const uint64_t smask = (uint64_t)(int64_t)((int32_t)hw >> 31);
   const int64_t ms = (int64_t)((m ^ smask) - smask);      // signed significand
-  const int64_t t = ms >> sh;                              // floor(2 x 2^(48 - Emax))
-  return (uint64_t)((t + (int64_t)(2 * kBal + 1)) >> 1);   // floor(x 2^(48 - Emax) + 1/2) + C
+  return (uint64_t)(shr_s64(ms, sh) + (int64_t)(2 * kBal + 1));
 }
 
-// Balanced digit s of W (integer form, for checks).
-QS_HD int digit(uint64_t w, int s) {
-  if (s == 0) return (int)((int64_t)w >> 42);
-  return (int)((w >> (42 - 7 * s)) & 127u) - 64;
+// Balanced digit s of W = T >> 1 (integer form, for checks).
+QS_HD int digit_t(uint64_t t, int s) {
+  if (s == 0) return (int)((int64_t)t >> 43);
+  return (int)((t >> (43 - 7 * s)) & 127u) - 64;
 }
 
-// The seven digits of W as floats (exact small integers).
-QS_HD void digit_floats(uint64_t w, float* f) {
-  const uint32_t lo = (uint32_t)w, hi = (uint32_t)(w >> 32);
-  const uint32_t d0 = (uint32_t)((int32_t)hi >> 10);
+// The seven digits as floats (exact small integers).
+QS_HD void digit_floats_t(uint64_t t, float* f) {
+  const uint32_t lo = (uint32_t)t, hi = (uint32_t)(t >> 32);
+  const uint32_t d0 = (uint32_t)((int32_t)hi >> 11);
   f[0] = qsdf::u2f(0x4B400000u + d0) - 12582912.0f;
-  f[1] = qsdf::u2f(0x4B400000u | ((hi >> 3) & 127u)) - 12582976.0f;
-  f[2] = qsdf::u2f(0x4B400000u | ((uint32_t)(w >> 28) & 127u)) - 12582976.0f;
-  f[3] = qsdf::u2f(0x4B400000u | ((lo >> 21) & 127u)) - 12582976.0f;
-  f[4] = qsdf::u2f(0x4B400000u | ((lo >> 14) & 127u)) - 12582976.0f;
-  f[5] = qsdf::u2f(0x4B400000u | ((lo >> 7) & 127u)) - 12582976.0f;
-  f[6] = qsdf::u2f(0x4B400000u | (lo & 127u)) - 12582976.0f;
+  f[1] = qsdf::u2f(0x4B400000u | ((hi >> 4) & 127u)) - 12582976.0f;
+  f[2] = qsdf::u2f(0x4B400000u | ((uint32_t)(t >> 29) & 127u)) - 12582976.0f;
+  f[3] = qsdf::u2f(0x4B400000u | ((lo >> 22) & 127u)) - 12582976.0f;
+  f[4] = qsdf::u2f(0x4B400000u | ((lo >> 15) & 127u)) - 12582976.0f;
+  f[5] = qsdf::u2f(0x4B400000u | ((lo >> 8) & 127u)) - 12582976.0f;
+  f[6] = qsdf::u2f(0x4B400000u | ((lo >> 1) & 127u)) - 12582976.0f;
 }
 
 // sum_L level_L 2^(7(6-L)) from the bit patterns b_L of (level_L + 1.5 * 2^23).

@@ -55,8 +55,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 // seven packed (re, im) digit pairs of one amplitude (words of re and im)
 __device__ __forceinline__ void slice_amp(const uint32_t* w, int emax, uint32_t* out) {
   float fr[kS], fi[kS];
-  qsoz::digit_floats(qsoz::fixed_w(w[0], w[1], emax), fr);
-  qsoz::digit_floats(qsoz::fixed_w(w[2], w[3], emax), fi);
+  qsoz::digit_floats_t(qsoz::fixed_t(w[0], w[1], emax), fr);
+  qsoz::digit_floats_t(qsoz::fixed_t(w[2], w[3], emax), fi);
 #pragma unroll
   for (int s = 0; s < kS; ++s) out[s] = pack_bf16(fr[s], fi[s]);
 }
@@ -121,15 +121,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_dense_ozaki(double2* __restrict_
   uint64_t* rowoff = toff + D;                                        // kRows
   uint64_t* tile_base = rowoff + kRows;                               // 2
   uint64_t* mbar = tile_base + 2;                                     // 2
-  int* csc = reinterpret_cast<int*>(mbar + 2);                        // N: column exponent - 2100
-  int* rowexp = csc + N;                                              // 2 x kRows (tile parity)
+  int* csc = reinterpret_cast<int*>(mbar + 2);                        // N: (column exponent - 2100) << 20
+  int* rowexp = csc + N;                                              // 2 x kRows: exponent field of the row maximum
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(rowexp + 2 * kRows);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   // B: column maxima of the exponents, then the digit slices (once per CTA)
   for (int n = tid; n < N; n += THREADS) {
-    int e = 0;
+    int e = qsoz::kEmaxFloor;
     for (int k = 0; k < K; ++k) e = max(e, qsoz::biased_exp((uint32_t)__double2hiint(realified(p, D, k, n))));
     csc[n] = e;
   }
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_dense_ozaki(double2* __restrict_
     const int n = idx / K, k = idx % K;
     const double v = realified(p, D, k, n);
     float f[kS];
-    qsoz::digit_floats(qsoz::fixed_w((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v), csc[n]), f);
+    qsoz::digit_floats_t(qsoz::fixed_t((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v), csc[n]), f);
     const uint32_t off = canon_off16(n, k, K);
 #pragma unroll
     for (int s = 0; s < kS; ++s)
@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_dense_ozaki(double2* __restrict_
     rowexp[kRows + g] = 0;
   }
   __syncthreads();
-  for (int n = tid; n < N; n += THREADS) csc[n] -= 2046 + 54;   // scale 2^(Ea + Eb - 54) with biased Ea, Eb
+  // scale 2^(Ea + Eb - 54) with biased Ea, Eb, as an exponent-field increment
+  for (int n = tid; n < N; n += THREADS) csc[n] = (int)((unsigned)(csc[n] - 2046 - 54) << 20);
   if (tid == 0) {
     tile_base[0] = insert_zeros(blockIdx.x, p.hi_ins, p.nhi) | p.ctrl_mask;
 #pragma unroll
@@ -213,15 +214,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_dense_ozaki(double2* __restrict_
     }
   };
   // row maximum of the exponents (the CG threads of a row are in different warps)
+  // (exponent fields compared in place: 0x7FF00000 of the high words)
   auto row_max = [&](int slot) {
-    int em = 0;
+    uint32_t em = (uint32_t)qsoz::kEmaxFloor << 20;
 #pragma unroll
-    for (int i = 0; i < EPT; ++i) em = max(em, max(qsoz::biased_exp(R[i][0]), qsoz::biased_exp(R[i][2])));
-    atomicMax(rowexp + slot * kRows + g, em);
+    for (int i = 0; i < EPT; ++i) em = max(em, max(R[i][0] & 0x7FF00000u, R[i][2] & 0x7FF00000u));
+    atomicMax(rowexp + slot * kRows + g, (int)em);
   };
 
   // epilogue of one tile: levels -> exact integers -> doubles -> scatter
-  auto epilogue = [&](uint32_t tbuf, int eg, uint64_t rb) {
+  auto epilogue = [&](uint32_t tbuf, int egs, uint64_t rb) {
 #pragma unroll
     for (int cc = 0; cc < CPW; cc += 8) {
       float v[kS][8];
@@ -238,10 +240,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_dense_ozaki(double2* __restrict_
           uint32_t bits[kS];
 #pragma unroll
           for (int L = 0; L < kS; ++L) bits[L] = __float_as_uint(v[L][q] + 12582912.0f);
-          const long long acc = qsoz::combine_levels(bits);
-          const double r = __ll2double_rn(acc);
-          const int hi = __double2hiint(r) + (int)((unsigned)(eg + scl[q]) << 20);
-          o[q] = acc != 0 ? __hiloint2double(hi, __double2loint(r)) : 0.0;
+          const double r = __ll2double_rn(qsoz::combine_levels(bits));
+          const int hi = __double2hiint(r);                // 0 only for r = 0, which stays 0
+          o[q] = __hiloint2double(hi + (hi != 0 ? egs + scl[q] : 0), __double2loint(r));
         }
 #pragma unroll
         for (int q = 0; q < 8; q += 2) psi[rb | tofs((cc + q) >> 1)] = make_double2(o[q], o[q + 1]);
@@ -266,7 +267,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_dense_ozaki(double2* __restrict_
     const int par = it & 1;                   // tile parity: row-maximum and base slots
     const uint64_t rb = tile_base[par] | roff;
     const bool has_next = c + gridDim.x < p.ntiles;
-    const int eg = rowexp[par * kRows + g];
+    const int egs = rowexp[par * kRows + g];   // exponent field of the row maximum
+    const int eg = egs >> 20;
     // digit slices of this thread's amplitudes, 16 bytes per slice and 4 amplitudes
     unsigned char* A = a_dig + b * (kS * ABYTES);
 #pragma unroll
@@ -316,9 +318,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_dense_ozaki(double2* __restrict_
       timed_out = wait_phase(mbar, phases & 1u);
       phases ^= 1u;
       fence_after_sync();
-      epilogue(0u, eg, rb);
+      epilogue(0u, egs, rb);
     }
-    eg_prev = eg;
+    eg_prev = egs;
     rb_prev = rb;
     if (has_next) row_max(par ^ 1);
     if (tid == helper && c + 2 * (uint64_t)gridDim.x < p.ntiles)

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <random>
 
 #include "qs_slices.cuh"
@@ -53,14 +54,18 @@ int main() {
     double x = std::ldexp(u(rng), ex(rng));
     if (it % 97 == 0) x = 0.0;
     if (it % 101 == 0) x = -0.0;
+    if (it % 103 == 0) x = std::ldexp(u(rng), -1040);   // subnormal: slices to zero
+    if (it % 107 == 0) x = std::ldexp(u(rng), -990);    // below the floor of the grid
     int emax = (x == 0.0 ? 1000 : bexp(x)) + (it % 3 == 0 ? 0 : gap(rng) % (it % 5 == 0 ? 70 : 4));
-    if (it % 7 == 0) emax = bexp(x) > 0 ? bexp(x) : 1;  // value at the row maximum
+    if (it % 7 == 0) emax = bexp(x);                    // value at the row maximum
+    if (it % 11 == 0) emax += 1100;                     // shifts far above 63
+    emax = std::max(emax, qsoz::kEmaxFloor);
     uint32_t hw, lw;
     words(x, hw, lw);
-    const uint64_t w = qsoz::fixed_w(hw, lw, emax);
+    const uint64_t w = qsoz::fixed_t(hw, lw, emax);
     long long v = 0;
     for (int s = 0; s < qsoz::kSlices; ++s) {
-      const int d = qsoz::digit(w, s);
+      const int d = qsoz::digit_t(w, s);
       if (s == 0)
         CHECK(d >= -128 && d <= 128, "d0 = %d", d);
       else
@@ -70,9 +75,9 @@ int main() {
     const long long ref = ref_fixed(x, emax);
     CHECK(v == ref, "x = %.17g emax = %d: V = %lld, expected %lld", x, emax, v, ref);
     float f[qsoz::kSlices];
-    qsoz::digit_floats(w, f);
+    qsoz::digit_floats_t(w, f);
     for (int s = 0; s < qsoz::kSlices; ++s) {
-      CHECK(f[s] == (float)qsoz::digit(w, s), "float digit %d", s);
+      CHECK(f[s] == (float)qsoz::digit_t(w, s), "float digit %d", s);
       CHECK((qsdf::f2u(f[s]) & 0xFFFFu) == 0u, "digit %d not exact in bf16", s);
     }
   }
@@ -131,7 +136,7 @@ int main() {
       a[k] = std::ldexp(gauss(rng), es(rng) - 15);
       b[k] = std::ldexp(gauss(rng), es(rng));
     }
-    int ea = 0, eb = 0;
+    int ea = qsoz::kEmaxFloor, eb = qsoz::kEmaxFloor;
     for (int k = 0; k < K; ++k) {
       ea = std::max(ea, bexp(a[k]));
       eb = std::max(eb, bexp(b[k]));
@@ -141,9 +146,9 @@ int main() {
       uint32_t h1, l1, h2, l2;
       words(a[k], h1, l1);
       words(b[k], h2, l2);
-      const uint64_t wa = qsoz::fixed_w(h1, l1, ea), wb = qsoz::fixed_w(h2, l2, eb);
+      const uint64_t wa = qsoz::fixed_t(h1, l1, ea), wb = qsoz::fixed_t(h2, l2, eb);
       for (int s = 0; s < qsoz::kSlices; ++s)
-        for (int t = 0; s + t < qsoz::kSlices; ++t) lv[s + t] += (long long)qsoz::digit(wa, s) * qsoz::digit(wb, t);
+        for (int t = 0; s + t < qsoz::kSlices; ++t) lv[s + t] += (long long)qsoz::digit_t(wa, s) * qsoz::digit_t(wb, t);
     }
     uint32_t bits[qsoz::kSlices];
     for (int L = 0; L < qsoz::kSlices; ++L) bits[L] = qsdf::f2u((float)lv[L] + 12582912.0f);
