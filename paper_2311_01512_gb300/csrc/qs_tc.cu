@@ -43,8 +43,8 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
 
 }  // namespace
 
-template <int NT, int THREADS, int NBUF>
-__global__ void __launch_bounds__(THREADS, 1) k_dense_tc(float2* __restrict__ psi, const __grid_constant__ TcParams p) {
+template <int NT, int THREADS, int NBUF, int CTAS>
+__global__ void __launch_bounds__(THREADS, CTAS) k_dense_tc(float2* __restrict__ psi, const __grid_constant__ TcParams p) {
   constexpr int D = 1 << NT;
   constexpr int K = 2 * D;                   // real inputs per group
   constexpr int N = 2 * D;                   // real outputs per group
@@ -455,22 +455,27 @@ static cudaError_t dense_tc_nt(void* amps, const TcParams& p, cudaStream_t st) {
   static_assert(CTAS * tc_cols(NBUF * N) <= 512, "tensor memory");
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_dense_tc<NT, THREADS, NBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_dense_tc<NT, THREADS, NBUF, CTAS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
   const uint64_t maxb = (uint64_t)num_sms() * CTAS;
   const unsigned g = (unsigned)(p.ntiles < maxb ? p.ntiles : maxb);
-  k_dense_tc<NT, THREADS, NBUF><<<g, THREADS, smem, st>>>(static_cast<float2*>(amps), p);
+  k_dense_tc<NT, THREADS, NBUF, CTAS><<<g, THREADS, smem, st>>>(static_cast<float2*>(amps), p);
   return cudaGetLastError();
 }
 
+// Launch shapes measured at 30 qubits (random targets): 3 targets 2.59 ms as
+// six single-buffered 128-thread CTAs per SM (3.26 ms as three double-buffered
+// 256-thread ones), 4 targets 3.17 ms as two double-buffered 512-thread CTAs,
+// 5 targets 3.28 ms as two single-buffered 256-thread CTAs (3.65 ms as one
+// double-buffered 512-thread CTA).
 cudaError_t launch_dense_tc(void* amps, const TcParams& p, cudaStream_t st) {
   switch (p.n) {
-    case 3: return dense_tc_nt<3, 256, 2, 3>(amps, p, st);
+    case 3: return dense_tc_nt<3, 128, 1, 6>(amps, p, st);
     case 4: return dense_tc_nt<4, 512, 2, 2>(amps, p, st);
-    case 5: return dense_tc_nt<5, 512, 2, 1>(amps, p, st);
+    case 5: return dense_tc_nt<5, 256, 1, 2>(amps, p, st);
     case 6: return dense_tc6(amps, p, st);
     default: return cudaErrorInvalidValue;
   }

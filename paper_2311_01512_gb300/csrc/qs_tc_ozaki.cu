@@ -20,10 +20,11 @@
 // [c EPT, (c+1) EPT), c = w / 4, of that row, for the gather, the slicing and
 // the epilogue alike, so the row's exponent and base index stay in registers.
 // Pipeline per CTA (persistent, tiles c, c + grid, ...): the loads of the
-// next tile are issued right after the current tile's slices are written, and
-// with two buffers of slices and accumulators the epilogue of tile i - 1 runs
-// while the tensor cores work on tile i; the row maxima of tile i + 1 are
-// taken after that epilogue, so a tile costs two CTA barriers.  The MMAs are
+// next tile are issued right after the current tile's slices are written, so
+// they are in flight during the MMAs and the epilogue; with two buffers of
+// slices and accumulators (NBUF = 2) the epilogue of tile i - 1 would run
+// while the tensor cores work on tile i.  The row maxima of tile i + 1 are
+// taken after the epilogue, so a tile costs two CTA barriers.  The MMAs are
 // issued by one thread in each of warps 0..3, which take the levels {6},
 // {5, 0}, {4, 1}, {3, 2}: seven slice products each.  Every wait is bounded:
 // on timeout the kernel records an error code, frees its tensor memory and
@@ -101,8 +102,8 @@ __device__ __forceinline__ void mma_level(uint32_t d_tmem, uint64_t adesc, uint6
 
 }  // namespace
 
-template <int NT, int THREADS, int NBUF>
-__global__ void __launch_bounds__(THREADS, 1) k_dense_ozaki(double2* __restrict__ psi, const __grid_constant__ TcParams p) {
+template <int NT, int THREADS, int NBUF, int CTAS>
+__global__ void __launch_bounds__(THREADS, CTAS) k_dense_ozaki(double2* __restrict__ psi, const __grid_constant__ TcParams p) {
   constexpr int D = 1 << NT;
   constexpr int K = 2 * D, N = 2 * D;
   constexpr int CG = THREADS / kRows;         // threads per row
@@ -348,24 +349,31 @@ static cudaError_t dense_ozaki_nt(void* amps, const TcParams& p, cudaStream_t st
   constexpr int D = 1 << NT, K = 2 * D, N = 2 * D;
   constexpr size_t smem = (size_t)NBUF * kS * (kRows * K * 2) + (size_t)kS * (N * K * 2) + 8 * (D + kRows + 4) +
                           4 * (N + 2 * kRows) + 16;
-  static_assert(smem <= 227 * 1024, "shared memory");
+  static_assert(smem * CTAS <= 227 * 1024, "shared memory");
+  static_assert(CTAS * tmem_cols(NBUF * kS * N) <= 512, "tensor memory");
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_dense_ozaki<NT, THREADS, NBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_dense_ozaki<NT, THREADS, NBUF, CTAS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
   const uint64_t maxb = (uint64_t)num_sms() * CTAS;
   const unsigned g = (unsigned)(p.ntiles < maxb ? p.ntiles : maxb);
-  k_dense_ozaki<NT, THREADS, NBUF><<<g, THREADS, smem, st>>>(static_cast<double2*>(amps), p);
+  k_dense_ozaki<NT, THREADS, NBUF, CTAS><<<g, THREADS, smem, st>>>(static_cast<double2*>(amps), p);
   return cudaGetLastError();
 }
 
+// Several independent single-buffered CTAs per SM, whose phases drift apart,
+// keep the SM busier than double buffering inside one CTA (measured at 30
+// qubits: 3 targets 10.3 ms as four 128-thread CTAs against 12.2 ms as two
+// double-buffered 256-thread CTAs; 4 targets 11.2 ms as two 256-thread CTAs
+// against 13.9 ms as one double-buffered 512-thread CTA).  Tensor memory
+// (seven levels of N columns per buffer) bounds the CTAs per SM.
 cudaError_t launch_dense_ozaki(void* amps, const TcParams& p, cudaStream_t st) {
   switch (p.n) {
-    case 3: return dense_ozaki_nt<3, 256, 2, 2>(amps, p, st);
-    case 4: return dense_ozaki_nt<4, 512, 2, 1>(amps, p, st);
+    case 3: return dense_ozaki_nt<3, 128, 1, 4>(amps, p, st);
+    case 4: return dense_ozaki_nt<4, 256, 1, 2>(amps, p, st);
     case 5: return dense_ozaki_nt<5, 512, 1, 1>(amps, p, st);
     default: return cudaErrorInvalidValue;
   }
