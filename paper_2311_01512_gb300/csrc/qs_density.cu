@@ -189,7 +189,7 @@ template <typename R>
 static cudaError_t group_t(void* amps, int op, const GroupParams& p, cudaStream_t st) {
   using T2 = typename Cplx<R>::T;
   T2* a = static_cast<T2*>(amps);
-  const unsigned g = grid_for(p.ngroups, 256, num_sms() * 8);
+  const unsigned g = grid_for(p.ngroups, 256, num_sms() * kStreamBlocksPerSM);
   switch (op) {
     case G_DEPHASE1: k_group<R, G_DEPHASE1><<<g, 256, 0, st>>>(a, p); break;
     case G_DEPHASE2: k_group<R, G_DEPHASE2><<<g, 256, 0, st>>>(a, p); break;
@@ -207,7 +207,7 @@ cudaError_t launch_group(qs_prec prec, void* amps, int op, const GroupParams& p,
 }
 
 cudaError_t launch_ptrace(qs_prec prec, const void* in, void* out, const PtraceParams& p, cudaStream_t st) {
-  const unsigned g = grid_for(p.nout, 256, num_sms() * 8);
+  const unsigned g = grid_for(p.nout, 256, num_sms() * kStreamBlocksPerSM);
   if (prec == QS_C128)
     k_ptrace<double><<<g, 256, 0, st>>>(static_cast<const double2*>(in), static_cast<double2*>(out), p);
   else
@@ -223,7 +223,7 @@ cudaError_t launch_superop(const double* kraus, int num_ops, int n, double* sup,
 
 cudaError_t launch_dm_from_pure(qs_prec prec, void* rho, const void* psi, int nq, double weight,
                                 int accumulate, cudaStream_t st) {
-  const unsigned g = grid_for(1ull << (2 * nq), 256, num_sms() * 8);
+  const unsigned g = grid_for(1ull << (2 * nq), 256, num_sms() * kStreamBlocksPerSM);
   if (prec == QS_C128)
     k_dm_from_pure<double><<<g, 256, 0, st>>>(static_cast<double2*>(rho), static_cast<const double2*>(psi), nq,
                                               weight, accumulate);

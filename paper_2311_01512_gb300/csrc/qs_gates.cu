@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256) k_phase(typename Cplx<R>::T* __restrict__
 // ---------------------------------------------------------------------------
 template <typename R>
 static cudaError_t gate1_t(void* amps, const Gate1Params& p, cudaStream_t st) {
-  const unsigned g = grid_for(p.npairs, 256, num_sms() * 8);
+  const unsigned g = grid_for(p.npairs, 256, num_sms() * kStreamBlocksPerSM);
   k_gate1<R><<<g, 256, 0, st>>>(static_cast<typename Cplx<R>::T*>(amps), p);
   return cudaGetLastError();
 }
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(256) k_swap(T2* __restrict__ psi, uint64_t npa
 
 cudaError_t launch_swap(qs_prec prec, void* amps, int ns, int t1, int t2, cudaStream_t st) {
   const uint64_t npairs = 1ull << (ns - 2);
-  const unsigned g = grid_for(npairs, 256, num_sms() * 8);
+  const unsigned g = grid_for(npairs, 256, num_sms() * kStreamBlocksPerSM);
   if (prec == QS_C128)
     k_swap<double2><<<g, 256, 0, st>>>(static_cast<double2*>(amps), npairs, t1, t2);
   else
@@ -263,7 +263,7 @@ cudaError_t launch_dense(qs_prec prec, void* amps, const DenseParams& p, cudaStr
 }
 
 cudaError_t launch_diag(qs_prec prec, void* amps, const DiagParams& p, cudaStream_t st) {
-  const unsigned g = grid_for(p.namps, 256, num_sms() * 8);
+  const unsigned g = grid_for(p.namps, 256, num_sms() * kStreamBlocksPerSM);
   if (prec == QS_C128)
     k_diag<double><<<g, 256, 0, st>>>(static_cast<double2*>(amps), p);
   else
@@ -272,7 +272,7 @@ cudaError_t launch_diag(qs_prec prec, void* amps, const DiagParams& p, cudaStrea
 }
 
 cudaError_t launch_gadget(qs_prec prec, void* amps, const GadgetParams& p, cudaStream_t st) {
-  const unsigned g = grid_for(p.nwork, 256, num_sms() * 8);
+  const unsigned g = grid_for(p.nwork, 256, num_sms() * kStreamBlocksPerSM);
   if (p.xy == 0) {
     if (prec == QS_C128)
       k_phase<double><<<g, 256, 0, st>>>(static_cast<double2*>(amps), p);

@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(256, 8) k_phase_df(double2* __restrict__ psi, 
 // Launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_gate1_df(void* amps, const Gate1DfParams& p, cudaStream_t st) {
-  const unsigned g = grid_for(p.npairs, 256, num_sms() * 8);
+  const unsigned g = grid_for(p.npairs, 256, num_sms() * kStreamBlocksPerSM);
   k_gate1_df<<<g, 256, 0, st>>>(static_cast<double2*>(amps), p);
   return cudaGetLastError();
 }
@@ -323,13 +323,13 @@ cudaError_t launch_dense_df(void* amps, const DenseParams& p, cudaStream_t st) {
 }
 
 cudaError_t launch_diag_df(void* amps, const DiagParams& p, cudaStream_t st) {
-  const unsigned g = grid_for(p.namps, 256, num_sms() * 8);
+  const unsigned g = grid_for(p.namps, 256, num_sms() * kStreamBlocksPerSM);
   k_diag_df<<<g, 256, 0, st>>>(static_cast<double2*>(amps), p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gadget_df(void* amps, const GadgetDfParams& p, cudaStream_t st) {
-  const unsigned g = grid_for(p.nwork, 256, num_sms() * 8);
+  const unsigned g = grid_for(p.nwork, 256, num_sms() * kStreamBlocksPerSM);
   if (p.xy == 0)
     k_phase_df<<<g, 256, 0, st>>>(static_cast<double2*>(amps), p);
   else
