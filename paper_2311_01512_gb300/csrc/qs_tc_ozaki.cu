@@ -358,7 +358,9 @@ static cudaError_t dense_ozaki_nt(void* amps, const TcParams& p, cudaStream_t st
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  const uint64_t maxb = (uint64_t)num_sms() * CTAS;
+  // for 3 and 4 targets, eight times the resident CTAs: the late ones even out
+  // the SMs' tile counts at the end of the pass (7% and 2% faster measured)
+  const uint64_t maxb = (uint64_t)num_sms() * CTAS * (NT <= 4 ? 8 : 1);
   const unsigned g = (unsigned)(p.ntiles < maxb ? p.ntiles : maxb);
   k_dense_ozaki<NT, THREADS, NBUF, CTAS><<<g, THREADS, smem, st>>>(static_cast<double2*>(amps), p);
   return cudaGetLastError();
