@@ -582,6 +582,11 @@ qs_status group_channel(qs_state* s, int op, int t1, int t2, const double* f) {
   for (int b = 0; b < p.nbits; ++b) p.ins[b] = (int8_t)pos[b];
   p.ngroups = 1ull << (s->ns - p.nbits);
   for (int k = 0; k < 4; ++k) p.f[k] = f[k];
+  // complex128 with double-float arithmetic: channels that mix or scale by
+  // non-trivial coefficients use the double-float kernel (the FP64 one is
+  // bound by the FP64 pipe, not by memory); dephasing stays on FP64
+  if (s->prec == QS_C128 && s->arith == QS_ARITH_DF && op != qsk::G_DEPHASE1 && op != qsk::G_DEPHASE2)
+    return cuda_status(qsk::launch_group_df(s->amps, op, p, s->stream));
   return cuda_status(qsk::launch_group(s->prec, s->amps, op, p, s->stream));
 }
 

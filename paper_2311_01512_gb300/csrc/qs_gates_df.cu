@@ -285,8 +285,107 @@ __global__ void __launch_bounds__(256, 8) k_phase_df(double2* __restrict__ psi, 
 }
 
 // ---------------------------------------------------------------------------
+// Channels on groups of Choi amplitudes, double-float arithmetic.  The same
+// updates as k_group in qs_density.cu (Sec. "Depolarising channel", "Damping
+// channel"; the one-qubit Pauli channel): each output is a real combination
+// of at most four amplitudes of its group, formed as an error-free FP32 dot
+// product and rounded once to double.  (Dephasing only scales and stays on
+// the FP64 kernel, which already moves memory at the HBM rate.)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 lin_df(df ca, const cdf& x, df cb, const cdf& y) {
+  qsdf::dot_acc re = qsdf::dot_first(ca, x.re), im = qsdf::dot_first(ca, x.im);
+  qsdf::dot_add(re, cb, y.re);
+  qsdf::dot_add(im, cb, y.im);
+  return make_double2(qsdf::finish(re), qsdf::finish(im));
+}
+
+__device__ __forceinline__ double2 scale_df(df c, const cdf& x) {
+  return make_double2(qsdf::finish(qsdf::dot_first(c, x.re)), qsdf::finish(qsdf::dot_first(c, x.im)));
+}
+
+__device__ __forceinline__ cdf split2(double2 v) {
+  cdf r;
+  r.re = qsdf::split(v.x);
+  r.im = qsdf::split(v.y);
+  return r;
+}
+
+template <int OP>
+__global__ void __launch_bounds__(256) k_group_df(double2* __restrict__ rho, const __grid_constant__ GroupParams p) {
+  const df f0 = qsdf::split(p.f[0]), f1 = qsdf::split(p.f[1]), f2 = qsdf::split(p.f[2]), f3 = qsdf::split(p.f[3]);
+  const df one{1.0f, 0.0f};
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < p.ngroups; k += stride) {
+    const uint64_t base = insert_zeros(k, p.ins, p.nbits);
+    if (OP == G_DEPOL1 || OP == G_PAULI1 || OP == G_DAMP) {
+      const uint64_t b0 = 1ull << p.mpos[0], b1 = 1ull << p.mpos[1];
+      const uint64_t i00 = base, i01 = base | b0, i10 = base | b1, i11 = base | b0 | b1;
+      const double2 va = rho[i00], vb = rho[i01], vc = rho[i10], vd = rho[i11];
+      const cdf a = split2(va), b = split2(vb), c = split2(vc), d = split2(vd);
+      if (OP == G_DEPOL1) {
+        rho[i00] = lin_df(f0, a, f1, d);
+        rho[i11] = lin_df(f0, d, f1, a);
+        rho[i01] = scale_df(f2, b);
+        rho[i10] = scale_df(f2, c);
+      } else if (OP == G_PAULI1) {
+        rho[i00] = lin_df(f0, a, f1, d);
+        rho[i11] = lin_df(f0, d, f1, a);
+        rho[i01] = lin_df(f2, b, f3, c);
+        rho[i10] = lin_df(f2, c, f3, b);
+      } else {  // damping
+        rho[i00] = lin_df(one, a, f1, d);
+        rho[i01] = scale_df(f2, b);
+        rho[i10] = scale_df(f2, c);
+        rho[i11] = scale_df(f0, d);
+      }
+    } else {  // two-qubit depolarising: members 0, 5, 10, 15 mix, the other 12 scale
+      uint64_t idx[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        uint64_t v = base;
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb)
+          if ((m >> bb) & 1) v |= 1ull << p.mpos[bb];
+        idx[m] = v;
+      }
+      const double2 w0 = rho[idx[0]], w5 = rho[idx[5]], w10 = rho[idx[10]], w15 = rho[idx[15]];
+      const cdf s[4] = {split2(w0), split2(w5), split2(w10), split2(w15)};
+      constexpr int mem[4] = {0, 5, 10, 15};
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        qsdf::dot_acc re = qsdf::dot_first(f0, s[m].re), im = qsdf::dot_first(f0, s[m].im);
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          if (o == m) continue;
+          qsdf::dot_add(re, f1, s[o].re);
+          qsdf::dot_add(im, f1, s[o].im);
+        }
+        rho[idx[mem[m]]] = make_double2(qsdf::finish(re), qsdf::finish(im));
+      }
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        if (m == 0 || m == 5 || m == 10 || m == 15) continue;
+        rho[idx[m]] = scale_df(f2, split2(rho[idx[m]]));
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+cudaError_t launch_group_df(void* amps, int op, const GroupParams& p, cudaStream_t st) {
+  double2* a = static_cast<double2*>(amps);
+  const unsigned g = grid_for(p.ngroups, 256, num_sms() * kStreamBlocksPerSM);
+  switch (op) {
+    case G_DEPOL1: k_group_df<G_DEPOL1><<<g, 256, 0, st>>>(a, p); break;
+    case G_DEPOL2: k_group_df<G_DEPOL2><<<g, 256, 0, st>>>(a, p); break;
+    case G_DAMP: k_group_df<G_DAMP><<<g, 256, 0, st>>>(a, p); break;
+    case G_PAULI1: k_group_df<G_PAULI1><<<g, 256, 0, st>>>(a, p); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 cudaError_t launch_gate1_df(void* amps, const Gate1DfParams& p, cudaStream_t st) {
   const unsigned g = grid_for(p.npairs, 256, num_sms() * kStreamBlocksPerSM);
   k_gate1_df<<<g, 256, 0, st>>>(static_cast<double2*>(amps), p);

@@ -207,6 +207,8 @@ cudaError_t batch_set_max_smem(int bytes);
 cudaError_t launch_batch(qs_prec prec, void* pool, const BatchState* states, const int* order, int nstates,
                          const BatchOp* ops, int* counter, int threads, int ctas, int smem_qubits, cudaStream_t st);
 cudaError_t launch_group(qs_prec prec, void* amps, int op, const GroupParams& p, cudaStream_t st);
+// complex128 channels in double-float arithmetic: G_DEPOL1, G_DEPOL2, G_DAMP, G_PAULI1 (qs_gates_df.cu)
+cudaError_t launch_group_df(void* amps, int op, const GroupParams& p, cudaStream_t st);
 cudaError_t launch_ptrace(qs_prec prec, const void* in, void* out, const PtraceParams& p,
                           cudaStream_t st);
 cudaError_t launch_superop(const double* kraus, int num_ops, int n, double* sup, cudaStream_t st);
