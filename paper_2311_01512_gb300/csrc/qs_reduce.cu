@@ -3,6 +3,7 @@
 // partial sum; stage two adds the partials in a fixed order, so results do not
 // depend on scheduling.
 #include "qs_device.cuh"
+#include "qs_df.cuh"
 
 namespace qsk {
 
@@ -69,58 +70,111 @@ __global__ void __launch_bounds__(256) k_expec_dm(const typename Cplx<R>::T* __r
 // (P psi)_i = beta_{i'} alpha_{i'}, i' = i xor xy (Sec. "Pauli tensor",
 // Eq. (Pauli tensor amplitude update)), in one pass over the amplitudes with
 // every term evaluated at each amplitude read:
-//  * terms with xy = 0 (I/Z strings) are diagonal: their sum over the run of
-//    such terms is sum_i |alpha_i|^2 sum_n h_n (-1)^{popc(i & yz_n)};
+//  * terms with xy = 0 (I/Z strings) are diagonal: h_n (-1)^{popc(i & yz_n)}
+//    |alpha_i|^2 from the amplitude alone;
 //  * terms that share xy (consecutive after the host's sort) share the
-//    partner load alpha_{i xor xy};
+//    partner load alpha_{i xor xy} and the product q = conj(alpha_i) alpha_{i'};
 //  * each Pauli string is Hermitian and h is real, so the contributions of i
 //    and i xor xy are complex conjugates: only indices with the highest bit
-//    of xy clear are visited, each counting 2 Re(...).  The imaginary part of
-//    the result is exactly zero.
+//    of xy clear are visited, each counting 2 Re(i^eta q) h (-1)^{popc(i' & yz)}.
+// Arithmetic is double-float (qs_df.cuh): q and |alpha_i|^2 as error-free
+// FP32 dot products, every contribution added to one per-thread accumulator
+// with TwoSum, so the loop needs no FP64 instruction; each thread rounds its
+// sum to double once.  The imaginary part of the result is exactly zero.
+__device__ __forceinline__ qsdf::df to_df(double x) { return qsdf::split(x); }
+__device__ __forceinline__ qsdf::df to_df(float x) { return qsdf::df{x, 0.0f}; }
+
+// A term as the kernel reads it from shared memory: h already split.
+struct TermDf {
+  uint64_t xy, yz;
+  float hh, hl;
+  int eta, pad;
+};
+// A run of terms sharing xy.
+struct GroupDf {
+  uint64_t xy, hb;       // flip mask, its highest bit (0 for the diagonal run)
+  int first, count;
+};
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_expec_sv(const typename Cplx<R>::T* __restrict__ psi, int nq,
                                                   const PauliTerm* __restrict__ terms, int nterms,
                                                   double2* __restrict__ partials) {
-  double sr = 0.0;
+  using qsdf::df;
+  using T2 = typename Cplx<R>::T;
+  extern __shared__ unsigned char sm_raw[];
+  TermDf* ts = reinterpret_cast<TermDf*>(sm_raw);
+  GroupDf* gs = reinterpret_cast<GroupDf*>(ts + nterms);
+  __shared__ int ngroups;
+  for (int n = threadIdx.x; n < nterms; n += blockDim.x) {
+    const PauliTerm t = terms[n];
+    const df h = qsdf::split(t.h);
+    ts[n] = TermDf{t.xy, t.yz, h.h, h.l, t.eta, 0};
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {                 // runs of equal xy, in order
+    int ng = 0;
+    for (int n = 0; n < nterms; ++n) {
+      if (n == 0 || ts[n].xy != ts[n - 1].xy) {
+        const uint64_t xy = ts[n].xy;
+        gs[ng] = GroupDf{xy, xy ? 1ull << (63 - __clzll((long long)xy)) : 0ull, n, 0};
+        ++ng;
+      }
+      ++gs[ng - 1].count;
+    }
+    ngroups = ng;
+  }
+  __syncthreads();
+  const int ng = ngroups;
+  qsdf::dot_acc acc{0.0f, 0.0f};
   const uint64_t dim = 1ull << nq;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  // partner of group g for amplitude i (zero where the group skips i or is diagonal)
+  auto partner = [&](int g, uint64_t i) -> T2 {
+    const GroupDf G = gs[g];
+    T2 b;
+    b.x = 0;
+    b.y = 0;
+    if (G.xy != 0 && !(i & G.hb)) b = psi[i ^ G.xy];
+    return b;
+  };
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride) {
-    const auto a = psi[i];
-    const double ar = (double)a.x, ai = (double)a.y;
-    int n = 0;
-    while (n < nterms) {
-      const uint64_t xy = terms[n].xy;
-      if (xy == 0) {
-        double d = 0.0;
-        for (; n < nterms && terms[n].xy == 0; ++n) d += parity64(i & terms[n].yz) ? -terms[n].h : terms[n].h;
-        sr += d * (ar * ar + ai * ai);
-        continue;
-      }
-      const uint64_t hb = 1ull << (63 - __clzll((long long)xy));
-      if (i & hb) {
-        for (; n < nterms && terms[n].xy == xy; ++n) {
+    const T2 a = psi[i];
+    const df ar = to_df(a.x), ai = to_df(a.y);
+    T2 bnext = ng > 0 ? partner(0, i) : T2{};
+    for (int g = 0; g < ng; ++g) {
+      const T2 b = bnext;
+      if (g + 1 < ng) bnext = partner(g + 1, i);      // one group ahead: two partner loads in flight
+      const GroupDf G = gs[g];
+      if (G.xy == 0) {
+        qsdf::dot_acc pa = qsdf::dot_first(ar, ar);    // |alpha_i|^2
+        qsdf::dot_add(pa, ai, ai);
+        const df p2 = qsdf::dot_result(pa);
+        for (int n = G.first; n < G.first + G.count; ++n) {
+          const bool neg = parity64(i & ts[n].yz);
+          qsdf::dot_add(acc, df{neg ? -ts[n].hh : ts[n].hh, neg ? -ts[n].hl : ts[n].hl}, p2);
         }
         continue;
       }
-      const uint64_t ip = i ^ xy;
-      const auto b = psi[ip];
-      const double br = (double)b.x, bi = (double)b.y;
-      double cr = 0.0, ci = 0.0;                        // sum_n h_n eta_n (-1)^{popc(ip & yz_n)}
-      for (; n < nterms && terms[n].xy == xy; ++n) {
-        const double h = parity64(ip & terms[n].yz) ? -terms[n].h : terms[n].h;
-        switch (terms[n].eta) {
-          case 0: cr += h; break;
-          case 1: ci += h; break;
-          case 2: cr -= h; break;
-          default: ci -= h; break;
-        }
+      if (i & G.hb) continue;
+      const uint64_t ip = i ^ G.xy;
+      const df br = to_df(b.x), bi = to_df(b.y);
+      // q = conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
+      qsdf::dot_acc qa = qsdf::dot_first(ar, br);
+      qsdf::dot_add(qa, ai, bi);
+      qsdf::dot_acc qb = qsdf::dot_first(ar, bi);
+      qsdf::dot_add(qb, qsdf::neg(ai), br);
+      const df qr = qsdf::dot_result(qa), qi = qsdf::dot_result(qb);
+      for (int n = G.first; n < G.first + G.count; ++n) {
+        // 2 Re(i^eta q) (-1)^{popc(ip & yz)} h: eta 0 -> qr, 1 -> -qi, 2 -> -qr, 3 -> qi
+        const int eta = ts[n].eta;
+        const bool neg = parity64(ip & ts[n].yz) != (eta == 1 || eta == 2);
+        const float s2 = neg ? -2.0f : 2.0f;                 // exact scaling
+        qsdf::dot_add(acc, df{s2 * ts[n].hh, s2 * ts[n].hl}, (eta & 1) ? qi : qr);
       }
-      // 2 Re(conj(a) (c b))
-      const double qr = ar * br + ai * bi, qi = ar * bi - ai * br;
-      sr += 2.0 * (qr * cr - qi * ci);
     }
   }
-  const double2 s = block_sum(make_double2(sr, 0.0));
+  const double2 s = block_sum(make_double2(qsdf::finish(acc), 0.0));
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
@@ -228,12 +282,21 @@ cudaError_t launch_expec_dm(qs_prec prec, const void* amps, int nq, const PauliT
 
 cudaError_t launch_expec_sv(qs_prec prec, const void* amps, int nq, const PauliTerm* terms, int nterms,
                             double2* partials, cudaStream_t st) {
+  const size_t smem = (sizeof(TermDf) + sizeof(GroupDf)) * (size_t)nterms;
+  static bool attr_done = false;
+  if (!attr_done) {
+    const int most = (int)((sizeof(TermDf) + sizeof(GroupDf)) * kTermChunk);
+    if (cudaFuncSetAttribute(k_expec_sv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) != cudaSuccess ||
+        cudaFuncSetAttribute(k_expec_sv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) != cudaSuccess)
+      return cudaGetLastError();
+    attr_done = true;
+  }
   if (prec == QS_C128)
-    k_expec_sv<double><<<kReduceBlocks, 256, 0, st>>>(static_cast<const double2*>(amps), nq, terms, nterms,
-                                                      partials);
+    k_expec_sv<double><<<kReduceBlocks, 256, smem, st>>>(static_cast<const double2*>(amps), nq, terms, nterms,
+                                                         partials);
   else
-    k_expec_sv<float><<<kReduceBlocks, 256, 0, st>>>(static_cast<const float2*>(amps), nq, terms, nterms,
-                                                     partials);
+    k_expec_sv<float><<<kReduceBlocks, 256, smem, st>>>(static_cast<const float2*>(amps), nq, terms, nterms,
+                                                        partials);
   return cudaGetLastError();
 }
 
