@@ -53,7 +53,7 @@ qs_status create(int nq, int ns, int is_density, qs_prec prec, void* d_amps, voi
   s->is_density = is_density;
   s->prec = prec;
   s->stream = static_cast<cudaStream_t>(stream);
-  const size_t scratch = sizeof(double2) * (qsk::kReduceBlocks + 2);
+  const size_t scratch = sizeof(double2) * (qsk::kPartials + 2);
   if (cudaMalloc(&s->d_partials, scratch) != cudaSuccess || cudaMalloc(&s->d_ring, kRingSlots * kSlotBytes) != cudaSuccess ||
       cudaMallocHost(&s->h_result, sizeof(double2) * 2) != cudaSuccess ||
       cudaMallocHost(&s->h_ring, kRingSlots * kSlotBytes) != cudaSuccess) {
@@ -61,8 +61,8 @@ qs_status create(int nq, int ns, int is_density, qs_prec prec, void* d_amps, voi
     release(s);
     return QS_ERR_OOM;
   }
-  s->d_result = s->d_partials + qsk::kReduceBlocks;
-  s->d_err = reinterpret_cast<int*>(s->d_partials + qsk::kReduceBlocks + 1);
+  s->d_result = s->d_partials + qsk::kPartials;
+  s->d_err = reinterpret_cast<int*>(s->d_partials + qsk::kPartials + 1);
   if (cudaMemset(s->d_err, 0, sizeof(int)) != cudaSuccess) {
     release(s);
     return QS_ERR_CUDA;
@@ -720,7 +720,9 @@ qs_status qs_calc_norm_or_trace(const qs_state* cs, double* out) {
   if (!s || !out) return QS_ERR_ARG;
   cudaError_t e = s->is_density ? qsk::launch_trace(s->prec, s->amps, s->nq, s->d_partials, s->stream)
                                 : qsk::launch_norm(s->prec, s->amps, s->ns, s->d_partials, s->stream);
-  if (e == cudaSuccess) e = qsk::launch_reduce_final(s->d_partials, s->d_result, 0, s->stream);
+  if (e == cudaSuccess)
+    e = qsk::launch_reduce_final(s->d_partials, s->d_result, 0, s->stream,
+                                 s->is_density ? qsk::kReduceBlocks : qsk::kNormBlocks);
   if (e != cudaSuccess) return QS_ERR_CUDA;
   return reduce_to_host(s, out);
 }

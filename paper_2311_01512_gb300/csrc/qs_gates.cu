@@ -137,11 +137,28 @@ __global__ void __launch_bounds__(256) k_diag(typename Cplx<R>::T* __restrict__ 
   for (int j = threadIdx.x; j < (1 << p.n); j += blockDim.x) d[j] = mk<R>((R)p.d[2 * j], (R)p.d[2 * j + 1]);
   __syncthreads();
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.namps; i += stride) {
-    int j = 0;
-    for (int q = 0; q < p.n; ++q) j |= (int)((i >> p.tpos[q]) & 1) << q;
-    const T2 a = psi[i], w = d[j];
-    psi[i] = mk<R>(w.x * a.x - w.y * a.y, w.x * a.y + w.y * a.x);
+  if constexpr (sizeof(R) == 4) {
+    // complex64: two neighbouring amplitudes (16 bytes) per thread and step
+    float4* p4 = reinterpret_cast<float4*>(psi);
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; 2 * k < p.namps; k += stride) {
+      const uint64_t i = 2 * k;
+      int j = 0;
+      for (int q = 0; q < p.n; ++q) j |= (int)((i >> p.tpos[q]) & 1) << q;
+      int j1 = j;
+      for (int q = 0; q < p.n; ++q)
+        if (p.tpos[q] == 0) j1 |= 1 << q;
+      const float4 a = p4[k];
+      const T2 w = d[j], w1 = d[j1];
+      p4[k] = make_float4(w.x * a.x - w.y * a.y, w.x * a.y + w.y * a.x, w1.x * a.z - w1.y * a.w,
+                          w1.x * a.w + w1.y * a.z);
+    }
+  } else {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.namps; i += stride) {
+      int j = 0;
+      for (int q = 0; q < p.n; ++q) j |= (int)((i >> p.tpos[q]) & 1) << q;
+      const T2 a = psi[i], w = d[j];
+      psi[i] = mk<R>(w.x * a.x - w.y * a.y, w.x * a.y + w.y * a.x);
+    }
   }
 }
 
@@ -177,10 +194,22 @@ __global__ void __launch_bounds__(256) k_phase(typename Cplx<R>::T* __restrict__
   using T2 = typename Cplx<R>::T;
   const R c = (R)p.c, s = (R)p.s;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.nwork; i += stride) {
-    const R si = parity64(i & p.yz) ? -s : s;
-    const T2 a = psi[i];
-    psi[i] = mk<R>(c * a.x - si * a.y, c * a.y + si * a.x);
+  if constexpr (sizeof(R) == 4) {
+    // complex64: two neighbouring amplitudes (16 bytes) per thread and step
+    float4* p4 = reinterpret_cast<float4*>(psi);
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; 2 * k < p.nwork; k += stride) {
+      const uint64_t i = 2 * k;
+      const R s0 = parity64(i & p.yz) ? -s : s;
+      const R s1 = parity64((i + 1) & p.yz) ? -s : s;
+      const float4 a = p4[k];
+      p4[k] = make_float4(c * a.x - s0 * a.y, c * a.y + s0 * a.x, c * a.z - s1 * a.w, c * a.w + s1 * a.z);
+    }
+  } else {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.nwork; i += stride) {
+      const R si = parity64(i & p.yz) ? -s : s;
+      const T2 a = psi[i];
+      psi[i] = mk<R>(c * a.x - si * a.y, c * a.y + si * a.x);
+    }
   }
 }
 

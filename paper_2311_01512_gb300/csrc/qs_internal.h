@@ -13,7 +13,9 @@ namespace qsk {
 constexpr int kMaxQ = QS_MAX_STORAGE_QUBITS;
 constexpr int kMaxDense = QS_MAX_DENSE_TARGETS;
 constexpr int kTileBits = 10;        // amplitudes staged per tile of the dense kernel: 2^10
-constexpr int kReduceBlocks = 1216;  // 152 SMs x 8: fixed grid of every stage-one reduction
+constexpr int kReduceBlocks = 1216;  // 152 SMs x 8: fixed grid of the stage-one expectation and trace reductions
+constexpr int kNormBlocks = 4864;    // 152 SMs x 32: fixed grid of the norm, a pure stream over the state
+constexpr int kPartials = kNormBlocks;  // partial sums a handle holds (the larger grid)
 constexpr int kTermChunk = 2048;     // Pauli terms per device upload
 constexpr int kCostFeatures = 64;    // cost-model network: input features
 constexpr int kCostHidden = 64;      // hidden units per layer (two layers)
@@ -227,7 +229,7 @@ cudaError_t launch_expec_sv(qs_prec prec, const void* amps, int nq, const PauliT
 // the diagonal (I/Z) terms of a statevector Pauli sum by warp Walsh-Hadamard transforms; N >= 5
 cudaError_t launch_expec_sv_diag(qs_prec prec, const void* amps, int nq, const PauliTerm* terms, int nterms,
                                  double2* partials, cudaStream_t st);
-cudaError_t launch_reduce_final(const double2* partials, double2* result, int accumulate,
-                                cudaStream_t st);
+cudaError_t launch_reduce_final(const double2* partials, double2* result, int accumulate, cudaStream_t st,
+                                int nblocks = kReduceBlocks);
 
 }  // namespace qsk

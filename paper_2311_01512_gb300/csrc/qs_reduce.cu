@@ -1,23 +1,31 @@
-// Reductions in FP64: norm, trace, and Pauli-sum expectation values.  Stage one
-// runs a fixed grid of kReduceBlocks blocks, each writing one complex128
-// partial sum; stage two adds the partials in a fixed order, so results do not
-// depend on scheduling.
+// Reductions: norm, trace, and Pauli-sum expectation values.  Stage one runs
+// a fixed grid (kNormBlocks for the norm, kReduceBlocks for the others), each
+// block writing one complex128 partial sum; stage two adds the partials in a
+// fixed order, so results do not depend on scheduling.
 #include "qs_device.cuh"
 #include "qs_df.cuh"
 
 namespace qsk {
 
+__device__ __forceinline__ qsdf::df to_df(double x) { return qsdf::split(x); }
+__device__ __forceinline__ qsdf::df to_df(float x) { return qsdf::df{x, 0.0f}; }
+
 // sum_i |alpha_i|^2 (Sec. "Local statevector algorithms": the state model).
+// Each thread sums its squares exactly in double-float (TwoProd squares,
+// TwoSum accumulation; no FP64 instruction in the loop) and rounds once; the
+// block and stage-two sums are FP64.
 template <typename R>
 __global__ void __launch_bounds__(256) k_norm(const typename Cplx<R>::T* __restrict__ psi, uint64_t n,
                                               double2* __restrict__ partials) {
-  double acc = 0.0;
+  qsdf::dot_acc acc{0.0f, 0.0f};
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const auto a = psi[i];
-    acc += (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+    const qsdf::df ar = to_df(a.x), ai = to_df(a.y);
+    qsdf::dot_add(acc, ar, ar);
+    qsdf::dot_add(acc, ai, ai);
   }
-  const double2 s = block_sum(make_double2(acc, 0.0));
+  const double2 s = block_sum(make_double2(qsdf::finish(acc), 0.0));
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
@@ -81,9 +89,6 @@ __global__ void __launch_bounds__(256) k_expec_dm(const typename Cplx<R>::T* __r
 // FP32 dot products, every contribution added to one per-thread accumulator
 // with TwoSum, so the loop needs no FP64 instruction; each thread rounds its
 // sum to double once.  The imaginary part of the result is exactly zero.
-__device__ __forceinline__ qsdf::df to_df(double x) { return qsdf::split(x); }
-__device__ __forceinline__ qsdf::df to_df(float x) { return qsdf::df{x, 0.0f}; }
-
 // A term as the kernel reads it from shared memory: h already split.
 struct TermDf {
   uint64_t xy, yz;
@@ -255,9 +260,9 @@ __global__ void __launch_bounds__(1024) k_reduce_final(const double2* __restrict
 cudaError_t launch_norm(qs_prec prec, const void* amps, int ns, double2* partials, cudaStream_t st) {
   const uint64_t n = 1ull << ns;
   if (prec == QS_C128)
-    k_norm<double><<<kReduceBlocks, 256, 0, st>>>(static_cast<const double2*>(amps), n, partials);
+    k_norm<double><<<kNormBlocks, 256, 0, st>>>(static_cast<const double2*>(amps), n, partials);
   else
-    k_norm<float><<<kReduceBlocks, 256, 0, st>>>(static_cast<const float2*>(amps), n, partials);
+    k_norm<float><<<kNormBlocks, 256, 0, st>>>(static_cast<const float2*>(amps), n, partials);
   return cudaGetLastError();
 }
 
@@ -300,8 +305,9 @@ cudaError_t launch_expec_sv(qs_prec prec, const void* amps, int nq, const PauliT
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_final(const double2* partials, double2* result, int accumulate, cudaStream_t st) {
-  k_reduce_final<<<1, 1024, 0, st>>>(partials, kReduceBlocks, result, accumulate);
+cudaError_t launch_reduce_final(const double2* partials, double2* result, int accumulate, cudaStream_t st,
+                                int nblocks) {
+  k_reduce_final<<<1, 1024, 0, st>>>(partials, nblocks, result, accumulate);
   return cudaGetLastError();
 }
 
