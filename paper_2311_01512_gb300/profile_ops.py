@@ -14,6 +14,14 @@ with the kernel sources' digest:
 
     python -m paper_2311_01512_gb300.profile_ops --qubits 28 --traffic-csv traffic28.csv \
         --scale-to 30 --out profiles/dram_traffic.json
+
+With --all it instead launches every kernel family of the library once, on
+a statevector of --qubits qubits in both precisions and a density matrix of
+--qubits / 2 qubits (its Choi vector as large): the streaming gates, the
+tensor-core gates on 2-6 targets, SWAP, the channels, the superoperator and
+Kraus map, the partial trace, the expectation kernels, norm and trace, the
+fused-block composition.  It is the sequence for a per-kernel table of DRAM
+bytes and times.
 """
 
 import argparse
@@ -25,7 +33,7 @@ import numpy as np
 # launch order of one repetition -> the bench's kernel family names
 _FAMILIES = {"k_gate1_df": ["k_gate1"], "k_diag_df": ["k_diag"], "k_gadget_df": ["k_gadget"],
              "k_dense_ozaki<3": ["k_dense<2>", "k_dense<3>"], "k_dense_ozaki<4": ["k_dense<4>"],
-             "k_dense_ozaki<5": ["k_dense<5>"], "k_dense_tc<5>": ["c64 k_dense<5>"]}
+             "k_dense_ozaki<5": ["k_dense<5>"], "k_dense_tc<5": ["c64 k_dense<5>"]}
 
 
 def summarize_traffic(path, qubits, scale_to, out):
@@ -63,9 +71,13 @@ def main(argv=None):
     ap.add_argument("--traffic-csv")
     ap.add_argument("--scale-to", type=int, default=30)
     ap.add_argument("--out", default="profiles/dram_traffic.json")
+    ap.add_argument("--all", action="store_true")
     args = ap.parse_args(argv)
     if args.traffic_csv:
         summarize_traffic(args.traffic_csv, args.qubits, args.scale_to, args.out)
+        return
+    if args.all:
+        every_kernel(args.qubits)
         return
     import torch
     from . import qs
@@ -95,6 +107,75 @@ def main(argv=None):
     print("norms", qs.qs_calc_norm_or_trace(s128.handle).real, qs.qs_calc_norm_or_trace(s64.handle).real)
     s128.close()
     s64.close()
+
+
+def every_kernel(nq):
+    import torch
+    from . import qs
+    from . import workloads as wl
+    stream = torch.cuda.Stream()
+    rng = np.random.default_rng(4)
+    with torch.cuda.stream(stream):
+        psi = torch.randn(1 << nq, dtype=torch.complex128, device="cuda")
+        psi /= torch.linalg.vector_norm(psi)
+    stream.synchronize()
+    u = wl.haar_unitary(2, rng)
+    mats = {n: wl.haar_unitary(1 << n, rng) for n in range(2, 7)}
+    targets = {2: [5, 19], 3: [2, 13, 21], 4: [2, 9, 13, 21], 5: [0, 4, 9, 17, nq - 2], 6: [1, 4, 9, 12, 17, nq - 3]}
+    diag = np.exp(1j * rng.uniform(0, 2 * np.pi, 8))
+    paulis, coeffs = wl.random_pauli_sum(nq, 8, rng)
+    zs = np.where(rng.random((16, nq)) < 0.4, 3, 0).astype(np.int32)
+    for prec in (qs.QS_C128, qs.QS_C64):
+        with torch.cuda.stream(stream):
+            t = psi if prec == qs.QS_C128 else psi.to(torch.complex64)
+        stream.synchronize()
+        st = qs.State(nq, prec=prec, stream=stream, storage=t)
+        h = st.handle
+        qs.qs_apply_ctrl_multi_target(h, [], [17], u)                       # one-target gate
+        qs.qs_apply_diagonal(h, [1, 7, 20], diag)                            # diagonal
+        qs.qs_apply_pauli_gadget(h, [0, 3, 8, 15, 22, nq - 1], [1, 2, 3, 1, 2, 3], 0.4)   # gadget
+        qs.qs_apply_pauli_gadget(h, [0, 4, 9, 17], [3, 3, 3, 3], 0.4)        # phase gadget
+        for n in range(2, 7 if prec == qs.QS_C64 else 6):
+            qs.qs_apply_ctrl_multi_target(h, [], targets[n], mats[n])        # tensor-core gates
+        qs.qs_apply_swap(h, 3, 17)
+        qs.qs_expec_pauli_sum(h, paulis, coeffs)                             # off-diagonal terms
+        qs.qs_expec_pauli_sum(h, zs, rng.standard_normal(16))                # Walsh-Hadamard diagonal terms
+        qs.qs_calc_norm_or_trace(h)
+        st.close()
+        del t
+    # fused blocks: FP64 composition, then the blocks
+    circ = qs.Circuit(nq, wl.unitary_circuit(nq, 12, rng))
+    circ.plan(qs.QS_PLAN_GREEDY, 4)
+    st = qs.State(nq, prec=qs.QS_C128, stream=stream, storage=psi)
+    circ.apply(st.handle)
+    qs.qs_synchronize(st.handle)
+    st.close()
+    circ.close()
+    del psi
+    torch.cuda.empty_cache()
+    # density matrix of nq / 2 qubits
+    nd = nq // 2
+    rho = qs.State(nd, density=True, prec=qs.QS_C128, stream=stream)
+    sv = qs.State(nd, prec=qs.QS_C128, stream=stream)
+    sv.set_amps(wl.random_statevector(nd, rng))
+    qs.qs_init_pure_densmatr(rho.handle, sv.handle, 1.0, 0)
+    h = rho.handle
+    qs.qs_apply_dephasing(h, 1, 0.05)
+    qs.qs_apply_two_qubit_dephasing(h, 1, 5, 0.05)
+    qs.qs_apply_depolarising(h, 2, 0.05)
+    qs.qs_apply_two_qubit_depolarising(h, 2, 6, 0.05)
+    qs.qs_apply_damping(h, 3, 0.05)
+    qs.qs_apply_pauli_channel(h, 4, 0.02, 0.03, 0.01)
+    qs.qs_apply_kraus(h, [0, 7], wl.haar_kraus(2, 4, rng))                   # superoperator + 4-target pass
+    qs.qs_apply_ctrl_multi_target(h, [], [1, 6], mats[2])                    # one superoperator pass
+    pd, cd = wl.random_pauli_sum(nd, 20, rng)
+    qs.qs_expec_pauli_sum(h, pd, cd)
+    red = rho.partial_trace([1, 4, 7])
+    qs.qs_calc_norm_or_trace(h)
+    red.close()
+    rho.close()
+    sv.close()
+    print("every kernel launched")
 
 
 if __name__ == "__main__":
