@@ -2,6 +2,7 @@
 // algorithms", local parts): decoherence channels, the Kraus superoperator
 // build, the partial trace, and state initialisation.
 #include "qs_device.cuh"
+#include "qs_df.cuh"
 
 namespace qsk {
 
@@ -177,6 +178,32 @@ __global__ void __launch_bounds__(256) k_dm_from_pure(typename Cplx<R>::T* __res
   }
 }
 
+// complex128 in double-float: w conj(psi_k) once per element as a pair, then
+// two two-term dot products (three when accumulating), each rounded once.
+__global__ void __launch_bounds__(256) k_dm_from_pure_df(double2* __restrict__ rho, const double2* __restrict__ psi,
+                                                         int nq, qsdf::df w, int accumulate) {
+  using qsdf::df;
+  const uint64_t total = 1ull << (2 * nq), mask = (1ull << nq) - 1;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const df one{1.0f, 0.0f};
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const double2 a = psi[i & mask], b = psi[i >> nq];
+    const df ar = qsdf::split(a.x), ai = qsdf::split(a.y);
+    const df cr = qsdf::dot_result(qsdf::dot_first(w, qsdf::split(b.x)));   // c = w psi_k
+    const df ci = qsdf::dot_result(qsdf::dot_first(w, qsdf::split(b.y)));
+    qsdf::dot_acc re = qsdf::dot_first(ar, cr);   // a conj(c)
+    qsdf::dot_add(re, ai, ci);
+    qsdf::dot_acc im = qsdf::dot_first(ai, cr);
+    qsdf::dot_add(im, qsdf::neg(ar), ci);
+    if (accumulate) {
+      const double2 o = rho[i];
+      qsdf::dot_add(re, qsdf::split(o.x), one);
+      qsdf::dot_add(im, qsdf::split(o.y), one);
+    }
+    rho[i] = make_double2(qsdf::finish(re), qsdf::finish(im));
+  }
+}
+
 template <typename R>
 __global__ void k_set_first_one(typename Cplx<R>::T* amps) {
   amps[0] = mk<R>((R)1, (R)0);
@@ -225,8 +252,8 @@ cudaError_t launch_dm_from_pure(qs_prec prec, void* rho, const void* psi, int nq
                                 int accumulate, cudaStream_t st) {
   const unsigned g = grid_for(1ull << (2 * nq), 256, num_sms() * kStreamBlocksPerSM);
   if (prec == QS_C128)
-    k_dm_from_pure<double><<<g, 256, 0, st>>>(static_cast<double2*>(rho), static_cast<const double2*>(psi), nq,
-                                              weight, accumulate);
+    k_dm_from_pure_df<<<g, 256, 0, st>>>(static_cast<double2*>(rho), static_cast<const double2*>(psi), nq,
+                                         qsdf::split_const(weight), accumulate);
   else
     k_dm_from_pure<float><<<g, 256, 0, st>>>(static_cast<float2*>(rho), static_cast<const float2*>(psi), nq,
                                              (float)weight, accumulate);

@@ -189,51 +189,104 @@ __global__ void __launch_bounds__(256) k_expec_sv(const typename Cplx<R>::T* __r
 // lanes gives W_j = sum_m |alpha_{base+m}|^2 (-1)^{popc(j & m)} in lane j, so
 // the tile's share of term n is (-1)^{popc(base & z_n)} W_{z_n mod 32}: five
 // butterfly steps per amplitude and one multiply-add per 32 terms replace one
-// add per term.  Needs N >= 5 (whole warps of amplitudes).
-template <typename R>
+// add per term.  All in double-float (no FP64 in the loop; each thread rounds
+// its sum once).  Needs N >= 5 (whole warps of amplitudes).
+__device__ __forceinline__ qsdf::df df_add(qsdf::df a, qsdf::df b) {
+  const float s = a.h + b.h;                    // TwoSum of the high parts
+  const float bb = s - a.h;
+  const float e = (a.h - (s - bb)) + (b.h - bb) + (a.l + b.l);
+  const float h = s + e;                        // renormalise
+  return qsdf::df{h, e - (h - s)};
+}
+
+// A diagonal term in shared memory: its Z mask and the two halves of its
+// coefficient (16 bytes: one load per lane).
+struct ZTermDf {
+  uint64_t z;
+  float hh, hl;
+};
+
+// A warp takes tiles of 32 U consecutive amplitudes (U transforms whose loads
+// are all in flight together), so each term is read from shared memory once
+// per U transforms.
+template <typename R, int U>
 __global__ void __launch_bounds__(256) k_expec_sv_diag(const typename Cplx<R>::T* __restrict__ psi, int nq,
                                                        const PauliTerm* __restrict__ terms, int nterms,
                                                        double2* __restrict__ partials) {
+  using qsdf::df;
+  extern __shared__ ZTermDf tz[];
+  for (int n = threadIdx.x; n < nterms; n += blockDim.x) {
+    const PauliTerm t = terms[n];
+    const df h = qsdf::split(t.h);
+    tz[n] = ZTermDf{t.yz, h.h, h.l};
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31;
-  double acc = 0.0;
-  const uint64_t dim = 1ull << nq;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  // dim and stride are multiples of 32: every lane of a warp runs the same iterations
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride) {
-    const auto a = psi[i];
-    double w = (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+  qsdf::dot_acc acc{0.0f, 0.0f};
+  const uint64_t ntiles = (1ull << nq) / (32 * U);
+  const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t tile = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tile < ntiles;
+       tile += nwarps) {
+    const uint64_t base = tile * (32 * U);
+    typename Cplx<R>::T a[U];
 #pragma unroll
-    for (int b = 1; b < 32; b <<= 1) {
-      const double o = __shfl_xor_sync(0xFFFFFFFFu, w, b);
-      w = (lane & b) ? (o - w) : (w + o);
+    for (int k = 0; k < U; ++k) a[k] = psi[base + 32 * k + lane];
+    df w[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const df ar = to_df(a[k].x), ai = to_df(a[k].y);
+      qsdf::dot_acc pa = qsdf::dot_first(ar, ar);
+      qsdf::dot_add(pa, ai, ai);
+      w[k] = qsdf::dot_result(pa);
+#pragma unroll
+      for (int b = 1; b < 32; b <<= 1) {
+        // lanes with bit b set keep o - w, the others w + o (one TwoSum each)
+        const df o{__shfl_xor_sync(0xFFFFFFFFu, w[k].h, b), __shfl_xor_sync(0xFFFFFFFFu, w[k].l, b)};
+        const float sg = (lane & b) ? -1.0f : 1.0f;
+        w[k] = df_add(df{sg * w[k].h, sg * w[k].l}, o);
+      }
     }
-    const uint64_t base = i & ~31ull;
     for (int n0 = 0; n0 < nterms; n0 += 32) {
       const int n = n0 + lane;
-      uint64_t z = 0;
-      double h = 0.0;
-      if (n < nterms) {
-        z = terms[n].yz;
-        h = terms[n].h;
+      ZTermDf t{0, 0.0f, 0.0f};
+      if (n < nterms) t = tz[n];
+      const int src = (int)(t.z & 31u);
+      const bool odd = parity64(base & t.z);
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const df wz{__shfl_sync(0xFFFFFFFFu, w[k].h, src), __shfl_sync(0xFFFFFFFFu, w[k].l, src)};
+        const bool neg = odd ^ (bool)(__popc((unsigned)(32 * k) & (unsigned)t.z) & 1);
+        qsdf::dot_add(acc, neg ? qsdf::neg(df{t.hh, t.hl}) : df{t.hh, t.hl}, wz);
       }
-      const double wz = __shfl_sync(0xFFFFFFFFu, w, (int)(z & 31u));
-      acc += (parity64(base & z) ? -h : h) * wz;
     }
   }
-  const double2 s = block_sum(make_double2(acc, 0.0));
+  const double2 s = block_sum(make_double2(qsdf::finish(acc), 0.0));
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+template <typename R, int U>
+static cudaError_t launch_diag(const void* amps, int nq, const PauliTerm* terms, int nterms, double2* partials,
+                               cudaStream_t st) {
+  static bool attr_done = false;
+  if (!attr_done) {
+    const cudaError_t e = cudaFuncSetAttribute(k_expec_sv_diag<R, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(sizeof(ZTermDf) * kTermChunk));
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  k_expec_sv_diag<R, U><<<kReduceBlocks, 256, sizeof(ZTermDf) * (size_t)nterms, st>>>(
+      static_cast<const typename Cplx<R>::T*>(amps), nq, terms, nterms, partials);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_expec_sv_diag(qs_prec prec, const void* amps, int nq, const PauliTerm* terms, int nterms,
                                  double2* partials, cudaStream_t st) {
-  if (nq < 5) return cudaErrorInvalidValue;
+  if (nq < 5 || nterms > kTermChunk) return cudaErrorInvalidValue;
   if (prec == QS_C128)
-    k_expec_sv_diag<double><<<kReduceBlocks, 256, 0, st>>>(static_cast<const double2*>(amps), nq, terms, nterms,
-                                                           partials);
-  else
-    k_expec_sv_diag<float><<<kReduceBlocks, 256, 0, st>>>(static_cast<const float2*>(amps), nq, terms, nterms,
-                                                          partials);
-  return cudaGetLastError();
+    return nq >= 7 ? launch_diag<double, 4>(amps, nq, terms, nterms, partials, st)
+                   : launch_diag<double, 1>(amps, nq, terms, nterms, partials, st);
+  return nq >= 7 ? launch_diag<float, 4>(amps, nq, terms, nterms, partials, st)
+                 : launch_diag<float, 1>(amps, nq, terms, nterms, partials, st);
 }
 
 // Stage two: one block of 1024 threads; thread j adds partials j, j + 1024, ...
