@@ -24,9 +24,9 @@
 // they are in flight during the MMAs and the epilogue; with two buffers of
 // slices and accumulators (NBUF = 2) the epilogue of tile i - 1 would run
 // while the tensor cores work on tile i.  The row maxima of tile i + 1 are
-// taken after the epilogue, so a tile costs two CTA barriers.  The MMAs are
-// issued by one thread in each of warps 0..3, which take the levels {6},
-// {5, 0}, {4, 1}, {3, 2}: seven slice products each.  Every wait is bounded:
+// taken after the epilogue, so a tile costs two CTA barriers.  Thread 0
+// issues the MMAs: one per A slice and K chunk, against all the B slices it
+// pairs with (see mma_tile).  Every wait is bounded:
 // on timeout the kernel records an error code, frees its tensor memory and
 // returns.
 #include "qs_device.cuh"
@@ -86,18 +86,30 @@ __device__ __forceinline__ double realified(const TcParams& p, int D, int k, int
   return c == 0 ? (cp == 0 ? mr : -mi) : (cp == 0 ? mi : mr);
 }
 
-// The MMAs of level L (slice pairs s + t = L) into the accumulator at d_tmem.
-// adesc / bdesc: descriptors of slice 0 of A and B; slices are abytes /
-// bbytes apart, 16-column K chunks 256 bytes apart (encoded address >> 4).
-template <int L, int KCH>
-__device__ __forceinline__ void mma_level(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t abytes, uint32_t bbytes) {
+// All slice products of one tile.  B's slices lie back to back in shared
+// memory (slice t at t * bbytes), so for A slice s one MMA against the first
+// 7 - s slices of B, with its accumulator starting at level s, adds A_s B_t
+// into level s + t for every t <= 6 - s at once: each A slice is read once
+// per 16-column K chunk.  Products wider than 256 columns are cut into
+// 256-column MMAs.  The first MMA (s = 0, first K chunk) initialises all
+// levels.  adesc / bdesc: descriptors of slice 0 of A and B; K chunks are
+// 256 bytes apart, 8-row groups of B kdim * 16 bytes (encoded address >> 4).
+template <int N, int KCH>
+__device__ __forceinline__ void mma_tile(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t abytes) {
+  constexpr int K = 16 * KCH;
 #pragma unroll
-  for (int s = 0; s <= L; ++s)
+  for (int s = 0; s < kS; ++s) {
+    constexpr int kMax = 256;
 #pragma unroll
-    for (int kk = 0; kk < KCH; ++kk)
-      mma_bf16(d_tmem, adesc + ((s * abytes + kk * 256) >> 4), bdesc + (((L - s) * bbytes + kk * 256) >> 4), idesc,
-               (s | kk) != 0);
+    for (int c0 = 0; c0 < (kS - s) * N; c0 += kMax) {
+      const int w = (kS - s) * N - c0 < kMax ? (kS - s) * N - c0 : kMax;
+      const uint32_t idesc = idesc_bf16(kRows, w);
+#pragma unroll
+      for (int kk = 0; kk < KCH; ++kk)
+        mma_bf16(d_tmem + (uint32_t)(s * N + c0), adesc + ((s * abytes + kk * 256) >> 4),
+                 bdesc + (((uint32_t)c0 * K * 2 + kk * 256) >> 4), idesc, (s | kk) != 0);
+    }
+  }
 }
 
 }  // namespace
@@ -170,7 +182,7 @@ __global__ void __launch_bounds__(THREADS, CTAS) k_dense_ozaki(double2* __restri
   if (tid == 0) {
     tile_base[0] = insert_zeros(blockIdx.x, p.hi_ins, p.nhi) | p.ctrl_mask;
 #pragma unroll
-    for (int b = 0; b < NBUF; ++b) mbar_init(mbar + b, 4);      // one commit from each MMA-issuing thread
+    for (int b = 0; b < NBUF; ++b) mbar_init(mbar + b, 1);      // one commit per tile
   }
   if (warp == 0) {
     tmem_alloc(tmem_slot, TCOLS);
@@ -181,7 +193,6 @@ __global__ void __launch_bounds__(THREADS, CTAS) k_dense_ozaki(double2* __restri
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t idesc = idesc_bf16(kRows, N);
   constexpr uint32_t sbo = K * 16;
 
   const int g = 32 * (warp & 3) + lane;       // row (tensor-memory lane)
@@ -190,8 +201,7 @@ __global__ void __launch_bounds__(THREADS, CTAS) k_dense_ozaki(double2* __restri
   const bool row_ok = g < (1 << row_bits);
   const uint64_t roff = rowoff[g];
   const uint32_t lane_addr = (uint32_t)(32 * (warp & 3)) << 16;
-  const bool issuer = lane == 0 && warp < 4;
-  const int helper = THREADS > kRows ? kRows : 0;   // computes tile bases (not an MMA issuer)
+  const int helper = THREADS > kRows ? kRows : 0;   // computes tile bases
   // target offsets of this thread's amplitudes: registers when few
   constexpr bool kRegOff = EPT <= 4;
   uint64_t toffr[kRegOff ? EPT : 1];
@@ -284,23 +294,10 @@ __global__ void __launch_bounds__(THREADS, CTAS) k_dense_ozaki(double2* __restri
     }
     fence_proxy_async();
     __syncthreads();
-    if (issuer) {
+    if (tid == 0) {
       fence_after_sync();
       const uint64_t ad = smem_desc(smem_u32(A), 128, sbo), bd = smem_desc(smem_u32(b_dig), 128, sbo);
-      const uint32_t d = tmem + (uint32_t)(b * LCOLS);
-      constexpr int KCH = K / 16;
-      if (warp == 0) {
-        mma_level<6, KCH>(d + 6 * N, ad, bd, idesc, ABYTES, BBYTES);
-      } else if (warp == 1) {
-        mma_level<5, KCH>(d + 5 * N, ad, bd, idesc, ABYTES, BBYTES);
-        mma_level<0, KCH>(d, ad, bd, idesc, ABYTES, BBYTES);
-      } else if (warp == 2) {
-        mma_level<4, KCH>(d + 4 * N, ad, bd, idesc, ABYTES, BBYTES);
-        mma_level<1, KCH>(d + N, ad, bd, idesc, ABYTES, BBYTES);
-      } else {
-        mma_level<3, KCH>(d + 3 * N, ad, bd, idesc, ABYTES, BBYTES);
-        mma_level<2, KCH>(d + 2 * N, ad, bd, idesc, ABYTES, BBYTES);
-      }
+      mma_tile<N, K / 16>(tmem + (uint32_t)(b * LCOLS), ad, bd, ABYTES);
       mma_commit(mbar + b);
     }
     if (cg == 0) rowexp[par * kRows + g] = 0;   // read by every thread of the row before the barrier
