@@ -8,6 +8,12 @@
 // order).  The launch shape (threads per CTA, CTAs per SM, and with it the
 // largest state kept in shared memory) is chosen by timing every candidate on
 // the batch itself.
+//
+// States larger than shared memory are cut into segments (cache blocking):
+// consecutive operations are grouped while the qubits they pair (dense
+// targets, gadget X/Y qubits) together with the five lowest qubits fit in a
+// tile of L qubits; the kernel then moves each tile through shared memory once
+// per segment instead of moving the state once per operation.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -29,9 +35,12 @@ struct qs_batch {
   void* pool = nullptr;
   std::vector<std::vector<qsk::BatchOp>> progs;
   qsk::BatchState* d_states = nullptr;
+  qsk::BatchSeg* d_segs = nullptr;
+  qsk::BatchXlat* d_xlat = nullptr;
   int* d_order = nullptr;
   qsk::BatchOp* d_ops = nullptr;
   int* d_counter = nullptr;
+  long num_segs = 0;
   int threads = 256, ctas = 0, smem_qubits = -1;
   cudaStream_t capture_stream = nullptr;  // own stream for recording (the caller's may be the legacy stream)
   cudaGraph_t graph = nullptr;
@@ -46,11 +55,14 @@ namespace {
 void free_device(qs_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  for (void* p : {(void*)b->d_states, (void*)b->d_order, (void*)b->d_ops, (void*)b->d_counter})
+  for (void* p : {(void*)b->d_states, (void*)b->d_segs, (void*)b->d_xlat, (void*)b->d_order, (void*)b->d_ops,
+                  (void*)b->d_counter})
     if (p) cudaFree(p);
   b->exec = nullptr;
   b->graph = nullptr;
   b->d_states = nullptr;
+  b->d_segs = nullptr;
+  b->d_xlat = nullptr;
   b->d_order = nullptr;
   b->d_ops = nullptr;
   b->d_counter = nullptr;
@@ -74,6 +86,159 @@ int smem_qubits_for(qs_prec prec, int ctas_per_sm) {
   int q = 0;
   while (((size_t)1 << (q + 1)) * amp <= per_cta) ++q;
   return q;
+}
+
+// ---- segment plans (for one tile size L) ------------------------------------
+struct Plan {
+  int L = -1;
+  std::vector<qsk::BatchState> states;
+  std::vector<qsk::BatchSeg> segs;
+  std::vector<qsk::BatchXlat> xlat;   // parallel to the operations
+  qsk::BatchState* d_states = nullptr;
+  qsk::BatchSeg* d_segs = nullptr;
+  qsk::BatchXlat* d_xlat = nullptr;
+  void release() {
+    for (void* p : {(void*)d_states, (void*)d_segs, (void*)d_xlat})
+      if (p) cudaFree(p);
+    d_states = nullptr;
+    d_segs = nullptr;
+    d_xlat = nullptr;
+  }
+};
+
+int popc32(uint32_t x) {
+  int n = 0;
+  for (; x; x &= x - 1) ++n;
+  return n;
+}
+
+// qubits an operation pairs amplitudes across
+uint32_t pairing_mask(const qsk::BatchOp& op) {
+  if (op.kind == 0) {
+    uint32_t m = 0;
+    for (int q = 0; q < op.n; ++q) m |= 1u << op.t[q];
+    return m;
+  }
+  return op.kind == 2 ? op.xy : 0u;
+}
+
+// position of qubit t among the tile qubits, -1 if it is not one
+int local_pos(uint32_t qmask, int t) {
+  return ((qmask >> t) & 1u) ? popc32(qmask & ((1u << t) - 1u)) : -1;
+}
+
+qsk::BatchXlat translate(const qsk::BatchOp& op, uint32_t qmask) {
+  qsk::BatchXlat x{};
+  for (int q = 0; q < 3; ++q) x.lt[q] = -1;
+  if (op.kind == 0) {
+    std::vector<int> lins;
+    for (int q = 0; q < op.n; ++q) {
+      x.lt[q] = (int8_t)local_pos(qmask, op.t[q]);
+      lins.push_back(x.lt[q]);
+    }
+    for (int c = 0; c < 32; ++c) {
+      if (!((op.ctrl >> c) & 1u)) continue;
+      const int p = local_pos(qmask, c);
+      if (p >= 0) {
+        x.lctrl |= 1u << p;
+        lins.push_back(p);
+      } else {
+        x.fctrl |= 1u << c;
+      }
+    }
+    std::sort(lins.begin(), lins.end());
+    x.nlins = (int)lins.size();
+    for (int i = 0; i < x.nlins; ++i) x.lins[i] = (int8_t)lins[i];
+  } else if (op.kind == 1) {
+    for (int q = 0; q < op.n; ++q) x.lt[q] = (int8_t)local_pos(qmask, op.t[q]);
+  } else {
+    for (int b = 0; b < 32; ++b) {
+      const int p = local_pos(qmask, b);
+      if ((op.xy >> b) & 1u) x.lxy |= 1u << p;       // every flip qubit is a tile qubit
+      if ((op.yz >> b) & 1u) {
+        if (p >= 0)
+          x.lyz |= 1u << p;
+        else
+          x.fyz |= 1u << b;
+      }
+    }
+    x.lh = (int8_t)(op.xy ? local_pos(qmask, op.h) : 0);
+  }
+  return x;
+}
+
+// Segments of every state larger than 2^L amplitudes.  Greedy: an operation
+// joins the open segment while the union of pairing qubits and the five
+// lowest qubits stays within L; an operation that alone exceeds it runs in
+// global memory.  The tile qubits are that union, filled up with the lowest
+// remaining qubits.
+void build_plan(Plan& P, int L, const std::vector<int>& nq, const std::vector<qsk::BatchState>& base,
+                const std::vector<qsk::BatchOp>& ops) {
+  P.L = L;
+  P.states = base;
+  P.segs.clear();
+  P.xlat.assign(ops.size(), qsk::BatchXlat{});
+  for (size_t s = 0; s < base.size(); ++s) {
+    qsk::BatchState& st = P.states[s];
+    st.first_seg = (int)P.segs.size();
+    st.nsegs = 0;
+    if (nq[s] <= L) continue;
+    const uint32_t low = (1u << std::min(5, nq[s])) - 1u;
+    auto emit = [&](int first, int n, uint32_t U, bool tiled) {
+      qsk::BatchSeg g{};
+      g.first_op = first;
+      g.nops = n;
+      g.L = tiled ? L : 0;
+      if (tiled) {
+        uint32_t Q = low | U;
+        for (int b = 0; popc32(Q) < L; ++b) Q |= 1u << b;
+        for (int b = 0, i = 0; b < 32; ++b)
+          if ((Q >> b) & 1u) g.q[i++] = (int8_t)b;
+        for (int k = first; k < first + n; ++k) P.xlat[k] = translate(ops[k], Q);
+      }
+      P.segs.push_back(g);
+    };
+    int k0 = st.first_op, cnt = 0;
+    uint32_t U = 0;
+    for (int k = st.first_op; k < st.first_op + st.nops; ++k) {
+      const uint32_t pm = pairing_mask(ops[k]);
+      if (popc32(low | pm) > L) {
+        if (cnt) emit(k0, cnt, U, true);
+        emit(k, 1, 0u, false);
+        k0 = k + 1;
+        cnt = 0;
+        U = 0;
+        continue;
+      }
+      if (popc32(low | U | pm) > L) {
+        emit(k0, cnt, U, true);
+        k0 = k;
+        cnt = 0;
+        U = 0;
+      }
+      U |= pm;
+      ++cnt;
+    }
+    if (cnt) emit(k0, cnt, U, true);
+    st.nsegs = (int)P.segs.size() - st.first_seg;
+  }
+}
+
+bool upload_plan(Plan& P) {
+  const size_t S = P.states.size();
+  if (cudaMalloc(&P.d_states, sizeof(qsk::BatchState) * S) != cudaSuccess ||
+      cudaMalloc(&P.d_segs, sizeof(qsk::BatchSeg) * std::max<size_t>(1, P.segs.size())) != cudaSuccess ||
+      cudaMalloc(&P.d_xlat, sizeof(qsk::BatchXlat) * std::max<size_t>(1, P.xlat.size())) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (cudaMemcpy(P.d_states, P.states.data(), sizeof(qsk::BatchState) * S, cudaMemcpyHostToDevice) != cudaSuccess)
+    return false;
+  if (!P.segs.empty() && cudaMemcpy(P.d_segs, P.segs.data(), sizeof(qsk::BatchSeg) * P.segs.size(),
+                                    cudaMemcpyHostToDevice) != cudaSuccess)
+    return false;
+  return P.xlat.empty() || cudaMemcpy(P.d_xlat, P.xlat.data(), sizeof(qsk::BatchXlat) * P.xlat.size(),
+                                      cudaMemcpyHostToDevice) == cudaSuccess;
 }
 
 }  // namespace
@@ -212,22 +377,21 @@ qs_status qs_batch_compile(qs_batch* b, int autotune) {
     return ((double)(1ull << b->nq[x]) * (1 + b->progs[x].size())) >
            ((double)(1ull << b->nq[y]) * (1 + b->progs[y].size()));
   });
-  if (cudaMalloc(&b->d_states, sizeof(qsk::BatchState) * S) != cudaSuccess ||
-      cudaMalloc(&b->d_order, sizeof(int) * S) != cudaSuccess ||
+  if (cudaMalloc(&b->d_order, sizeof(int) * S) != cudaSuccess ||
       cudaMalloc(&b->d_ops, sizeof(qsk::BatchOp) * std::max<size_t>(1, ops.size())) != cudaSuccess ||
       cudaMalloc(&b->d_counter, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     free_device(b);
     return QS_ERR_OOM;
   }
-  if (cudaMemcpy(b->d_states, states.data(), sizeof(qsk::BatchState) * S, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->d_order, order.data(), sizeof(int) * S, cudaMemcpyHostToDevice) != cudaSuccess ||
+  if (cudaMemcpy(b->d_order, order.data(), sizeof(int) * S, cudaMemcpyHostToDevice) != cudaSuccess ||
       (!ops.empty() &&
        cudaMemcpy(b->d_ops, ops.data(), sizeof(qsk::BatchOp) * ops.size(), cudaMemcpyHostToDevice) != cudaSuccess)) {
     free_device(b);
     return QS_ERR_CUDA;
   }
-  // launch-shape candidates: (threads, CTAs per SM)
+  // launch-shape candidates: (threads, CTAs per SM); each shared-memory size
+  // (tile size) has its own segment plan
   const int sms = qsk::num_sms();
   if (qsk::batch_set_max_smem(200 * 1024) != cudaSuccess) {
     cudaGetLastError();
@@ -235,19 +399,38 @@ qs_status qs_batch_compile(qs_batch* b, int autotune) {
   }
   std::vector<std::pair<int, int>> cands;
   if (autotune)
-    cands = {{128, 4}, {256, 2}, {256, 4}, {512, 1}, {512, 2}, {1024, 1}};
+    cands = {{128, 4}, {256, 2}, {256, 4}, {512, 1}, {512, 2}};
   else
     cands = {{256, 2}};
+  std::vector<Plan> plans;
+  plans.reserve(cands.size());       // pointers into it stay valid
+  auto plan_for = [&](int L) -> Plan* {
+    for (auto& P : plans)
+      if (P.L == L) return &P;
+    plans.emplace_back();
+    build_plan(plans.back(), L, b->nq, states, ops);
+    return &plans.back();
+  };
+  for (const auto& c : cands) {
+    Plan* P = plan_for(smem_qubits_for(b->prec, c.second));
+    if (!P->d_states && !upload_plan(*P)) {
+      for (auto& Q : plans) Q.release();
+      free_device(b);
+      return QS_ERR_OOM;
+    }
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
+  int best_plan = -1;
   for (const auto& c : cands) {
     const int sq = smem_qubits_for(b->prec, c.second);
+    Plan* P = plan_for(sq);
     if (cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream) != cudaSuccess) return QS_ERR_CUDA;
     cudaEventRecord(e0, b->stream);
-    if (qsk::launch_batch(b->prec, b->pool, b->d_states, b->d_order, S, b->d_ops, b->d_counter, c.first,
-                          sms * c.second, sq, b->stream) != cudaSuccess) {
+    if (qsk::launch_batch(b->prec, b->pool, P->d_states, b->d_order, S, b->d_ops, P->d_segs, P->d_xlat,
+                          b->d_counter, c.first, sms * c.second, sq, b->stream) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
@@ -260,11 +443,18 @@ qs_status qs_batch_compile(qs_batch* b, int autotune) {
       b->threads = c.first;
       b->ctas = sms * c.second;
       b->smem_qubits = sq;
+      best_plan = (int)(P - plans.data());
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (b->ctas == 0) return QS_ERR_CUDA;
+  for (int i = 0; i < (int)plans.size(); ++i)
+    if (i != best_plan) plans[i].release();
+  if (b->ctas == 0 || best_plan < 0) return QS_ERR_CUDA;
+  b->d_states = plans[best_plan].d_states;
+  b->d_segs = plans[best_plan].d_segs;
+  b->d_xlat = plans[best_plan].d_xlat;
+  b->num_segs = (long)plans[best_plan].segs.size();
   b->best_ms = best;
   // record on the batch's own stream: reset the work counter, one persistent launch
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return QS_ERR_CUDA;
@@ -276,8 +466,8 @@ qs_status qs_batch_compile(qs_batch* b, int autotune) {
   }
   cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->capture_stream);
   if (e == cudaSuccess)
-    e = qsk::launch_batch(b->prec, b->pool, b->d_states, b->d_order, S, b->d_ops, b->d_counter, b->threads, b->ctas,
-                          b->smem_qubits, b->capture_stream);
+    e = qsk::launch_batch(b->prec, b->pool, b->d_states, b->d_order, S, b->d_ops, b->d_segs, b->d_xlat, b->d_counter,
+                          b->threads, b->ctas, b->smem_qubits, b->capture_stream);
   cudaGraph_t g = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &g);
   if (e != cudaSuccess || e2 != cudaSuccess || !g) {

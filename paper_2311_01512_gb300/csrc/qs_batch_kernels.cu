@@ -19,26 +19,97 @@ namespace {
 
 using qsdf::df;
 
-// ---- arithmetic policies -------------------------------------------------
-struct ArithF32 {
-  using T2 = float2;
-  struct C {
-    float re, im;
-  };
-  __device__ static C load(const T2* p) {
-    const float2 v = *p;
-    return C{v.x, v.y};
-  }
-  __device__ static void store(T2* p, float re, float im) { *p = make_float2(re, im); }
+// ---- the operation's constants --------------------------------------------
+// Converted once per operation into shared memory (complex64: floats;
+// complex128: double-float pairs), up to 32 reals: a 4x4 matrix, 8 diagonal
+// entries, or cos / sin of a gadget.  Converting them per amplitude instead
+// would put two f64 -> f32 conversions (FP64 rate) or two integer splits on
+// every multiply.
+template <typename T2>
+struct Konst;
+template <>
+struct Konst<float2> {
+  using K = float;
+  __device__ static K conv(double v) { return (float)v; }
+};
+template <>
+struct Konst<double2> {
+  using K = df;
+  __device__ static K conv(double v) { return qsdf::split(v); }
 };
 
-// y = sum_k m_k x_k (complex) over K terms, FP32
+template <typename T2>
+using KT = typename Konst<T2>::K;
+
+template <typename T2>
+__device__ __forceinline__ void load_consts(const BatchOp& op, typename Konst<T2>::K* kc) {
+  const int kind = op.kind;
+  const int nreal = kind == 0 ? 2 << (2 * op.n) : (kind == 1 ? 2 << op.n : 2);
+  for (int i = threadIdx.x; i < nreal; i += blockDim.x)
+    kc[i] = Konst<T2>::conv(kind == 2 ? (i == 0 ? op.c : op.s) : op.m[i]);
+}
+
+// ---- element access -----------------------------------------------------------
+// complex64: float2 everywhere.  complex128: double2 in global memory (split
+// into double-float pairs on load, rounded to double on store, one DADD per
+// real), and in shared memory float4 pairs (re.h, re.l, im.h, im.l), so a state
+// or a tile in shared memory goes through all its operations without a split
+// or a rounding to double in between.
+struct CF {
+  float re, im;
+};
+struct CDF {
+  df re, im;
+};
+
+__device__ __forceinline__ CF ld(const float2* a, uint32_t i) {
+  const float2 v = a[i];
+  return CF{v.x, v.y};
+}
+__device__ __forceinline__ CDF ld(const double2* a, uint32_t i) {
+  const double2 v = a[i];
+  return CDF{qsdf::split(v.x), qsdf::split(v.y)};
+}
+__device__ __forceinline__ CDF ld(const float4* a, uint32_t i) {
+  const float4 v = a[i];
+  return CDF{df{v.x, v.y}, df{v.z, v.w}};
+}
+__device__ __forceinline__ void st(double2* a, uint32_t i, const qsdf::dot_acc& re, const qsdf::dot_acc& im) {
+  a[i] = make_double2(qsdf::finish(re), qsdf::finish(im));
+}
+__device__ __forceinline__ void st(float4* a, uint32_t i, const qsdf::dot_acc& re, const qsdf::dot_acc& im) {
+  const df r = qsdf::dot_result(re), m = qsdf::dot_result(im);
+  a[i] = make_float4(r.h, r.l, m.h, m.l);
+}
+
+// shared-memory form of a global amplitude and back
+template <typename T2>
+struct SmemOf;
+template <>
+struct SmemOf<float2> {
+  using T = float2;
+  __device__ static T in(float2 v) { return v; }
+  __device__ static float2 out(T v) { return v; }
+};
+template <>
+struct SmemOf<double2> {
+  using T = float4;
+  __device__ static T in(double2 v) {
+    const df r = qsdf::split(v.x), m = qsdf::split(v.y);
+    return make_float4(r.h, r.l, m.h, m.l);
+  }
+  __device__ static double2 out(T v) {
+    return make_double2(qsdf::to_double(v.x) + qsdf::to_double(v.y), qsdf::to_double(v.z) + qsdf::to_double(v.w));
+  }
+};
+
+// ---- complex dot products y = sum_k m_k x_k --------------------------------
 template <int K>
-__device__ __forceinline__ float2 cdot_f32(const double* m, const ArithF32::C* x) {
+__device__ __forceinline__ float2 cdot_f32(const float* m, const CF* x) {
   float re = 0.f, im = 0.f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const float mr = (float)m[2 * k], mi = (float)m[2 * k + 1];
+    const float mr = m[2 * k], mi = m[2 * k + 1];
     re = fmaf(mr, x[k].re, re);
     re = fmaf(-mi, x[k].im, re);
     im = fmaf(mr, x[k].im, im);
@@ -47,178 +118,239 @@ __device__ __forceinline__ float2 cdot_f32(const double* m, const ArithF32::C* x
   return make_float2(re, im);
 }
 
-struct CDF {
-  df re, im;
-};
-
-__device__ __forceinline__ CDF load_df(const double2* p) {
-  const double2 v = *p;
-  return CDF{qsdf::split(v.x), qsdf::split(v.y)};
-}
-
 template <int K>
-__device__ __forceinline__ double2 cdot_df(const double* m, const CDF* x) {
-  CDF c = {qsdf::split(m[0]), qsdf::split(m[1])};
-  qsdf::dot_acc re = qsdf::dot_first(c.re, x[0].re);
-  qsdf::dot_add(re, qsdf::neg(c.im), x[0].im);
-  qsdf::dot_acc im = qsdf::dot_first(c.re, x[0].im);
-  qsdf::dot_add(im, c.im, x[0].re);
+__device__ __forceinline__ void cdot_df(const df* m, const CDF* x, qsdf::dot_acc& re, qsdf::dot_acc& im) {
+  re = qsdf::dot_first(m[0], x[0].re);
+  qsdf::dot_add(re, qsdf::neg(m[1]), x[0].im);
+  im = qsdf::dot_first(m[0], x[0].im);
+  qsdf::dot_add(im, m[1], x[0].re);
 #pragma unroll
   for (int k = 1; k < K; ++k) {
-    c = CDF{qsdf::split(m[2 * k]), qsdf::split(m[2 * k + 1])};
-    qsdf::dot_add(re, c.re, x[k].re);
-    qsdf::dot_add(re, qsdf::neg(c.im), x[k].im);
-    qsdf::dot_add(im, c.re, x[k].im);
-    qsdf::dot_add(im, c.im, x[k].re);
+    qsdf::dot_add(re, m[2 * k], x[k].re);
+    qsdf::dot_add(re, qsdf::neg(m[2 * k + 1]), x[k].im);
+    qsdf::dot_add(im, m[2 * k], x[k].im);
+    qsdf::dot_add(im, m[2 * k + 1], x[k].re);
   }
-  return make_double2(qsdf::finish(re), qsdf::finish(im));
 }
 
-__device__ __forceinline__ uint32_t insert_zeros32(uint32_t k, const int8_t* pos, int n) {
+// zero bits inserted at the ascending positions packed 8 bits each in pos
+__device__ __forceinline__ uint32_t insert_zeros_packed(uint32_t k, uint64_t pos, int n) {
   for (int q = 0; q < n; ++q) {
-    const int p = pos[q];
+    const int p = (int)((pos >> (8 * q)) & 0xFFu);
     k = ((k >> p) << (p + 1)) | (k & ((1u << p) - 1));
   }
   return k;
 }
 
-// ---- one operation on a state held at `a` (shared or global) -------------
-template <typename T2>
-__device__ void apply_op(T2* a, int nq, const BatchOp& op);
+__device__ __forceinline__ uint64_t pack_pos(const int8_t* pos, int n) {
+  uint64_t r = 0;
+  for (int q = 0; q < n; ++q) r |= (uint64_t)(uint8_t)pos[q] << (8 * q);
+  return r;
+}
 
-template <>
-__device__ void apply_op<float2>(float2* a, int nq, const BatchOp& op) {
+// ---- the arithmetic of one update at given indices ---------------------------
+// complex64 (float2, constants as floats)
+__device__ __forceinline__ void op_dense1(float2* a, uint32_t i0, uint32_t i1, const float* m) {
+  const CF x[2] = {ld(a, i0), ld(a, i1)};
+  const float2 y0 = cdot_f32<2>(m, x), y1 = cdot_f32<2>(m + 4, x);
+  a[i0] = y0;
+  a[i1] = y1;
+}
+__device__ __forceinline__ void op_dense2(float2* a, const uint32_t* idx, const float* m) {
+  CF x[4];
+#pragma unroll
+  for (int l = 0; l < 4; ++l) x[l] = ld(a, idx[l]);
+  float2 y[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) y[j] = cdot_f32<4>(m + 8 * j, x);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) a[idx[j]] = y[j];
+}
+__device__ __forceinline__ void op_diag(float2* a, uint32_t i, const float* d) {
+  const float2 v = a[i];
+  a[i] = make_float2(d[0] * v.x - d[1] * v.y, d[0] * v.y + d[1] * v.x);
+}
+
+// complex128 in double-float (P = double2 in global memory, float4 in shared)
+template <typename P>
+__device__ __forceinline__ void op_dense1(P* a, uint32_t i0, uint32_t i1, const df* m) {
+  const CDF x[2] = {ld(a, i0), ld(a, i1)};
+  qsdf::dot_acc r0, m0, r1, m1;
+  cdot_df<2>(m, x, r0, m0);
+  cdot_df<2>(m + 4, x, r1, m1);
+  st(a, i0, r0, m0);
+  st(a, i1, r1, m1);
+}
+template <typename P>
+__device__ __forceinline__ void op_dense2(P* a, const uint32_t* idx, const df* m) {
+  CDF x[4];
+#pragma unroll
+  for (int l = 0; l < 4; ++l) x[l] = ld(a, idx[l]);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {       // every input is read before the first store
+    qsdf::dot_acc re, im;
+    cdot_df<4>(m + 8 * j, x, re, im);
+    st(a, idx[j], re, im);
+  }
+}
+template <typename P>
+__device__ __forceinline__ void op_diag(P* a, uint32_t i, const df* d) {
+  const CDF x = ld(a, i);
+  qsdf::dot_acc re, im;
+  cdot_df<1>(d, &x, re, im);
+  st(a, i, re, im);
+}
+
+// Pauli gadget constants: cos(phi), sin(phi), -sin(phi)
+template <typename K>
+struct Gad {
+  K c, s, ns;
+};
+__device__ __forceinline__ Gad<float> make_gad(const float* kc) { return Gad<float>{kc[0], kc[1], -kc[1]}; }
+__device__ __forceinline__ Gad<df> make_gad(const df* kc) { return Gad<df>{kc[0], kc[1], qsdf::neg(kc[1])}; }
+// diagonal gadget (no X/Y): a_i -> (c + i s_i) a_i, s_i = -s if neg else s
+__device__ __forceinline__ void op_phase(float2* a, uint32_t i, const Gad<float>& G, bool neg) {
+  const float si = neg ? G.ns : G.s;
+  const float2 v = a[i];
+  a[i] = make_float2(G.c * v.x - si * v.y, G.c * v.y + si * v.x);
+}
+template <typename P>
+__device__ __forceinline__ void op_phase(P* a, uint32_t i, const Gad<df>& G, bool neg) {
+  const CDF x = ld(a, i);
+  const df si = neg ? G.ns : G.s;
+  // (c + i si) x: re = c x.re - si x.im, im = c x.im + si x.re
+  qsdf::dot_acc re = qsdf::dot_first(G.c, x.re);
+  qsdf::dot_add(re, qsdf::neg(si), x.im);
+  qsdf::dot_acc im = qsdf::dot_first(G.c, x.im);
+  qsdf::dot_add(im, si, x.re);
+  st(a, i, re, im);
+}
+// paired gadget update of (a_i, a_j), j = i xor xy: a_i -> c a_i + s_j i^q a_j and
+// a_j -> c a_j + s_i i^q a_i, with s_k = -s where the phase parity of k is odd
+__device__ __forceinline__ void op_pair(float2* a, uint32_t i, uint32_t j, const Gad<float>& G, bool negi,
+                                        bool negj, int q) {
+  const float2 x = a[i], y = a[j];
+  const float sj = negj ? G.ns : G.s, si = negi ? G.ns : G.s;
+  const float2 ry = rot_i(y, q), rx = rot_i(x, q);
+  a[i] = make_float2(G.c * x.x + sj * ry.x, G.c * x.y + sj * ry.y);
+  a[j] = make_float2(G.c * y.x + si * rx.x, G.c * y.y + si * rx.y);
+}
+template <typename P>
+__device__ __forceinline__ void op_pair(P* a, uint32_t i, uint32_t j, const Gad<df>& G, bool negi, bool negj,
+                                        int q) {
+  const CDF x = ld(a, i), y = ld(a, j);
+  const df sj = negj ? G.ns : G.s, si = negi ? G.ns : G.s;
+  auto rot = [](const CDF& v, int r) {
+    switch (r & 3) {
+      case 0: return v;
+      case 1: return CDF{qsdf::neg(v.im), v.re};
+      case 2: return CDF{qsdf::neg(v.re), qsdf::neg(v.im)};
+      default: return CDF{v.im, qsdf::neg(v.re)};
+    }
+  };
+  const CDF ry = rot(y, q), rx = rot(x, q);
+  qsdf::dot_acc r0 = qsdf::dot_first(G.c, x.re), i0 = qsdf::dot_first(G.c, x.im);
+  qsdf::dot_add(r0, sj, ry.re);
+  qsdf::dot_add(i0, sj, ry.im);
+  qsdf::dot_acc r1 = qsdf::dot_first(G.c, y.re), i1 = qsdf::dot_first(G.c, y.im);
+  qsdf::dot_add(r1, si, rx.re);
+  qsdf::dot_add(i1, si, rx.im);
+  st(a, i, r0, i0);
+  st(a, j, r1, i1);
+}
+
+// ---- one operation on a whole state held at `a` (shared or global) ---------
+// kc: the operation's constants (load_consts).
+template <typename P, typename K>
+__device__ void apply_op(P* a, int nq, const BatchOp& op, const K* kc) {
   const uint32_t dim = 1u << nq;
-  if (op.kind == 0) {
-    const int n = op.n;
-    const uint32_t groups = dim >> op.nins;
+  const int kind = op.kind, n = op.n;
+  if (kind == 0) {
+    const int nins = op.nins;
+    const uint64_t ins = pack_pos(op.ins, nins);
+    const uint32_t ctrl = op.ctrl, b0 = 1u << op.t[0], b1 = n > 1 ? 1u << op.t[1] : 0u;
+    const uint32_t groups = dim >> nins;
     for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
-      const uint32_t base = insert_zeros32(g, op.ins, op.nins) | op.ctrl;
+      const uint32_t base = insert_zeros_packed(g, ins, nins) | ctrl;
       if (n == 1) {
-        const uint32_t i0 = base, i1 = base | (1u << op.t[0]);
-        ArithF32::C x[2] = {ArithF32::load(a + i0), ArithF32::load(a + i1)};
-        const float2 y0 = cdot_f32<2>(op.m, x), y1 = cdot_f32<2>(op.m + 4, x);
-        a[i0] = y0;
-        a[i1] = y1;
+        op_dense1(a, base, base | b0, kc);
       } else {
-        uint32_t idx[4];
-        ArithF32::C x[4];
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-          idx[l] = base | ((l & 1) ? (1u << op.t[0]) : 0u) | ((l & 2) ? (1u << op.t[1]) : 0u);
-          x[l] = ArithF32::load(a + idx[l]);
-        }
-        float2 y[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) y[j] = cdot_f32<4>(op.m + 8 * j, x);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) a[idx[j]] = y[j];
+        const uint32_t idx[4] = {base, base | b0, base | b1, base | b0 | b1};
+        op_dense2(a, idx, kc);
       }
     }
-  } else if (op.kind == 1) {
+  } else if (kind == 1) {
+    const int t0 = op.t[0], t1 = n > 1 ? op.t[1] : 0, t2 = n > 2 ? op.t[2] : 0;
     for (uint32_t i = threadIdx.x; i < dim; i += blockDim.x) {
-      int j = 0;
-      for (int q = 0; q < op.n; ++q) j |= (int)((i >> op.t[q]) & 1u) << q;
-      const float dr = (float)op.m[2 * j], di = (float)op.m[2 * j + 1];
-      const float2 v = a[i];
-      a[i] = make_float2(dr * v.x - di * v.y, dr * v.y + di * v.x);
+      int j = (int)((i >> t0) & 1u);
+      if (n > 1) j |= (int)((i >> t1) & 1u) << 1;
+      if (n > 2) j |= (int)((i >> t2) & 1u) << 2;
+      op_diag(a, i, kc + 2 * j);
     }
   } else {
-    const float c = (float)op.c, s = (float)op.s;
-    if (op.xy == 0) {
-      for (uint32_t i = threadIdx.x; i < dim; i += blockDim.x) {
-        const float si = (__popc(i & op.yz) & 1) ? -s : s;
-        const float2 v = a[i];
-        a[i] = make_float2(c * v.x - si * v.y, c * v.y + si * v.x);
-      }
+    const auto G = make_gad(kc);
+    const uint32_t xy = op.xy, yz = op.yz;
+    if (xy == 0) {
+      for (uint32_t i = threadIdx.x; i < dim; i += blockDim.x) op_phase(a, i, G, __popc(i & yz) & 1);
     } else {
-      const int q = (op.eta + 1) & 3;
+      const int q = (op.eta + 1) & 3, h = op.h;
       for (uint32_t k = threadIdx.x; k < (dim >> 1); k += blockDim.x) {
-        const uint32_t i = ((k >> op.h) << (op.h + 1)) | (k & ((1u << op.h) - 1));
-        const uint32_t j = i ^ op.xy;
-        const float2 x = a[i], y = a[j];
-        const float sj = (__popc(j & op.yz) & 1) ? -s : s, si = (__popc(i & op.yz) & 1) ? -s : s;
-        const float2 ry = rot_i(y, q), rx = rot_i(x, q);
-        a[i] = make_float2(c * x.x + sj * ry.x, c * x.y + sj * ry.y);
-        a[j] = make_float2(c * y.x + si * rx.x, c * y.y + si * rx.y);
+        const uint32_t i = ((k >> h) << (h + 1)) | (k & ((1u << h) - 1));
+        const uint32_t j = i ^ xy;
+        op_pair(a, i, j, G, __popc(i & yz) & 1, __popc(j & yz) & 1, q);
       }
     }
   }
 }
 
-template <>
-__device__ void apply_op<double2>(double2* a, int nq, const BatchOp& op) {
-  const uint32_t dim = 1u << nq;
-  if (op.kind == 0) {
-    const int n = op.n;
-    const uint32_t groups = dim >> op.nins;
+// ---- one operation on one tile in shared memory ---------------------------
+// Local index i (L bits) is the amplitude base | (i deposited on the tile
+// qubits); the translation x gives the operation's masks in local terms and
+// the parts outside the tile, which are constant over the tile (taken from
+// base).
+template <typename P, typename K>
+__device__ void apply_tile_op(P* a, int L, const BatchOp& op, const BatchXlat& x, uint32_t base, const K* kc) {
+  const uint32_t dim = 1u << L;
+  const int kind = op.kind, n = op.n;
+  if (kind == 0) {
+    if ((base & x.fctrl) != x.fctrl) return;          // a control outside the tile is 0 here
+    const int nins = x.nlins;
+    const uint64_t ins = pack_pos(x.lins, nins);
+    const uint32_t ctrl = x.lctrl, b0 = 1u << x.lt[0], b1 = n > 1 ? 1u << x.lt[1] : 0u;
+    const uint32_t groups = dim >> nins;
     for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
-      const uint32_t base = insert_zeros32(g, op.ins, op.nins) | op.ctrl;
+      const uint32_t lb = insert_zeros_packed(g, ins, nins) | ctrl;
       if (n == 1) {
-        const uint32_t i0 = base, i1 = base | (1u << op.t[0]);
-        CDF x[2] = {load_df(a + i0), load_df(a + i1)};
-        const double2 y0 = cdot_df<2>(op.m, x), y1 = cdot_df<2>(op.m + 4, x);
-        a[i0] = y0;
-        a[i1] = y1;
+        op_dense1(a, lb, lb | b0, kc);
       } else {
-        uint32_t idx[4];
-        CDF x[4];
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-          idx[l] = base | ((l & 1) ? (1u << op.t[0]) : 0u) | ((l & 2) ? (1u << op.t[1]) : 0u);
-          x[l] = load_df(a + idx[l]);
-        }
-        double2 y[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) y[j] = cdot_df<4>(op.m + 8 * j, x);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) a[idx[j]] = y[j];
+        const uint32_t idx[4] = {lb, lb | b0, lb | b1, lb | b0 | b1};
+        op_dense2(a, idx, kc);
       }
     }
-  } else if (op.kind == 1) {
+  } else if (kind == 1) {
+    int jfix = 0, lt[3] = {-1, -1, -1};
+    for (int q = 0; q < n; ++q) {
+      lt[q] = x.lt[q];
+      if (lt[q] < 0) jfix |= (int)((base >> op.t[q]) & 1u) << q;
+    }
     for (uint32_t i = threadIdx.x; i < dim; i += blockDim.x) {
-      int j = 0;
-      for (int q = 0; q < op.n; ++q) j |= (int)((i >> op.t[q]) & 1u) << q;
-      const CDF x = load_df(a + i);
-      a[i] = cdot_df<1>(op.m + 2 * j, &x);
+      int j = jfix;
+      if (lt[0] >= 0) j |= (int)((i >> lt[0]) & 1u);
+      if (lt[1] >= 0) j |= (int)((i >> lt[1]) & 1u) << 1;
+      if (lt[2] >= 0) j |= (int)((i >> lt[2]) & 1u) << 2;
+      op_diag(a, i, kc + 2 * j);
     }
   } else {
-    const df c = qsdf::split(op.c), s = qsdf::split(op.s), ns = qsdf::neg(s);
+    const auto G = make_gad(kc);
+    const uint32_t fpar = __popc(base & x.fyz) & 1, lyz = x.lyz, lxy = x.lxy;
     if (op.xy == 0) {
-      for (uint32_t i = threadIdx.x; i < dim; i += blockDim.x) {
-        const CDF x = load_df(a + i);
-        const df si = (__popc(i & op.yz) & 1) ? ns : s;
-        // (c + i si) x: re = c x.re - si x.im, im = c x.im + si x.re
-        qsdf::dot_acc re = qsdf::dot_first(c, x.re);
-        qsdf::dot_add(re, qsdf::neg(si), x.im);
-        qsdf::dot_acc im = qsdf::dot_first(c, x.im);
-        qsdf::dot_add(im, si, x.re);
-        a[i] = make_double2(qsdf::finish(re), qsdf::finish(im));
-      }
+      for (uint32_t i = threadIdx.x; i < dim; i += blockDim.x) op_phase(a, i, G, (__popc(i & lyz) & 1) ^ fpar);
     } else {
-      const int q = (op.eta + 1) & 3;
+      const int q = (op.eta + 1) & 3, h = x.lh;
       for (uint32_t k = threadIdx.x; k < (dim >> 1); k += blockDim.x) {
-        const uint32_t i = ((k >> op.h) << (op.h + 1)) | (k & ((1u << op.h) - 1));
-        const uint32_t j = i ^ op.xy;
-        const CDF x = load_df(a + i), y = load_df(a + j);
-        const df sj = (__popc(j & op.yz) & 1) ? ns : s, si = (__popc(i & op.yz) & 1) ? ns : s;
-        auto rot = [](const CDF& v, int r) {
-          switch (r & 3) {
-            case 0: return v;
-            case 1: return CDF{qsdf::neg(v.im), v.re};
-            case 2: return CDF{qsdf::neg(v.re), qsdf::neg(v.im)};
-            default: return CDF{v.im, qsdf::neg(v.re)};
-          }
-        };
-        const CDF ry = rot(y, q), rx = rot(x, q);
-        qsdf::dot_acc r0 = qsdf::dot_first(c, x.re), i0 = qsdf::dot_first(c, x.im);
-        qsdf::dot_add(r0, sj, ry.re);
-        qsdf::dot_add(i0, sj, ry.im);
-        qsdf::dot_acc r1 = qsdf::dot_first(c, y.re), i1 = qsdf::dot_first(c, y.im);
-        qsdf::dot_add(r1, si, rx.re);
-        qsdf::dot_add(i1, si, rx.im);
-        a[i] = make_double2(qsdf::finish(r0), qsdf::finish(i0));
-        a[j] = make_double2(qsdf::finish(r1), qsdf::finish(i1));
+        const uint32_t i = ((k >> h) << (h + 1)) | (k & ((1u << h) - 1));
+        const uint32_t j = i ^ lxy;
+        op_pair(a, i, j, G, (__popc(i & lyz) & 1) ^ fpar, (__popc(j & lyz) & 1) ^ fpar, q);
       }
     }
   }
@@ -226,12 +358,23 @@ __device__ void apply_op<double2>(double2* a, int nq, const BatchOp& op) {
 
 }  // namespace
 
+// One CTA per state at a time.  States of at most smem_qubits qubits are
+// copied to shared memory, run there, and copied back.  Larger states run
+// segment by segment: a tiled segment loads each tile (one 16-byte or 8-byte
+// gather per amplitude through two 128-entry offset tables; the five lowest
+// qubits are always tile qubits, so a warp reads 32 consecutive amplitudes),
+// applies the segment's operations to it and writes it back.
 template <typename T2>
-__global__ void k_batch(T2* __restrict__ pool, const BatchState* __restrict__ states, const int* __restrict__ order,
-                        int nstates, const BatchOp* __restrict__ ops, int* __restrict__ counter, int smem_qubits) {
+__global__ void __launch_bounds__(512)
+    k_batch(T2* __restrict__ pool, const BatchState* __restrict__ states, const int* __restrict__ order, int nstates,
+            const BatchOp* __restrict__ ops, const BatchSeg* __restrict__ segs, const BatchXlat* __restrict__ xlat,
+            int* __restrict__ counter, int smem_qubits) {
+  using SM = SmemOf<T2>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T2* sm = reinterpret_cast<T2*>(smem_raw);
+  typename SM::T* sm = reinterpret_cast<typename SM::T*>(smem_raw);
   __shared__ int s_work;
+  __shared__ uint32_t s_tl[128], s_th[128];
+  __shared__ KT<T2> s_k[2][32];          // constants of the current and the next operation
   while (true) {
     if (threadIdx.x == 0) s_work = atomicAdd(counter, 1);
     __syncthreads();
@@ -241,19 +384,70 @@ __global__ void k_batch(T2* __restrict__ pool, const BatchState* __restrict__ st
     const BatchState st = states[order[w]];
     T2* g = pool + st.offset;
     const uint32_t dim = 1u << st.nq;
-    const bool in_smem = st.nq <= smem_qubits;
-    if (in_smem) {
-      for (uint32_t i = threadIdx.x; i < dim; i += blockDim.x) sm[i] = g[i];
+    if (st.nq <= smem_qubits) {
+      for (uint32_t i = threadIdx.x; i < dim; i += blockDim.x) sm[i] = SM::in(g[i]);
+      if (st.nops > 0) load_consts<T2>(ops[st.first_op], s_k[0]);
       __syncthreads();
+      for (int k = 0; k < st.nops; ++k) {
+        apply_op(sm, st.nq, ops[st.first_op + k], s_k[k & 1]);
+        if (k + 1 < st.nops) load_consts<T2>(ops[st.first_op + k + 1], s_k[(k + 1) & 1]);
+        __syncthreads();
+      }
+      for (uint32_t i = threadIdx.x; i < dim; i += blockDim.x) g[i] = SM::out(sm[i]);
+      __syncthreads();
+      continue;
     }
-    T2* a = in_smem ? sm : g;
-    for (int k = 0; k < st.nops; ++k) {
-      apply_op<T2>(a, st.nq, ops[st.first_op + k]);
+    for (int sg = st.first_seg; sg < st.first_seg + st.nsegs; ++sg) {
+      const BatchSeg S = segs[sg];
+      if (S.L == 0) {
+        load_consts<T2>(ops[S.first_op], s_k[0]);
+        __syncthreads();
+        for (int k = 0; k < S.nops; ++k) {
+          apply_op(g, st.nq, ops[S.first_op + k], s_k[k & 1]);
+          if (k + 1 < S.nops) load_consts<T2>(ops[S.first_op + k + 1], s_k[(k + 1) & 1]);
+          __syncthreads();
+        }
+        continue;
+      }
+      const int L = S.L, hi = L - 7;                  // 8 <= L <= 14
+      uint32_t qmask = 0;
+      for (int b = 0; b < L; ++b) qmask |= 1u << S.q[b];
+      for (int j = threadIdx.x; j < 128; j += blockDim.x) {
+        uint32_t tl = 0, th = 0;
+        for (int b = 0; b < 7; ++b)
+          if ((j >> b) & 1) tl |= 1u << S.q[b];
+        for (int b = 0; b < hi; ++b)
+          if ((j >> b) & 1) th |= 1u << S.q[7 + b];
+        s_tl[j] = tl;
+        s_th[j] = th;
+      }
       __syncthreads();
-    }
-    if (in_smem) {
-      for (uint32_t i = threadIdx.x; i < dim; i += blockDim.x) g[i] = sm[i];
-      __syncthreads();
+      const uint32_t fmask = (dim - 1) & ~qmask;       // the other qubits: the tile number, deposited
+      const uint32_t ntiles = dim >> L, tdim = 1u << L;
+      for (uint32_t tile = 0; tile < ntiles; ++tile) {
+        uint32_t base = 0;
+        {
+          uint32_t m = fmask, t = tile;
+          while (m) {
+            const uint32_t low = m & (~m + 1u);
+            if (t & 1u) base |= low;
+            m ^= low;
+            t >>= 1;
+          }
+        }
+        for (uint32_t i = threadIdx.x; i < tdim; i += blockDim.x)
+          sm[i] = SM::in(g[base | s_tl[i & 127u] | s_th[i >> 7]]);
+        load_consts<T2>(ops[S.first_op], s_k[0]);
+        __syncthreads();
+        for (int k = 0; k < S.nops; ++k) {
+          apply_tile_op(sm, L, ops[S.first_op + k], xlat[S.first_op + k], base, s_k[k & 1]);
+          if (k + 1 < S.nops) load_consts<T2>(ops[S.first_op + k + 1], s_k[(k + 1) & 1]);
+          __syncthreads();
+        }
+        for (uint32_t i = threadIdx.x; i < tdim; i += blockDim.x)
+          g[base | s_tl[i & 127u] | s_th[i >> 7]] = SM::out(sm[i]);
+        __syncthreads();
+      }
     }
   }
 }
@@ -266,14 +460,15 @@ cudaError_t batch_set_max_smem(int bytes) {
 
 // No attribute calls here: this launch is also recorded into a CUDA graph.
 cudaError_t launch_batch(qs_prec prec, void* pool, const BatchState* states, const int* order, int nstates,
-                         const BatchOp* ops, int* counter, int threads, int ctas, int smem_qubits, cudaStream_t st) {
+                         const BatchOp* ops, const BatchSeg* segs, const BatchXlat* xlat, int* counter, int threads,
+                         int ctas, int smem_qubits, cudaStream_t st) {
   const size_t smem = (smem_qubits >= 0 ? (size_t(1) << smem_qubits) : 0) * (prec == QS_C128 ? 16 : 8);
   if (prec == QS_C128)
-    k_batch<double2><<<ctas, threads, smem, st>>>(static_cast<double2*>(pool), states, order, nstates, ops, counter,
-                                                  smem_qubits);
+    k_batch<double2><<<ctas, threads, smem, st>>>(static_cast<double2*>(pool), states, order, nstates, ops, segs,
+                                                  xlat, counter, smem_qubits);
   else
-    k_batch<float2><<<ctas, threads, smem, st>>>(static_cast<float2*>(pool), states, order, nstates, ops, counter,
-                                                 smem_qubits);
+    k_batch<float2><<<ctas, threads, smem, st>>>(static_cast<float2*>(pool), states, order, nstates, ops, segs, xlat,
+                                                 counter, smem_qubits);
   return cudaGetLastError();
 }
 

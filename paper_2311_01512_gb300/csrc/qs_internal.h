@@ -174,7 +174,30 @@ struct BatchState {
   int nq;
   int first_op;
   int nops;
+  int first_seg;         // states larger than shared memory: their segments
+  int nsegs;
   int pad;
+};
+// A run of one state's operations applied tile by tile: every operation's
+// pairing qubits (dense targets, gadget X/Y qubits) lie in the L tile qubits
+// q[0..L-1] (ascending), so each tile of 2^L amplitudes (fixed values of the
+// other qubits) goes through shared memory once for the whole run.  L = 0:
+// the operations run one by one in global memory.
+struct BatchSeg {
+  int first_op, nops;    // global operation indices
+  int L;
+  int pad;
+  int8_t q[16];
+};
+// An operation in its segment's tile coordinates (one per operation, parallel
+// to the operation array).
+struct BatchXlat {
+  uint32_t lctrl, fctrl;    // dense: controls inside the tile (local mask) / outside it (global mask)
+  uint32_t lxy, lyz, fyz;   // gadget: local flip and phase masks; phase mask outside the tile (global)
+  int nlins;                // dense: number of local insertion positions
+  int8_t lins[8];           // dense: ascending local positions of targets and in-tile controls
+  int8_t lt[3];             // local target positions (-1: outside the tile, diagonals only)
+  int8_t lh;                // gadget: local position of the highest flip bit
 };
 
 // Launchers.  Each returns cudaGetLastError() after the launch.  amps is the
@@ -207,7 +230,8 @@ cudaError_t launch_mlp_adam(float* params, const float* grad, float* m, float* v
 int num_sms();  // multiprocessors of the current device (cached)
 cudaError_t batch_set_max_smem(int bytes);
 cudaError_t launch_batch(qs_prec prec, void* pool, const BatchState* states, const int* order, int nstates,
-                         const BatchOp* ops, int* counter, int threads, int ctas, int smem_qubits, cudaStream_t st);
+                         const BatchOp* ops, const BatchSeg* segs, const BatchXlat* xlat, int* counter, int threads,
+                         int ctas, int smem_qubits, cudaStream_t st);
 cudaError_t launch_group(qs_prec prec, void* amps, int op, const GroupParams& p, cudaStream_t st);
 // complex128 channels in double-float arithmetic: G_DEPOL1, G_DEPOL2, G_DAMP, G_PAULI1 (qs_gates_df.cu)
 cudaError_t launch_group_df(void* amps, int op, const GroupParams& p, cudaStream_t st);

@@ -2,7 +2,10 @@
 own random circuit, run in one recorded launch, against the CPU oracle state
 by state (complex128 in double-float: 1e-12 per 1000 gates; complex64: 1 - F
 <= 1e-6).  Sizes include states too large for shared memory, so both the
-shared-memory and the global-memory paths run."""
+shared-memory path and the tiled path (segments of operations applied tile by
+tile, with controls, diagonal targets and gadget phase qubits both inside and
+outside the tile) run, and so does the global-memory path of an operation
+that pairs more qubits than a tile holds."""
 
 import numpy as np
 import pytest
@@ -28,6 +31,14 @@ def test_batch_matches_oracle(qs, prec):
     circuits = []
     for s, nq in enumerate(sizes):
         ops = wl.unitary_circuit(nq, int(rng.integers(10, 60)), rng)
+        for k in range(0, len(ops), 5):             # diagonals on 1..3 qubits
+            n = int(rng.integers(1, min(3, nq) + 1))
+            targs = [int(x) for x in rng.choice(nq, n, replace=False)]
+            ops.insert(k, {"op": "diagonal", "targs": targs,
+                           "diag": np.exp(1j * rng.uniform(0, 2 * np.pi, 1 << n))})
+        if nq >= 15:                                 # X/Y on every qubit: more than a tile
+            ops.insert(len(ops) // 2, {"op": "gadget", "targs": list(range(nq)),
+                                       "paulis": [int(x) for x in rng.integers(1, 3, nq)], "theta": 0.7})
         for op in ops:
             batch.add(s, op)
         circuits.append(ops)
