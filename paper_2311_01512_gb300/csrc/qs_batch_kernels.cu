@@ -40,6 +40,8 @@ struct Konst<double2> {
 
 template <typename T2>
 using KT = typename Konst<T2>::K;
+template <typename K>
+constexpr bool kDfConst = sizeof(K) == 8;
 
 template <typename T2>
 __device__ __forceinline__ void load_consts(const BatchOp& op, typename Konst<T2>::K* kc) {
@@ -270,11 +272,22 @@ __device__ void apply_op(P* a, int nq, const BatchOp& op, const K* kc) {
     const uint64_t ins = pack_pos(op.ins, nins);
     const uint32_t ctrl = op.ctrl, b0 = 1u << op.t[0], b1 = n > 1 ? 1u << op.t[1] : 0u;
     const uint32_t groups = dim >> nins;
-    for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
-      const uint32_t base = insert_zeros_packed(g, ins, nins) | ctrl;
-      if (n == 1) {
+    if (n == 1 && kDfConst<K>) {
+      K m[8];   // complex128: in registers (the loop's stores may alias shared memory)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) m[i] = kc[i];
+      for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
+        const uint32_t base = insert_zeros_packed(g, ins, nins) | ctrl;
+        op_dense1(a, base, base | b0, m);
+      }
+    } else if (n == 1) {
+      for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
+        const uint32_t base = insert_zeros_packed(g, ins, nins) | ctrl;
         op_dense1(a, base, base | b0, kc);
-      } else {
+      }
+    } else {
+      for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
+        const uint32_t base = insert_zeros_packed(g, ins, nins) | ctrl;
         const uint32_t idx[4] = {base, base | b0, base | b1, base | b0 | b1};
         op_dense2(a, idx, kc);
       }
@@ -318,11 +331,22 @@ __device__ void apply_tile_op(P* a, int L, const BatchOp& op, const BatchXlat& x
     const uint64_t ins = pack_pos(x.lins, nins);
     const uint32_t ctrl = x.lctrl, b0 = 1u << x.lt[0], b1 = n > 1 ? 1u << x.lt[1] : 0u;
     const uint32_t groups = dim >> nins;
-    for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
-      const uint32_t lb = insert_zeros_packed(g, ins, nins) | ctrl;
-      if (n == 1) {
+    if (n == 1 && kDfConst<K>) {
+      K m[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) m[i] = kc[i];
+      for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
+        const uint32_t lb = insert_zeros_packed(g, ins, nins) | ctrl;
+        op_dense1(a, lb, lb | b0, m);
+      }
+    } else if (n == 1) {
+      for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
+        const uint32_t lb = insert_zeros_packed(g, ins, nins) | ctrl;
         op_dense1(a, lb, lb | b0, kc);
-      } else {
+      }
+    } else {
+      for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
+        const uint32_t lb = insert_zeros_packed(g, ins, nins) | ctrl;
         const uint32_t idx[4] = {lb, lb | b0, lb | b1, lb | b0 | b1};
         op_dense2(a, idx, kc);
       }
@@ -365,7 +389,7 @@ __device__ void apply_tile_op(P* a, int L, const BatchOp& op, const BatchXlat& x
 // qubits are always tile qubits, so a warp reads 32 consecutive amplitudes),
 // applies the segment's operations to it and writes it back.
 template <typename T2>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, sizeof(T2) == 8 ? 2 : 1)
     k_batch(T2* __restrict__ pool, const BatchState* __restrict__ states, const int* __restrict__ order, int nstates,
             const BatchOp* __restrict__ ops, const BatchSeg* __restrict__ segs, const BatchXlat* __restrict__ xlat,
             int* __restrict__ counter, int smem_qubits) {
