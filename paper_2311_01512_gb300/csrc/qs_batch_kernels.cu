@@ -40,8 +40,6 @@ struct Konst<double2> {
 
 template <typename T2>
 using KT = typename Konst<T2>::K;
-template <typename K>
-constexpr bool kDfConst = sizeof(K) == 8;
 
 template <typename T2>
 __device__ __forceinline__ void load_consts(const BatchOp& op, typename Konst<T2>::K* kc) {
@@ -272,18 +270,13 @@ __device__ void apply_op(P* a, int nq, const BatchOp& op, const K* kc) {
     const uint64_t ins = pack_pos(op.ins, nins);
     const uint32_t ctrl = op.ctrl, b0 = 1u << op.t[0], b1 = n > 1 ? 1u << op.t[1] : 0u;
     const uint32_t groups = dim >> nins;
-    if (n == 1 && kDfConst<K>) {
-      K m[8];   // complex128: in registers (the loop's stores may alias shared memory)
+    if (n == 1) {
+      K m[8];   // in registers for the sweep (its stores may alias shared memory)
 #pragma unroll
       for (int i = 0; i < 8; ++i) m[i] = kc[i];
       for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
         const uint32_t base = insert_zeros_packed(g, ins, nins) | ctrl;
         op_dense1(a, base, base | b0, m);
-      }
-    } else if (n == 1) {
-      for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
-        const uint32_t base = insert_zeros_packed(g, ins, nins) | ctrl;
-        op_dense1(a, base, base | b0, kc);
       }
     } else {
       for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
@@ -331,18 +324,13 @@ __device__ void apply_tile_op(P* a, int L, const BatchOp& op, const BatchXlat& x
     const uint64_t ins = pack_pos(x.lins, nins);
     const uint32_t ctrl = x.lctrl, b0 = 1u << x.lt[0], b1 = n > 1 ? 1u << x.lt[1] : 0u;
     const uint32_t groups = dim >> nins;
-    if (n == 1 && kDfConst<K>) {
+    if (n == 1) {
       K m[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) m[i] = kc[i];
       for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
         const uint32_t lb = insert_zeros_packed(g, ins, nins) | ctrl;
         op_dense1(a, lb, lb | b0, m);
-      }
-    } else if (n == 1) {
-      for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
-        const uint32_t lb = insert_zeros_packed(g, ins, nins) | ctrl;
-        op_dense1(a, lb, lb | b0, kc);
       }
     } else {
       for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
