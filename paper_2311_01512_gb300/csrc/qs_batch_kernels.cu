@@ -133,19 +133,29 @@ __device__ __forceinline__ void cdot_df(const df* m, const CDF* x, qsdf::dot_acc
   }
 }
 
-// zero bits inserted at the ascending positions packed 8 bits each in pos
-__device__ __forceinline__ uint32_t insert_zeros_packed(uint32_t k, uint64_t pos, int n) {
-  for (int q = 0; q < n; ++q) {
-    const int p = (int)((pos >> (8 * q)) & 0xFFu);
-    k = ((k >> p) << (p + 1)) | (k & ((1u << p) - 1));
-  }
-  return k;
+// Zero bits inserted at up to 7 ascending positions p_q, given as the masks
+// hm_q = ~0 << p_q (unused entries 0): k + (k & hm) shifts the bits at and
+// above p up by one and leaves a zero at p.
+struct InsMasks {
+  uint32_t hm[7];
+  int n;
+};
+
+__device__ __forceinline__ InsMasks ins_masks(const int8_t* pos, int n) {
+  InsMasks m;
+  m.n = n;
+#pragma unroll
+  for (int q = 0; q < 7; ++q) m.hm[q] = q < n ? 0xFFFFFFFFu << pos[q] : 0u;
+  return m;
 }
 
-__device__ __forceinline__ uint64_t pack_pos(const int8_t* pos, int n) {
-  uint64_t r = 0;
-  for (int q = 0; q < n; ++q) r |= (uint64_t)(uint8_t)pos[q] << (8 * q);
-  return r;
+__device__ __forceinline__ uint32_t insert_zeros_m(uint32_t k, const InsMasks& m) {
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    if (q >= m.n) break;         // uniform over the block
+    k += k & m.hm[q];
+  }
+  return k;
 }
 
 // ---- the arithmetic of one update at given indices ---------------------------
@@ -267,7 +277,7 @@ __device__ void apply_op(P* a, int nq, const BatchOp& op, const K* kc) {
   const int kind = op.kind, n = op.n;
   if (kind == 0) {
     const int nins = op.nins;
-    const uint64_t ins = pack_pos(op.ins, nins);
+    const InsMasks ins = ins_masks(op.ins, nins);
     const uint32_t ctrl = op.ctrl, b0 = 1u << op.t[0], b1 = n > 1 ? 1u << op.t[1] : 0u;
     const uint32_t groups = dim >> nins;
     if (n == 1) {
@@ -275,12 +285,12 @@ __device__ void apply_op(P* a, int nq, const BatchOp& op, const K* kc) {
 #pragma unroll
       for (int i = 0; i < 8; ++i) m[i] = kc[i];
       for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
-        const uint32_t base = insert_zeros_packed(g, ins, nins) | ctrl;
+        const uint32_t base = insert_zeros_m(g, ins) | ctrl;
         op_dense1(a, base, base | b0, m);
       }
     } else {
       for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
-        const uint32_t base = insert_zeros_packed(g, ins, nins) | ctrl;
+        const uint32_t base = insert_zeros_m(g, ins) | ctrl;
         const uint32_t idx[4] = {base, base | b0, base | b1, base | b0 | b1};
         op_dense2(a, idx, kc);
       }
@@ -321,7 +331,7 @@ __device__ void apply_tile_op(P* a, int L, const BatchOp& op, const BatchXlat& x
   if (kind == 0) {
     if ((base & x.fctrl) != x.fctrl) return;          // a control outside the tile is 0 here
     const int nins = x.nlins;
-    const uint64_t ins = pack_pos(x.lins, nins);
+    const InsMasks ins = ins_masks(x.lins, nins);
     const uint32_t ctrl = x.lctrl, b0 = 1u << x.lt[0], b1 = n > 1 ? 1u << x.lt[1] : 0u;
     const uint32_t groups = dim >> nins;
     if (n == 1) {
@@ -329,12 +339,12 @@ __device__ void apply_tile_op(P* a, int L, const BatchOp& op, const BatchXlat& x
 #pragma unroll
       for (int i = 0; i < 8; ++i) m[i] = kc[i];
       for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
-        const uint32_t lb = insert_zeros_packed(g, ins, nins) | ctrl;
+        const uint32_t lb = insert_zeros_m(g, ins) | ctrl;
         op_dense1(a, lb, lb | b0, m);
       }
     } else {
       for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
-        const uint32_t lb = insert_zeros_packed(g, ins, nins) | ctrl;
+        const uint32_t lb = insert_zeros_m(g, ins) | ctrl;
         const uint32_t idx[4] = {lb, lb | b0, lb | b1, lb | b0 | b1};
         op_dense2(a, idx, kc);
       }
