@@ -391,6 +391,32 @@ qs_status qs_calc_norm_or_trace(const qs_state* state, double* out);
  * amplitudes are then unspecified. */
 qs_status qs_synchronize(const qs_state* state);
 
+/* ---------------------------------------------------------------------------
+ * Recorded programs (not in the paper): the operations applied to one state
+ * between qs_record_begin and qs_record_end are captured as a CUDA graph on the
+ * state's stream and replayed with one launch by qs_program_run, which removes
+ * the per-call host work (validation, staging, one launch per kernel) that
+ * bounds small states.
+ * - While recording, operation calls (gates, diagonals, gadgets, SWAP, Kraus
+ *   maps, channels, dense blocks, planned circuits) validate their arguments as
+ *   usual but launch nothing; their matrices and Kraus operators are copied to
+ *   device memory owned by the program.  Calls that read results or
+ *   synchronise (amplitude copies, norms, expectation values, partial traces,
+ *   qs_synchronize, qs_destroy) return QS_ERR_ARG while recording.
+ * - The state must use a stream other than the legacy default stream
+ *   (QS_ERR_ARG otherwise).  One recording per state at a time.
+ * - qs_program_run queues one replay on the state's stream (asynchronous); a
+ *   replay applies the recorded operations to the state's current amplitudes.
+ * - The program must be destroyed before its state; qs_program_destroy waits
+ *   for the state's stream.
+ * ------------------------------------------------------------------------- */
+typedef struct qs_program qs_program;
+qs_status qs_record_begin(qs_state* state);
+/* Ends the recording; *out receives the program (NULL on error). */
+qs_status qs_record_end(qs_state* state, qs_program** out);
+qs_status qs_program_run(qs_program* program);
+qs_status qs_program_destroy(qs_program* program);
+
 #ifdef __cplusplus
 }
 #endif

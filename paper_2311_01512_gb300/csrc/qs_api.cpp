@@ -77,12 +77,69 @@ qs_status create(int nq, int ns, int is_density, qs_prec prec, void* d_amps, voi
   return QS_OK;
 }
 
+// ---- recorded programs ------------------------------------------------------
+}  // namespace qsapi
+
+// A recorded program: the CUDA graph captured from the state's stream between
+// qs_record_begin and qs_record_end, and the device memory its kernels read
+// (matrices, Kraus operators, superoperators), which lives as long as the
+// program.
+struct qs_program {
+  qs_state* state = nullptr;
+  std::vector<void*> chunks;      // device arena, never moved (the graph holds its addresses)
+  size_t used = 0, cap = 0;       // in the last chunk
+  cudaStream_t side = nullptr;    // uploads during recording (outside the capture)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace qsapi {
+
+void* rec_alloc(qs_program* p, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (p->chunks.empty() || p->used + bytes > p->cap) {
+    const size_t cap = std::max<size_t>(bytes, size_t(4) << 20);
+    void* c = nullptr;
+    if (cudaMalloc(&c, cap) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    p->chunks.push_back(c);
+    p->used = 0;
+    p->cap = cap;
+  }
+  void* d = static_cast<unsigned char*>(p->chunks.back()) + p->used;
+  p->used += bytes;
+  return d;
+}
+
+qs_status rec_put(qs_program* p, const void* host, size_t bytes, const void** dev, int* slot) {
+  *slot = -1;
+  void* d = rec_alloc(p, bytes);
+  if (!d) return QS_ERR_OOM;
+  if (cudaMemcpyAsync(d, host, bytes, cudaMemcpyHostToDevice, p->side) != cudaSuccess ||
+      cudaStreamSynchronize(p->side) != cudaSuccess)
+    return QS_ERR_CUDA;
+  *dev = d;
+  return QS_OK;
+}
+
+void program_free(qs_program* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  for (void* c : p->chunks) cudaFree(c);
+  if (p->side) cudaStreamDestroy(p->side);
+  delete p;
+}
+
 // Stage `bytes` of host data through the next ring slot and return its device
 // copy.  The slot is reused only after the event recorded by its previous user
 // has completed.  The caller records the slot's event after queuing the
 // kernels that read it (ring_done).
 qs_status ring_put(qs_state* s, const void* host, size_t bytes, const void** dev, int* slot) {
   if (bytes > kSlotBytes) return QS_ERR_ARG;
+  if (s->rec) return rec_put(s->rec, host, bytes, dev, slot);
   const int k = s->ring_next;
   s->ring_next = (k + 1) % kRingSlots;
   if (cudaEventSynchronize(s->ring_ev[k]) != cudaSuccess) return QS_ERR_CUDA;
@@ -96,7 +153,13 @@ qs_status ring_put(qs_state* s, const void* host, size_t bytes, const void** dev
 }
 
 // A device-side ring slot with no host data (written by a kernel).
-qs_status ring_take(qs_state* s, void** dev, int* slot) {
+qs_status ring_take(qs_state* s, size_t bytes, void** dev, int* slot) {
+  if (bytes > kSlotBytes) return QS_ERR_ARG;
+  if (s->rec) {
+    *slot = -1;
+    *dev = rec_alloc(s->rec, bytes);
+    return *dev ? QS_OK : QS_ERR_OOM;
+  }
   const int k = s->ring_next;
   s->ring_next = (k + 1) % kRingSlots;
   if (cudaEventSynchronize(s->ring_ev[k]) != cudaSuccess) return QS_ERR_CUDA;
@@ -105,7 +168,10 @@ qs_status ring_take(qs_state* s, void** dev, int* slot) {
   return QS_OK;
 }
 
-qs_status ring_done(qs_state* s, int slot) { return cuda_status(cudaEventRecord(s->ring_ev[slot], s->stream)); }
+qs_status ring_done(qs_state* s, int slot) {
+  if (slot < 0) return QS_OK;      // arena data of a recorded program: nothing to release
+  return cuda_status(cudaEventRecord(s->ring_ev[slot], s->stream));
+}
 
 // Validate qubits: each in [0, nq), no repeats within a list, targets and
 // controls disjoint (Sec. "Many-control one-target gate": t not in c).
@@ -333,7 +399,7 @@ qs_status qs_create_densmatr(int num_qubits, qs_prec prec, void* d_amps, void* c
 }
 
 qs_status qs_destroy(qs_state* state) {
-  if (!state) return QS_ERR_ARG;
+  if (!state || state->rec) return QS_ERR_ARG;
   const cudaError_t e = cudaStreamSynchronize(state->stream);
   release(state);
   return cuda_status(e);
@@ -369,6 +435,7 @@ qs_status qs_device_ptr(const qs_state* s, void** d_amps) {
 }
 
 qs_status qs_set_amps(qs_state* s, const void* host_amps, size_t first, size_t count) {
+  if (s && s->rec) return QS_ERR_ARG;   // not while recording
   if (!s || (!host_amps && count)) return QS_ERR_ARG;
   const size_t total = size_t(1) << s->ns;
   if (first > total || count > total - first) return QS_ERR_ARG;
@@ -378,6 +445,7 @@ qs_status qs_set_amps(qs_state* s, const void* host_amps, size_t first, size_t c
 }
 
 qs_status qs_get_amps(const qs_state* s, void* host_amps, size_t first, size_t count) {
+  if (s && s->rec) return QS_ERR_ARG;   // not while recording
   if (!s || (!host_amps && count)) return QS_ERR_ARG;
   const size_t total = size_t(1) << s->ns;
   if (first > total || count > total - first) return QS_ERR_ARG;
@@ -424,7 +492,7 @@ qs_status qs_apply_ctrl_multi_target(qs_state* s, const int* ctrls, int nctrl, c
   if (s->is_density && nctrl == 0 && ntarg == 2 && tc) {
     void* dsup = nullptr;
     int slot_s = -1;
-    st = ring_take(s, &dsup, &slot_s);
+    st = ring_take(s, sizeof(double) * 2 * 256, &dsup, &slot_s);
     if (st == QS_OK)
       st = cuda_status(qsk::launch_superop(static_cast<const double*>(dmat), 1, 2, static_cast<double*>(dsup),
                                            s->stream));
@@ -545,7 +613,7 @@ qs_status qs_apply_kraus(qs_state* s, const int* targs, int n, const double* kra
   int slot_k = -1, slot_s = -1;
   st = ring_put(s, kraus, kbytes, &dk, &slot_k);
   if (st != QS_OK) return st;
-  st = ring_take(s, &dsup, &slot_s);
+  st = ring_take(s, sizeof(double) * 2 * ((size_t)1 << (4 * n)), &dsup, &slot_s);
   if (st == QS_OK)
     st = cuda_status(qsk::launch_superop(static_cast<const double*>(dk), num_ops, n, static_cast<double*>(dsup),
                                          s->stream));
@@ -629,6 +697,7 @@ qs_status qs_apply_pauli_channel(qs_state* s, int t, double px, double py, doubl
 }
 
 qs_status qs_partial_trace(const qs_state* in, const int* targs, int n, void* d_out_amps, qs_state** out) {
+  if (in && in->rec) return QS_ERR_ARG;   // not while recording
   if (!in || !out || !d_out_amps) return QS_ERR_ARG;
   *out = nullptr;
   if (!in->is_density) return QS_ERR_NOT_DENSMATR;
@@ -663,6 +732,7 @@ qs_status qs_partial_trace(const qs_state* in, const int* targs, int n, void* d_
 
 qs_status qs_expec_pauli_sum(const qs_state* cs, const int* paulis, const double* coeffs, int num_terms,
                              double* out) {
+  if (cs && cs->rec) return QS_ERR_ARG;   // not while recording
   qs_state* s = const_cast<qs_state*>(cs);
   if (!s || !paulis || !coeffs || !out || num_terms < 1) return QS_ERR_ARG;
   std::vector<qsk::PauliTerm> terms((size_t)num_terms);
@@ -716,6 +786,7 @@ qs_status qs_expec_pauli_sum(const qs_state* cs, const int* paulis, const double
 }
 
 qs_status qs_calc_norm_or_trace(const qs_state* cs, double* out) {
+  if (cs && cs->rec) return QS_ERR_ARG;   // not while recording
   qs_state* s = const_cast<qs_state*>(cs);
   if (!s || !out) return QS_ERR_ARG;
   cudaError_t e = s->is_density ? qsk::launch_trace(s->prec, s->amps, s->nq, s->d_partials, s->stream)
@@ -728,6 +799,7 @@ qs_status qs_calc_norm_or_trace(const qs_state* cs, double* out) {
 }
 
 qs_status qs_synchronize(const qs_state* s) {
+  if (s && s->rec) return QS_ERR_ARG;   // not while recording
   if (!s) return QS_ERR_ARG;
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return QS_ERR_CUDA;
   int err = 0;
@@ -737,6 +809,66 @@ qs_status qs_synchronize(const qs_state* s) {
     return QS_ERR_TIMEOUT;
   }
   return QS_OK;
+}
+
+qs_status qs_record_begin(qs_state* s) {
+  if (!s || s->rec || !s->stream) return QS_ERR_ARG;
+  qs_program* p = new (std::nothrow) qs_program();
+  if (!p) return QS_ERR_OOM;
+  p->state = s;
+  if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    program_free(p);
+    return QS_ERR_CUDA;
+  }
+  if (!rec_alloc(p, 256)) {
+    program_free(p);
+    return QS_ERR_OOM;
+  }
+  // relaxed: the uploads on the side stream and arena allocations may run
+  // during the capture
+  if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    program_free(p);
+    return QS_ERR_CUDA;
+  }
+  s->rec = p;
+  return QS_OK;
+}
+
+qs_status qs_record_end(qs_state* s, qs_program** out) {
+  if (!s || !s->rec || !out) return QS_ERR_ARG;
+  *out = nullptr;
+  qs_program* p = s->rec;
+  s->rec = nullptr;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+  if (e != cudaSuccess || !g) {
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    program_free(p);
+    return QS_ERR_CUDA;
+  }
+  p->graph = g;
+  if (cudaGraphInstantiate(&p->exec, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    program_free(p);
+    return QS_ERR_CUDA;
+  }
+  *out = p;
+  return QS_OK;
+}
+
+qs_status qs_program_run(qs_program* p) {
+  if (!p || !p->exec || p->state->rec) return QS_ERR_ARG;
+  return cuda_status(cudaGraphLaunch(p->exec, p->state->stream));
+}
+
+qs_status qs_program_destroy(qs_program* p) {
+  if (!p) return QS_ERR_ARG;
+  const cudaError_t e = cudaStreamSynchronize(p->state->stream);
+  program_free(p);
+  return cuda_status(e);
 }
 
 }  // extern "C"

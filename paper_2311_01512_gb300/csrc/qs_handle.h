@@ -36,6 +36,9 @@ struct qs_state {
   unsigned char* d_ring = nullptr;
   cudaEvent_t ring_ev[qsapi::kRingSlots] = {};
   int ring_next = 0;
+  // between qs_record_begin and qs_record_end: the program being recorded
+  // (operation data goes to its device arena instead of the ring)
+  qs_program* rec = nullptr;
 };
 
 namespace qsapi {
@@ -43,6 +46,8 @@ namespace qsapi {
 qs_status cuda_status(cudaError_t e);
 qs_status check_qubits(int nq, const int* targs, int ntarg, const int* ctrls, int nctrl);
 qs_status ring_put(qs_state* s, const void* host, size_t bytes, const void** dev, int* slot);
+// device scratch for `bytes` written by a kernel (ring slot, or arena while recording)
+qs_status ring_take(qs_state* s, size_t bytes, void** dev, int* slot);
 qs_status ring_done(qs_state* s, int slot);
 // One dense-gate pass on storage positions (already shifted for the conjugate
 // pass of a density matrix).  host_mat is needed only for one-target gates

@@ -64,6 +64,10 @@ SIGNATURES = {
     "qs_expec_pauli_sum": (_I, [_P, _IP, _DP, _I, _DP]),
     "qs_calc_norm_or_trace": (_I, [_P, _DP]),
     "qs_synchronize": (_I, [_P]),
+    "qs_record_begin": (_I, [_P]),
+    "qs_record_end": (_I, [_P, ctypes.POINTER(_P)]),
+    "qs_program_run": (_I, [_P]),
+    "qs_program_destroy": (_I, [_P]),
     "qs_expec_pauli_sum_noalloc": (_I, [_P, _I, _I, _I, _IP, _DP, _I, _P, _DP]),
     "qs_circuit_create": (_I, [_I, ctypes.POINTER(_P)]),
     "qs_circuit_destroy": (_I, [_P]),
@@ -292,6 +296,24 @@ def qs_calc_norm_or_trace(h):
 
 def qs_synchronize(h):
     _check(_lib.qs_synchronize(h), "qs_synchronize")
+
+
+def qs_record_begin(h):
+    _check(_lib.qs_record_begin(h), "qs_record_begin")
+
+
+def qs_record_end(h):
+    p = _P()
+    _check(_lib.qs_record_end(h, ctypes.byref(p)), "qs_record_end")
+    return p
+
+
+def qs_program_run(p):
+    _check(_lib.qs_program_run(p), "qs_program_run")
+
+
+def qs_program_destroy(p):
+    _check(_lib.qs_program_destroy(p), "qs_program_destroy")
 
 
 def qs_get_info(h):
