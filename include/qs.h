@@ -407,8 +407,10 @@ qs_status qs_synchronize(const qs_state* state);
  *   (QS_ERR_ARG otherwise).  One recording per state at a time.
  * - qs_program_run queues one replay on the state's stream (asynchronous); a
  *   replay applies the recorded operations to the state's current amplitudes.
- * - The program must be destroyed before its state; qs_program_destroy waits
- *   for the state's stream.
+ * - The program must be destroyed before its state, and before any planned
+ *   circuit whose qs_circuit_apply it recorded (the fused blocks' matrices stay
+ *   in the circuit's device memory); qs_program_destroy waits for the state's
+ *   stream.
  * ------------------------------------------------------------------------- */
 typedef struct qs_program qs_program;
 qs_status qs_record_begin(qs_state* state);
