@@ -322,20 +322,30 @@ qs_status qs_circuit_plan_cost(qs_circuit* circuit, qs_costmodel* model, const q
                                int max_block_qubits, int window);
 
 /* ------------------------------------------------------------------------
- * Batched engine (not in the paper): many independent statevectors of at
- * most 24 qubits, each with its own circuit of dense gates (1 or 2 targets,
- * up to 5 controls), diagonals (up to 3 targets) and Pauli gadgets, run by
- * ONE persistent kernel launch recorded in a CUDA graph.  CTAs take states
- * from a work counter, largest first; a state that fits in shared memory is
- * processed there.  complex64 in FP32, complex128 in double-float
- * arithmetic (see qs_arith).  The gate semantics are those of
- * qs_apply_ctrl_multi_target, qs_apply_diagonal and qs_apply_pauli_gadget.
+ * Batched engine (not in the paper): many independent states of at most 24
+ * storage qubits (statevectors, or density matrices of at most 12 qubits as
+ * Choi vectors), each with its own circuit of dense gates (1 or 2 targets,
+ * up to 5 controls), diagonals (up to 3 targets), Pauli gadgets and, on
+ * density matrices, Kraus maps and the decoherence channels, run by ONE
+ * persistent kernel launch recorded in a CUDA graph.  CTAs take states from
+ * a work counter, largest first; a state that fits in shared memory is
+ * processed there, a larger one tile by tile.  complex64 in FP32, complex128
+ * in double-float arithmetic (see qs_arith).  The semantics are those of the
+ * single-state calls of the same names (qs_apply_ctrl_multi_target, ...,
+ * qs_apply_damping); on a density matrix a unitary, diagonal or gadget is
+ * applied as U on t and U* on t + N, a Kraus map or channel as one pass of
+ * its superoperator on (t, t + N) or (t1, t2, t1 + N, t2 + N).
  * ------------------------------------------------------------------------ */
 typedef struct qs_batch qs_batch;
 
-/* num_qubits[s] in 1..24 for every state s; all states share `prec` and the
- * stream. */
+/* Statevectors only: num_qubits[s] in 1..24 for every state s; all states
+ * share `prec` and the stream. */
 qs_status qs_batch_create(int num_states, const int* num_qubits, qs_prec prec, void* cuda_stream, qs_batch** out);
+/* is_density[s] != 0: state s is an num_qubits[s]-qubit density matrix held
+ * as a 2 num_qubits[s]-qubit Choi vector (is_density NULL: all
+ * statevectors).  Storage qubits at most 24. */
+qs_status qs_batch_create_mixed(int num_states, const int* num_qubits, const int* is_density, qs_prec prec,
+                                void* cuda_stream, qs_batch** out);
 qs_status qs_batch_destroy(qs_batch* batch);
 /* Amplitudes the caller's device pool must hold, and where state s starts
  * (each state starts on a 256-byte boundary). */
@@ -348,6 +358,18 @@ qs_status qs_batch_add_unitary(qs_batch* batch, int state, const int* ctrls, int
 qs_status qs_batch_add_diagonal(qs_batch* batch, int state, const int* targs, int ntarg, const double* diag);
 qs_status qs_batch_add_pauli_gadget(qs_batch* batch, int state, const int* targs, const int* paulis, int n,
                                     double theta);
+/* Density-matrix states only (QS_ERR_NOT_DENSMATR otherwise): a Kraus map of
+ * num_ops operators on n = 1 or 2 targets (as qs_apply_kraus), and the
+ * channels of qs_apply_dephasing, qs_apply_two_qubit_dephasing,
+ * qs_apply_depolarising, qs_apply_two_qubit_depolarising, qs_apply_damping
+ * and qs_apply_pauli_channel (probabilities in [0, 1]). */
+qs_status qs_batch_add_kraus(qs_batch* batch, int state, const int* targs, int n, const double* kraus, int num_ops);
+qs_status qs_batch_add_dephasing(qs_batch* batch, int state, int t, double p);
+qs_status qs_batch_add_two_qubit_dephasing(qs_batch* batch, int state, int t1, int t2, double p);
+qs_status qs_batch_add_depolarising(qs_batch* batch, int state, int t, double p);
+qs_status qs_batch_add_two_qubit_depolarising(qs_batch* batch, int state, int t1, int t2, double p);
+qs_status qs_batch_add_damping(qs_batch* batch, int state, int t, double p);
+qs_status qs_batch_add_pauli_channel(qs_batch* batch, int state, int t, double px, double py, double pz);
 /* Upload the programs and record the launch in a CUDA graph.  With
  * autotune != 0 every candidate launch shape is timed by running the whole
  * batch once on the bound pool: the pool's contents are unspecified

@@ -29,18 +29,23 @@
 struct qs_batch {
   qs_prec prec = QS_C64;
   cudaStream_t stream = nullptr;
-  std::vector<int> nq;
+  std::vector<int> nq;          // storage qubits (2N for a density matrix)
+  std::vector<int> nlog;        // N: the qubits operations name
+  std::vector<int> dens;        // density matrix (Choi vector) or statevector
   std::vector<size_t> offset;  // amplitudes
   size_t pool_amps = 0;
   void* pool = nullptr;
   std::vector<std::vector<qsk::BatchOp>> progs;
+  std::vector<std::vector<double>> consts;   // per state; BatchOp::coff indexes it until compile
   qsk::BatchState* d_states = nullptr;
   qsk::BatchSeg* d_segs = nullptr;
   qsk::BatchXlat* d_xlat = nullptr;
   int* d_order = nullptr;
   qsk::BatchOp* d_ops = nullptr;
+  double* d_consts = nullptr;
   int* d_counter = nullptr;
   long num_segs = 0;
+  int wide = 0;                 // some operation is dense on 3 or 4 targets
   int threads = 256, ctas = 0, smem_qubits = -1;
   cudaStream_t capture_stream = nullptr;  // own stream for recording (the caller's may be the legacy stream)
   cudaGraph_t graph = nullptr;
@@ -56,8 +61,9 @@ void free_device(qs_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   for (void* p : {(void*)b->d_states, (void*)b->d_segs, (void*)b->d_xlat, (void*)b->d_order, (void*)b->d_ops,
-                  (void*)b->d_counter})
+                  (void*)b->d_consts, (void*)b->d_counter})
     if (p) cudaFree(p);
+  b->d_consts = nullptr;
   b->exec = nullptr;
   b->graph = nullptr;
   b->d_states = nullptr;
@@ -74,10 +80,69 @@ qs_status check_state(const qs_batch* b, int s) {
   return QS_OK;
 }
 
-qs_status add(qs_batch* b, int s, qsk::BatchOp&& op) {
+// one operation on storage qubits, with its nc constants
+qs_status add(qs_batch* b, int s, qsk::BatchOp op, const double* c, size_t nc) {
+  op.coff = b->consts[s].size();
+  b->consts[s].insert(b->consts[s].end(), c, c + nc);
   b->progs[s].push_back(op);
   b->compiled = false;
   return QS_OK;
+}
+
+// dense operation on storage targets t (matrix bit q on t[q]) with storage controls c
+qs_status add_dense(qs_batch* b, int s, const std::vector<int>& c, const std::vector<int>& t, const double* mat) {
+  qsk::BatchOp op{};
+  op.kind = 0;
+  op.n = (int)t.size();
+  std::vector<int> ins(t);
+  for (int q = 0; q < op.n; ++q) op.t[q] = t[q];
+  for (int q : c) {
+    op.ctrl |= 1u << q;
+    ins.push_back(q);
+  }
+  if (ins.size() > 7) return QS_ERR_TOO_MANY_TARGETS;
+  std::sort(ins.begin(), ins.end());
+  op.nins = (int)ins.size();
+  for (int i = 0; i < op.nins; ++i) op.ins[i] = (int8_t)ins[i];
+  return add(b, s, op, mat, (size_t)2 << (2 * op.n));
+}
+
+// Superoperator of a channel on the Choi vector as a dense operation on
+// (t, t + N) (one qubit) or (t1, t2, t1 + N, t2 + N) (two qubits): member m
+// has bit q of m on the q-th of those positions; S (real, row-major, d x d)
+// gives new beta_m = sum_k S[m][k] beta_k.
+qs_status add_superop(qs_batch* b, int s, const std::vector<int>& targs, const std::vector<double>& S) {
+  const int n = (int)targs.size(), d = 1 << (2 * n);
+  std::vector<int> t(targs);
+  for (int q = 0; q < n; ++q) t.push_back(targs[q] + b->nlog[s]);
+  std::vector<double> m((size_t)2 * d * d, 0.0);
+  for (int i = 0; i < d * d; ++i) m[2 * i] = S[i];
+  return add_dense(b, s, {}, t, m.data());
+}
+
+qs_status check_density(const qs_batch* b, int s) {
+  if (check_state(b, s) != QS_OK) return QS_ERR_ARG;
+  return b->dens[s] ? QS_OK : QS_ERR_NOT_DENSMATR;
+}
+
+qs_status check_prob(double p) { return (p >= 0.0 && p <= 1.0) ? QS_OK : QS_ERR_ARG; }
+
+// One-qubit channels in the paper's Choi-vector form: members 00 and 11 (bits
+// t, t + N) mix as f0 self + f1 other; 01 and 10 as f2 self + f3 other.
+qs_status add_channel1(qs_batch* b, int s, int t, double f0, double f1, double f2, double f3) {
+  if (check_density(b, s) != QS_OK) return check_density(b, s);
+  qs_status st = qsapi::check_qubits(b->nlog[s], &t, 1, nullptr, 0);
+  if (st != QS_OK) return st;
+  std::vector<double> S(16, 0.0);
+  S[0 * 4 + 0] = f0;  // 00
+  S[0 * 4 + 3] = f1;
+  S[3 * 4 + 3] = f0;  // 11
+  S[3 * 4 + 0] = f1;
+  S[1 * 4 + 1] = f2;  // 01 (bit t set)
+  S[1 * 4 + 2] = f3;
+  S[2 * 4 + 2] = f2;  // 10
+  S[2 * 4 + 1] = f3;
+  return add_superop(b, s, {t}, S);
 }
 
 int smem_qubits_for(qs_prec prec, int ctas_per_sm) {
@@ -129,7 +194,7 @@ int local_pos(uint32_t qmask, int t) {
 
 qsk::BatchXlat translate(const qsk::BatchOp& op, uint32_t qmask) {
   qsk::BatchXlat x{};
-  for (int q = 0; q < 3; ++q) x.lt[q] = -1;
+  for (int q = 0; q < 4; ++q) x.lt[q] = -1;
   if (op.kind == 0) {
     std::vector<int> lins;
     for (int q = 0; q < op.n; ++q) {
@@ -241,22 +306,55 @@ bool upload_plan(Plan& P) {
                                       cudaMemcpyHostToDevice) == cudaSuccess;
 }
 
+// Two-qubit channels on the members of (t1, t2, t1 + N, t2 + N): member bits
+// 0, 1 are t1, t2 and bits 2, 3 are t1 + N, t2 + N.
+qs_status add_channel2(qs_batch* b, int state, int t1, int t2, bool depol, double p) {
+  if (check_density(b, state) != QS_OK) return check_density(b, state);
+  const int tt[2] = {t1, t2};
+  qs_status st = qsapi::check_qubits(b->nlog[state], tt, 2, nullptr, 0);
+  if (st != QS_OK) return st;
+  std::vector<double> S(256, 0.0);
+  for (int m = 0; m < 16; ++m) {
+    const bool same1 = ((m >> 0) & 1) == ((m >> 2) & 1), same2 = ((m >> 1) & 1) == ((m >> 3) & 1);
+    if (!depol) {
+      S[m * 16 + m] = (same1 && same2) ? 1.0 : 1.0 - 4.0 * p / 3.0;
+    } else if (same1 && same2) {
+      S[m * 16 + m] = 1.0 - 4.0 * p / 5.0;
+      for (int f : {0x5, 0xA, 0xF}) S[m * 16 + (m ^ f)] = 4.0 * p / 15.0;   // flip t1 pair, t2 pair, both
+    } else {
+      S[m * 16 + m] = 1.0 - 16.0 * p / 15.0;
+    }
+  }
+  return add_superop(b, state, {t1, t2}, S);
+}
+
 }  // namespace
 
 extern "C" {
 
 qs_status qs_batch_create(int num_states, const int* num_qubits, qs_prec prec, void* cuda_stream, qs_batch** out) {
+  return qs_batch_create_mixed(num_states, num_qubits, nullptr, prec, cuda_stream, out);
+}
+
+qs_status qs_batch_create_mixed(int num_states, const int* num_qubits, const int* is_density, qs_prec prec,
+                                void* cuda_stream, qs_batch** out) {
   if (!out || num_states < 1 || !num_qubits || (prec != QS_C64 && prec != QS_C128)) return QS_ERR_ARG;
   *out = nullptr;
   qs_batch* b = new (std::nothrow) qs_batch();
   if (!b) return QS_ERR_OOM;
   b->prec = prec;
   b->stream = static_cast<cudaStream_t>(cuda_stream);
-  b->nq.assign(num_qubits, num_qubits + num_states);
+  b->nlog.assign(num_qubits, num_qubits + num_states);
+  b->dens.assign(num_states, 0);
+  if (is_density)
+    for (int s = 0; s < num_states; ++s) b->dens[s] = is_density[s] ? 1 : 0;
+  for (int s = 0; s < num_states; ++s) b->nq.push_back(b->dens[s] ? 2 * b->nlog[s] : b->nlog[s]);
   b->progs.resize(num_states);
+  b->consts.resize(num_states);
   size_t off = 0;
-  for (int q : b->nq) {
-    if (q < 1 || q > 24) {
+  for (int s = 0; s < num_states; ++s) {
+    const int q = b->nq[s];
+    if (b->nlog[s] < 1 || q > 24) {
       delete b;
       return QS_ERR_ARG;
     }
@@ -301,60 +399,136 @@ qs_status qs_batch_add_unitary(qs_batch* b, int state, const int* ctrls, int nct
                                const double* mat) {
   if (check_state(b, state) != QS_OK || !mat || ntarg < 1) return QS_ERR_ARG;
   if (ntarg > 2 || nctrl > 5) return QS_ERR_TOO_MANY_TARGETS;
-  qs_status st = qsapi::check_qubits(b->nq[state], targs, ntarg, ctrls, nctrl);
+  qs_status st = qsapi::check_qubits(b->nlog[state], targs, ntarg, ctrls, nctrl);
   if (st != QS_OK) return st;
-  qsk::BatchOp op{};
-  op.kind = 0;
-  op.n = ntarg;
-  std::vector<int> ins;
-  for (int q = 0; q < ntarg; ++q) {
-    op.t[q] = targs[q];
-    ins.push_back(targs[q]);
-  }
-  for (int q = 0; q < nctrl; ++q) {
-    op.ctrl |= 1u << ctrls[q];
-    ins.push_back(ctrls[q]);
-  }
-  std::sort(ins.begin(), ins.end());
-  op.nins = (int)ins.size();
-  for (int i = 0; i < op.nins; ++i) op.ins[i] = (int8_t)ins[i];
-  std::memcpy(op.m, mat, sizeof(double) * 2 * (1u << (2 * ntarg)));
-  return add(b, state, std::move(op));
+  std::vector<int> c(ctrls, ctrls + nctrl), t(targs, targs + ntarg);
+  st = add_dense(b, state, c, t, mat);
+  if (st != QS_OK || !b->dens[state]) return st;
+  // density matrix: U^* on t + N with controls c + N (Sec. "Unitary gates")
+  const size_t nm = (size_t)2 << (2 * ntarg);
+  std::vector<double> conj(mat, mat + nm);
+  for (size_t i = 1; i < nm; i += 2) conj[i] = -conj[i];
+  for (int& q : c) q += b->nlog[state];
+  for (int& q : t) q += b->nlog[state];
+  return add_dense(b, state, c, t, conj.data());
 }
 
 qs_status qs_batch_add_diagonal(qs_batch* b, int state, const int* targs, int ntarg, const double* diag) {
   if (check_state(b, state) != QS_OK || !diag || ntarg < 1) return QS_ERR_ARG;
   if (ntarg > 3) return QS_ERR_TOO_MANY_TARGETS;
-  qs_status st = qsapi::check_qubits(b->nq[state], targs, ntarg, nullptr, 0);
+  qs_status st = qsapi::check_qubits(b->nlog[state], targs, ntarg, nullptr, 0);
   if (st != QS_OK) return st;
   qsk::BatchOp op{};
   op.kind = 1;
   op.n = ntarg;
   for (int q = 0; q < ntarg; ++q) op.t[q] = targs[q];
-  std::memcpy(op.m, diag, sizeof(double) * 2 * (1u << ntarg));
-  return add(b, state, std::move(op));
+  const size_t nd = (size_t)2 << ntarg;
+  st = add(b, state, op, diag, nd);
+  if (st != QS_OK || !b->dens[state]) return st;
+  std::vector<double> conj(diag, diag + nd);   // density matrix: conj(d) on t + N
+  for (size_t i = 1; i < nd; i += 2) conj[i] = -conj[i];
+  for (int q = 0; q < ntarg; ++q) op.t[q] = targs[q] + b->nlog[state];
+  return add(b, state, op, conj.data(), nd);
 }
 
 qs_status qs_batch_add_pauli_gadget(qs_batch* b, int state, const int* targs, const int* paulis, int n,
                                     double theta) {
   if (check_state(b, state) != QS_OK || n < 0 || (n > 0 && (!targs || !paulis))) return QS_ERR_ARG;
-  qs_status st = qsapi::check_qubits(b->nq[state], targs, n, nullptr, 0);
+  qs_status st = qsapi::check_qubits(b->nlog[state], targs, n, nullptr, 0);
   if (st != QS_OK) return st;
-  qsk::BatchOp op{};
-  op.kind = 2;
-  int ny = 0;
-  for (int q = 0; q < n; ++q) {
+  for (int q = 0; q < n; ++q)
     if (paulis[q] < 0 || paulis[q] > 3) return QS_ERR_ARG;
-    if (paulis[q] == 1 || paulis[q] == 2) op.xy |= 1u << targs[q];
-    if (paulis[q] == 2 || paulis[q] == 3) op.yz |= 1u << targs[q];
-    if (paulis[q] == 2) ++ny;
+  auto one = [&](int shift, double th) {
+    qsk::BatchOp op{};
+    op.kind = 2;
+    int ny = 0;
+    for (int q = 0; q < n; ++q) {
+      const int t = targs[q] + shift;
+      if (paulis[q] == 1 || paulis[q] == 2) op.xy |= 1u << t;
+      if (paulis[q] == 2 || paulis[q] == 3) op.yz |= 1u << t;
+      if (paulis[q] == 2) ++ny;
+    }
+    op.eta = ny & 3;
+    op.h = op.xy ? 31 - __builtin_clz(op.xy) : 0;
+    const double phi = -0.5 * th;
+    const double cs[2] = {std::cos(phi), std::sin(phi)};
+    return add(b, state, op, cs, 2);
+  };
+  st = one(0, theta);
+  if (st != QS_OK || !b->dens[state]) return st;
+  int ny = 0;
+  for (int q = 0; q < n; ++q) ny += paulis[q] == 2;
+  // U(theta)^* = U((-1)^(#Y + 1) theta) on t + N (Algorithm "specific unitaries on density matrices")
+  return one(b->nlog[state], (ny % 2 == 0) ? -theta : theta);
+}
+
+qs_status qs_batch_add_kraus(qs_batch* b, int state, const int* targs, int n, const double* kraus, int num_ops) {
+  if (check_state(b, state) != QS_OK || !kraus || !targs || num_ops < 1 || n < 1) return QS_ERR_ARG;
+  if (!b->dens[state]) return QS_ERR_NOT_DENSMATR;
+  if (n > 2) return QS_ERR_TOO_MANY_TARGETS;
+  qs_status st = qsapi::check_qubits(b->nlog[state], targs, n, nullptr, 0);
+  if (st != QS_OK) return st;
+  // S = sum_m conj(K_m) (x) K_m: K on the ket bits t (low n bits of the member
+  // index), conj(K) on the bra bits t + N (Sec. "Kraus map")
+  const int d = 1 << n, dd = d * d;
+  std::vector<double> m((size_t)2 * dd * dd, 0.0);
+  for (int k = 0; k < num_ops; ++k) {
+    const double* K = kraus + (size_t)2 * d * d * k;
+    for (int ih = 0; ih < d; ++ih)
+      for (int il = 0; il < d; ++il)
+        for (int jh = 0; jh < d; ++jh)
+          for (int jl = 0; jl < d; ++jl) {
+            const double ar = K[2 * (ih * d + jh)], ai = -K[2 * (ih * d + jh) + 1];   // conj(K[ih][jh])
+            const double br = K[2 * (il * d + jl)], bi = K[2 * (il * d + jl) + 1];
+            const size_t e = (size_t)(ih * d + il) * dd + (jh * d + jl);
+            m[2 * e] += ar * br - ai * bi;
+            m[2 * e + 1] += ar * bi + ai * br;
+          }
   }
-  op.eta = ny & 3;
-  op.h = op.xy ? 31 - __builtin_clz(op.xy) : 0;
-  const double phi = -0.5 * theta;
-  op.c = std::cos(phi);
-  op.s = std::sin(phi);
-  return add(b, state, std::move(op));
+  std::vector<int> t(targs, targs + n);
+  for (int q = 0; q < n; ++q) t.push_back(targs[q] + b->nlog[state]);
+  return add_dense(b, state, {}, t, m.data());
+}
+
+// The channels, in the paper's Choi-vector update rules (Sec. "Dephasing
+// channel", "Depolarising channel", "Damping channel"), as superoperators.
+qs_status qs_batch_add_dephasing(qs_batch* b, int state, int t, double p) {
+  if (check_prob(p) != QS_OK) return QS_ERR_ARG;
+  return add_channel1(b, state, t, 1.0, 0.0, 1.0 - 2.0 * p, 0.0);
+}
+
+qs_status qs_batch_add_depolarising(qs_batch* b, int state, int t, double p) {
+  if (check_prob(p) != QS_OK) return QS_ERR_ARG;
+  return add_channel1(b, state, t, 1.0 - 2.0 * p / 3.0, 2.0 * p / 3.0, 1.0 - 4.0 * p / 3.0, 0.0);
+}
+
+qs_status qs_batch_add_pauli_channel(qs_batch* b, int state, int t, double px, double py, double pz) {
+  if (check_prob(px) != QS_OK || check_prob(py) != QS_OK || check_prob(pz) != QS_OK) return QS_ERR_ARG;
+  return add_channel1(b, state, t, 1.0 - px - py, px + py, 1.0 - px - py - 2.0 * pz, px - py);
+}
+
+qs_status qs_batch_add_damping(qs_batch* b, int state, int t, double p) {
+  if (check_prob(p) != QS_OK) return QS_ERR_ARG;
+  if (check_density(b, state) != QS_OK) return check_density(b, state);
+  qs_status st = qsapi::check_qubits(b->nlog[state], &t, 1, nullptr, 0);
+  if (st != QS_OK) return st;
+  std::vector<double> S(16, 0.0);
+  S[0 * 4 + 0] = 1.0;             // 00 -> 00 + p 11
+  S[0 * 4 + 3] = p;
+  S[1 * 4 + 1] = std::sqrt(1.0 - p);
+  S[2 * 4 + 2] = std::sqrt(1.0 - p);
+  S[3 * 4 + 3] = 1.0 - p;
+  return add_superop(b, state, {t}, S);
+}
+
+qs_status qs_batch_add_two_qubit_dephasing(qs_batch* b, int state, int t1, int t2, double p) {
+  if (check_prob(p) != QS_OK) return QS_ERR_ARG;
+  return add_channel2(b, state, t1, t2, false, p);
+}
+
+qs_status qs_batch_add_two_qubit_depolarising(qs_batch* b, int state, int t1, int t2, double p) {
+  if (check_prob(p) != QS_OK) return QS_ERR_ARG;
+  return add_channel2(b, state, t1, t2, true, p);
 }
 
 qs_status qs_batch_compile(qs_batch* b, int autotune) {
@@ -363,14 +537,22 @@ qs_status qs_batch_compile(qs_batch* b, int autotune) {
   const int S = (int)b->nq.size();
   std::vector<qsk::BatchState> states(S);
   std::vector<qsk::BatchOp> ops;
+  std::vector<double> consts;
   for (int s = 0; s < S; ++s) {
     states[s].offset = b->offset[s];
     states[s].nq = b->nq[s];
     states[s].first_op = (int)ops.size();
     states[s].nops = (int)b->progs[s].size();
-    ops.insert(ops.end(), b->progs[s].begin(), b->progs[s].end());
+    for (qsk::BatchOp op : b->progs[s]) {
+      op.coff += consts.size();
+      ops.push_back(op);
+    }
+    consts.insert(consts.end(), b->consts[s].begin(), b->consts[s].end());
   }
   b->total_ops = (long)ops.size();
+  b->wide = 0;
+  for (const auto& op : ops)
+    if (op.kind == 0 && op.n > 2) b->wide = 1;
   std::vector<int> order(S);
   for (int s = 0; s < S; ++s) order[s] = s;
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
@@ -379,6 +561,7 @@ qs_status qs_batch_compile(qs_batch* b, int autotune) {
   });
   if (cudaMalloc(&b->d_order, sizeof(int) * S) != cudaSuccess ||
       cudaMalloc(&b->d_ops, sizeof(qsk::BatchOp) * std::max<size_t>(1, ops.size())) != cudaSuccess ||
+      cudaMalloc(&b->d_consts, sizeof(double) * std::max<size_t>(1, consts.size())) != cudaSuccess ||
       cudaMalloc(&b->d_counter, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     free_device(b);
@@ -386,7 +569,9 @@ qs_status qs_batch_compile(qs_batch* b, int autotune) {
   }
   if (cudaMemcpy(b->d_order, order.data(), sizeof(int) * S, cudaMemcpyHostToDevice) != cudaSuccess ||
       (!ops.empty() &&
-       cudaMemcpy(b->d_ops, ops.data(), sizeof(qsk::BatchOp) * ops.size(), cudaMemcpyHostToDevice) != cudaSuccess)) {
+       cudaMemcpy(b->d_ops, ops.data(), sizeof(qsk::BatchOp) * ops.size(), cudaMemcpyHostToDevice) != cudaSuccess) ||
+      (!consts.empty() && cudaMemcpy(b->d_consts, consts.data(), sizeof(double) * consts.size(),
+                                     cudaMemcpyHostToDevice) != cudaSuccess)) {
     free_device(b);
     return QS_ERR_CUDA;
   }
@@ -429,8 +614,8 @@ qs_status qs_batch_compile(qs_batch* b, int autotune) {
     Plan* P = plan_for(sq);
     if (cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream) != cudaSuccess) return QS_ERR_CUDA;
     cudaEventRecord(e0, b->stream);
-    if (qsk::launch_batch(b->prec, b->pool, P->d_states, b->d_order, S, b->d_ops, P->d_segs, P->d_xlat,
-                          b->d_counter, c.first, sms * c.second, sq, b->stream) != cudaSuccess) {
+    if (qsk::launch_batch(b->prec, b->pool, P->d_states, b->d_order, S, b->d_ops, b->d_consts, P->d_segs,
+                          P->d_xlat, b->d_counter, c.first, sms * c.second, sq, b->wide, b->stream) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
@@ -466,8 +651,8 @@ qs_status qs_batch_compile(qs_batch* b, int autotune) {
   }
   cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->capture_stream);
   if (e == cudaSuccess)
-    e = qsk::launch_batch(b->prec, b->pool, b->d_states, b->d_order, S, b->d_ops, b->d_segs, b->d_xlat, b->d_counter,
-                          b->threads, b->ctas, b->smem_qubits, b->capture_stream);
+    e = qsk::launch_batch(b->prec, b->pool, b->d_states, b->d_order, S, b->d_ops, b->d_consts, b->d_segs, b->d_xlat,
+                          b->d_counter, b->threads, b->ctas, b->smem_qubits, b->wide, b->capture_stream);
   cudaGraph_t g = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &g);
   if (e != cudaSuccess || e2 != cudaSuccess || !g) {

@@ -7,9 +7,11 @@
 //
 // Operations (the statevector gates of Sec. "One-target gate", "Many-control
 // one-target gate", "Many-target gate", "Phase gadget", "Pauli gadget"):
-// dense gates on 1 or 2 targets with controls, diagonals on up to 3 targets,
-// Pauli gadgets.  complex64 states compute in FP32, complex128 states in
-// double-float (qs_df.cuh).
+// dense gates on 1 to 4 targets with controls, diagonals on up to 3 targets,
+// Pauli gadgets.  A density matrix is its Choi vector, on which the host has
+// lowered unitaries to their two passes and channels to superoperators
+// (dense operations on t and t + N).  complex64 states compute in FP32,
+// complex128 states in double-float (qs_df.cuh).
 #include "qs_device.cuh"
 #include "qs_df.cuh"
 
@@ -20,9 +22,9 @@ namespace {
 using qsdf::df;
 
 // ---- the operation's constants --------------------------------------------
-// Converted once per operation into shared memory (complex64: floats;
-// complex128: double-float pairs), up to 32 reals: a 4x4 matrix, 8 diagonal
-// entries, or cos / sin of a gadget.  Converting them per amplitude instead
+// Converted once per operation from the batch's pool of doubles into shared
+// memory (complex64: floats; complex128: double-float pairs), up to 512 reals:
+// a 16x16 matrix, 8 diagonal entries, or cos / sin of a gadget.  Converting them per amplitude instead
 // would put two f64 -> f32 conversions (FP64 rate) or two integer splits on
 // every multiply.
 template <typename T2>
@@ -41,12 +43,15 @@ struct Konst<double2> {
 template <typename T2>
 using KT = typename Konst<T2>::K;
 
+constexpr int kMaxConsts = 512;
+
 template <typename T2>
-__device__ __forceinline__ void load_consts(const BatchOp& op, typename Konst<T2>::K* kc) {
+__device__ __forceinline__ void load_consts(const BatchOp& op, const double* __restrict__ pool,
+                                            typename Konst<T2>::K* kc) {
   const int kind = op.kind;
   const int nreal = kind == 0 ? 2 << (2 * op.n) : (kind == 1 ? 2 << op.n : 2);
-  for (int i = threadIdx.x; i < nreal; i += blockDim.x)
-    kc[i] = Konst<T2>::conv(kind == 2 ? (i == 0 ? op.c : op.s) : op.m[i]);
+  const double* src = pool + op.coff;
+  for (int i = threadIdx.x; i < nreal; i += blockDim.x) kc[i] = Konst<T2>::conv(src[i]);
 }
 
 // ---- element access -----------------------------------------------------------
@@ -176,6 +181,26 @@ __device__ __forceinline__ void op_dense2(float2* a, const uint32_t* idx, const 
 #pragma unroll
   for (int j = 0; j < 4; ++j) a[idx[j]] = y[j];
 }
+// amplitude l of a dense group: base with target bit q set where bit q of l is
+template <int NT>
+__device__ __forceinline__ uint32_t group_index(uint32_t base, const uint32_t* tb, int l) {
+  uint32_t o = base;
+#pragma unroll
+  for (int q = 0; q < NT; ++q)
+    if ((l >> q) & 1) o |= tb[q];
+  return o;
+}
+
+// dense on the 2^NT amplitudes of the group at base
+template <int NT>
+__device__ __forceinline__ void op_denseN(float2* a, uint32_t base, const uint32_t* tb, const float* m) {
+  constexpr int D = 1 << NT;
+  CF x[D];
+#pragma unroll
+  for (int l = 0; l < D; ++l) x[l] = ld(a, group_index<NT>(base, tb, l));
+#pragma unroll
+  for (int j = 0; j < D; ++j) a[group_index<NT>(base, tb, j)] = cdot_f32<D>(m + 2 * D * j, x);   // inputs read first
+}
 __device__ __forceinline__ void op_diag(float2* a, uint32_t i, const float* d) {
   const float2 v = a[i];
   a[i] = make_float2(d[0] * v.x - d[1] * v.y, d[0] * v.y + d[1] * v.x);
@@ -201,6 +226,19 @@ __device__ __forceinline__ void op_dense2(P* a, const uint32_t* idx, const df* m
     qsdf::dot_acc re, im;
     cdot_df<4>(m + 8 * j, x, re, im);
     st(a, idx[j], re, im);
+  }
+}
+template <int NT, typename P>
+__device__ __forceinline__ void op_denseN(P* a, uint32_t base, const uint32_t* tb, const df* m) {
+  constexpr int D = 1 << NT;
+  CDF x[D];
+#pragma unroll
+  for (int l = 0; l < D; ++l) x[l] = ld(a, group_index<NT>(base, tb, l));
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    qsdf::dot_acc re, im;
+    cdot_df<D>(m + 2 * D * j, x, re, im);
+    st(a, group_index<NT>(base, tb, j), re, im);
   }
 }
 template <typename P>
@@ -269,9 +307,22 @@ __device__ __forceinline__ void op_pair(P* a, uint32_t i, uint32_t j, const Gad<
   st(a, j, r1, i1);
 }
 
+// dense sweep on 3 or 4 targets: target bits tb[q] (global or tile-local).
+// Out of line, so its registers do not weigh on the other operations.
+template <int NT, typename P, typename K>
+__device__ __noinline__ void dense_sweep(P* a, uint32_t groups, InsMasks ins, uint32_t ctrl, uint32_t tb0,
+                                         uint32_t tb1, uint32_t tb2, uint32_t tb3, const K* kc) {
+  const uint32_t tb[4] = {tb0, tb1, tb2, tb3};
+  for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x)
+    op_denseN<NT>(a, insert_zeros_m(g, ins) | ctrl, tb, kc);
+}
+
 // ---- one operation on a whole state held at `a` (shared or global) ---------
 // kc: the operation's constants (load_consts).
-template <typename P, typename K>
+// WIDE: the batch has dense operations on 3 or 4 targets (superoperators of
+// density-matrix channels); without them the kernel carries no call to the
+// out-of-line sweeps, whose call sites cost the narrow kernel registers.
+template <bool WIDE, typename P, typename K>
 __device__ void apply_op(P* a, int nq, const BatchOp& op, const K* kc) {
   const uint32_t dim = 1u << nq;
   const int kind = op.kind, n = op.n;
@@ -288,12 +339,18 @@ __device__ void apply_op(P* a, int nq, const BatchOp& op, const K* kc) {
         const uint32_t base = insert_zeros_m(g, ins) | ctrl;
         op_dense1(a, base, base | b0, m);
       }
-    } else {
+    } else if (n == 2) {
       for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
         const uint32_t base = insert_zeros_m(g, ins) | ctrl;
         const uint32_t idx[4] = {base, base | b0, base | b1, base | b0 | b1};
         op_dense2(a, idx, kc);
       }
+    } else if constexpr (WIDE) {
+      const uint32_t tb2 = 1u << op.t[2], tb3 = n > 3 ? 1u << op.t[3] : 0u;
+      if (n == 3)
+        dense_sweep<3>(a, groups, ins, ctrl, b0, b1, tb2, tb3, kc);
+      else
+        dense_sweep<4>(a, groups, ins, ctrl, b0, b1, tb2, tb3, kc);
     }
   } else if (kind == 1) {
     const int t0 = op.t[0], t1 = n > 1 ? op.t[1] : 0, t2 = n > 2 ? op.t[2] : 0;
@@ -324,7 +381,7 @@ __device__ void apply_op(P* a, int nq, const BatchOp& op, const K* kc) {
 // qubits); the translation x gives the operation's masks in local terms and
 // the parts outside the tile, which are constant over the tile (taken from
 // base).
-template <typename P, typename K>
+template <bool WIDE, typename P, typename K>
 __device__ void apply_tile_op(P* a, int L, const BatchOp& op, const BatchXlat& x, uint32_t base, const K* kc) {
   const uint32_t dim = 1u << L;
   const int kind = op.kind, n = op.n;
@@ -342,12 +399,18 @@ __device__ void apply_tile_op(P* a, int L, const BatchOp& op, const BatchXlat& x
         const uint32_t lb = insert_zeros_m(g, ins) | ctrl;
         op_dense1(a, lb, lb | b0, m);
       }
-    } else {
+    } else if (n == 2) {
       for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
         const uint32_t lb = insert_zeros_m(g, ins) | ctrl;
         const uint32_t idx[4] = {lb, lb | b0, lb | b1, lb | b0 | b1};
         op_dense2(a, idx, kc);
       }
+    } else if constexpr (WIDE) {
+      const uint32_t tb2 = 1u << x.lt[2], tb3 = n > 3 ? 1u << x.lt[3] : 0u;
+      if (n == 3)
+        dense_sweep<3>(a, groups, ins, ctrl, b0, b1, tb2, tb3, kc);
+      else
+        dense_sweep<4>(a, groups, ins, ctrl, b0, b1, tb2, tb3, kc);
     }
   } else if (kind == 1) {
     int jfix = 0, lt[3] = {-1, -1, -1};
@@ -386,17 +449,17 @@ __device__ void apply_tile_op(P* a, int L, const BatchOp& op, const BatchXlat& x
 // gather per amplitude through two 128-entry offset tables; the five lowest
 // qubits are always tile qubits, so a warp reads 32 consecutive amplitudes),
 // applies the segment's operations to it and writes it back.
-template <typename T2>
+template <typename T2, bool WIDE>
 __global__ void __launch_bounds__(512, sizeof(T2) == 8 ? 2 : 1)
     k_batch(T2* __restrict__ pool, const BatchState* __restrict__ states, const int* __restrict__ order, int nstates,
-            const BatchOp* __restrict__ ops, const BatchSeg* __restrict__ segs, const BatchXlat* __restrict__ xlat,
-            int* __restrict__ counter, int smem_qubits) {
+            const BatchOp* __restrict__ ops, const double* __restrict__ consts, const BatchSeg* __restrict__ segs,
+            const BatchXlat* __restrict__ xlat, int* __restrict__ counter, int smem_qubits) {
   using SM = SmemOf<T2>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   typename SM::T* sm = reinterpret_cast<typename SM::T*>(smem_raw);
   __shared__ int s_work;
   __shared__ uint32_t s_tl[128], s_th[128];
-  __shared__ KT<T2> s_k[2][32];          // constants of the current and the next operation
+  __shared__ KT<T2> s_k[2][kMaxConsts];  // constants of the current and the next operation
   while (true) {
     if (threadIdx.x == 0) s_work = atomicAdd(counter, 1);
     __syncthreads();
@@ -408,11 +471,11 @@ __global__ void __launch_bounds__(512, sizeof(T2) == 8 ? 2 : 1)
     const uint32_t dim = 1u << st.nq;
     if (st.nq <= smem_qubits) {
       for (uint32_t i = threadIdx.x; i < dim; i += blockDim.x) sm[i] = SM::in(g[i]);
-      if (st.nops > 0) load_consts<T2>(ops[st.first_op], s_k[0]);
+      if (st.nops > 0) load_consts<T2>(ops[st.first_op], consts, s_k[0]);
       __syncthreads();
       for (int k = 0; k < st.nops; ++k) {
-        apply_op(sm, st.nq, ops[st.first_op + k], s_k[k & 1]);
-        if (k + 1 < st.nops) load_consts<T2>(ops[st.first_op + k + 1], s_k[(k + 1) & 1]);
+        apply_op<WIDE>(sm, st.nq, ops[st.first_op + k], s_k[k & 1]);
+        if (k + 1 < st.nops) load_consts<T2>(ops[st.first_op + k + 1], consts, s_k[(k + 1) & 1]);
         __syncthreads();
       }
       for (uint32_t i = threadIdx.x; i < dim; i += blockDim.x) g[i] = SM::out(sm[i]);
@@ -422,11 +485,11 @@ __global__ void __launch_bounds__(512, sizeof(T2) == 8 ? 2 : 1)
     for (int sg = st.first_seg; sg < st.first_seg + st.nsegs; ++sg) {
       const BatchSeg S = segs[sg];
       if (S.L == 0) {
-        load_consts<T2>(ops[S.first_op], s_k[0]);
+        load_consts<T2>(ops[S.first_op], consts, s_k[0]);
         __syncthreads();
         for (int k = 0; k < S.nops; ++k) {
-          apply_op(g, st.nq, ops[S.first_op + k], s_k[k & 1]);
-          if (k + 1 < S.nops) load_consts<T2>(ops[S.first_op + k + 1], s_k[(k + 1) & 1]);
+          apply_op<WIDE>(g, st.nq, ops[S.first_op + k], s_k[k & 1]);
+          if (k + 1 < S.nops) load_consts<T2>(ops[S.first_op + k + 1], consts, s_k[(k + 1) & 1]);
           __syncthreads();
         }
         continue;
@@ -459,11 +522,11 @@ __global__ void __launch_bounds__(512, sizeof(T2) == 8 ? 2 : 1)
         }
         for (uint32_t i = threadIdx.x; i < tdim; i += blockDim.x)
           sm[i] = SM::in(g[base | s_tl[i & 127u] | s_th[i >> 7]]);
-        load_consts<T2>(ops[S.first_op], s_k[0]);
+        load_consts<T2>(ops[S.first_op], consts, s_k[0]);
         __syncthreads();
         for (int k = 0; k < S.nops; ++k) {
-          apply_tile_op(sm, L, ops[S.first_op + k], xlat[S.first_op + k], base, s_k[k & 1]);
-          if (k + 1 < S.nops) load_consts<T2>(ops[S.first_op + k + 1], s_k[(k + 1) & 1]);
+          apply_tile_op<WIDE>(sm, L, ops[S.first_op + k], xlat[S.first_op + k], base, s_k[k & 1]);
+          if (k + 1 < S.nops) load_consts<T2>(ops[S.first_op + k + 1], consts, s_k[(k + 1) & 1]);
           __syncthreads();
         }
         for (uint32_t i = threadIdx.x; i < tdim; i += blockDim.x)
@@ -475,22 +538,33 @@ __global__ void __launch_bounds__(512, sizeof(T2) == 8 ? 2 : 1)
 }
 
 cudaError_t batch_set_max_smem(int bytes) {
-  cudaError_t e = cudaFuncSetAttribute(k_batch<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_batch<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  for (const void* f : {(const void*)k_batch<double2, false>, (const void*)k_batch<double2, true>,
+                        (const void*)k_batch<float2, false>, (const void*)k_batch<float2, true>}) {
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // No attribute calls here: this launch is also recorded into a CUDA graph.
 cudaError_t launch_batch(qs_prec prec, void* pool, const BatchState* states, const int* order, int nstates,
-                         const BatchOp* ops, const BatchSeg* segs, const BatchXlat* xlat, int* counter, int threads,
-                         int ctas, int smem_qubits, cudaStream_t st) {
+                         const BatchOp* ops, const double* consts, const BatchSeg* segs, const BatchXlat* xlat,
+                         int* counter, int threads, int ctas, int smem_qubits, int wide, cudaStream_t st) {
   const size_t smem = (smem_qubits >= 0 ? (size_t(1) << smem_qubits) : 0) * (prec == QS_C128 ? 16 : 8);
-  if (prec == QS_C128)
-    k_batch<double2><<<ctas, threads, smem, st>>>(static_cast<double2*>(pool), states, order, nstates, ops, segs,
-                                                  xlat, counter, smem_qubits);
+  double2* p128 = static_cast<double2*>(pool);
+  float2* p64 = static_cast<float2*>(pool);
+  if (prec == QS_C128 && wide)
+    k_batch<double2, true><<<ctas, threads, smem, st>>>(p128, states, order, nstates, ops, consts, segs, xlat, counter,
+                                                        smem_qubits);
+  else if (prec == QS_C128)
+    k_batch<double2, false><<<ctas, threads, smem, st>>>(p128, states, order, nstates, ops, consts, segs, xlat,
+                                                         counter, smem_qubits);
+  else if (wide)
+    k_batch<float2, true><<<ctas, threads, smem, st>>>(p64, states, order, nstates, ops, consts, segs, xlat, counter,
+                                                       smem_qubits);
   else
-    k_batch<float2><<<ctas, threads, smem, st>>>(static_cast<float2*>(pool), states, order, nstates, ops, segs, xlat,
-                                                 counter, smem_qubits);
+    k_batch<float2, false><<<ctas, threads, smem, st>>>(p64, states, order, nstates, ops, consts, segs, xlat, counter,
+                                                        smem_qubits);
   return cudaGetLastError();
 }
 

@@ -158,16 +158,16 @@ struct ComposeBlock {
 // Batched engine (qs_batch_kernels.cu): one operation of a state's program
 // and one state (at most 24 qubits: 32-bit indices).
 struct BatchOp {
-  int kind;              // 0 dense on 1 or 2 targets with controls, 1 diagonal (<= 3 targets), 2 Pauli gadget
+  int kind;              // 0 dense on 1..4 targets with controls, 1 diagonal (<= 3 targets), 2 Pauli gadget
   int n;
-  int t[3];
+  int t[4];
   uint32_t ctrl;         // control mask
   uint32_t xy, yz;       // gadget masks
   int eta, h;            // gadget: number of Y mod 4, highest bit of xy
-  int nins;              // dense: sorted target and control positions
+  int nins;              // dense: sorted target and control positions (at most 7)
   int8_t ins[8];
-  double c, s;           // gadget: cos(phi), sin(phi), phi = -theta/2
-  double m[32];          // dense: 2^n x 2^n row-major; diagonal: 2^n entries (complex128 re, im)
+  uint64_t coff;         // constants in the batch's pool of doubles: dense 2^n x 2^n row-major (re, im),
+                         // diagonal 2^n entries, gadget cos(phi), sin(phi)
 };
 struct BatchState {
   uint64_t offset;       // first amplitude in the pool
@@ -196,7 +196,7 @@ struct BatchXlat {
   uint32_t lxy, lyz, fyz;   // gadget: local flip and phase masks; phase mask outside the tile (global)
   int nlins;                // dense: number of local insertion positions
   int8_t lins[8];           // dense: ascending local positions of targets and in-tile controls
-  int8_t lt[3];             // local target positions (-1: outside the tile, diagonals only)
+  int8_t lt[4];             // local target positions (-1: outside the tile, diagonals only)
   int8_t lh;                // gadget: local position of the highest flip bit
 };
 
@@ -230,8 +230,8 @@ cudaError_t launch_mlp_adam(float* params, const float* grad, float* m, float* v
 int num_sms();  // multiprocessors of the current device (cached)
 cudaError_t batch_set_max_smem(int bytes);
 cudaError_t launch_batch(qs_prec prec, void* pool, const BatchState* states, const int* order, int nstates,
-                         const BatchOp* ops, const BatchSeg* segs, const BatchXlat* xlat, int* counter, int threads,
-                         int ctas, int smem_qubits, cudaStream_t st);
+                         const BatchOp* ops, const double* consts, const BatchSeg* segs, const BatchXlat* xlat,
+                         int* counter, int threads, int ctas, int smem_qubits, int wide, cudaStream_t st);
 cudaError_t launch_group(qs_prec prec, void* amps, int op, const GroupParams& p, cudaStream_t st);
 // complex128 channels in double-float arithmetic: G_DEPOL1, G_DEPOL2, G_DAMP, G_PAULI1 (qs_gates_df.cu)
 cudaError_t launch_group_df(void* amps, int op, const GroupParams& p, cudaStream_t st);

@@ -90,6 +90,14 @@ SIGNATURES = {
                                 ctypes.c_float, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_float)]),
     "qs_circuit_plan_cost": (_I, [_P, _P, _P, _I, _I]),
     "qs_batch_create": (_I, [_I, _IP, _I, _P, ctypes.POINTER(_P)]),
+    "qs_batch_create_mixed": (_I, [_I, _IP, _IP, _I, _P, ctypes.POINTER(_P)]),
+    "qs_batch_add_kraus": (_I, [_P, _I, _IP, _I, _DP, _I]),
+    "qs_batch_add_dephasing": (_I, [_P, _I, _I, _D]),
+    "qs_batch_add_two_qubit_dephasing": (_I, [_P, _I, _I, _I, _D]),
+    "qs_batch_add_depolarising": (_I, [_P, _I, _I, _D]),
+    "qs_batch_add_two_qubit_depolarising": (_I, [_P, _I, _I, _I, _D]),
+    "qs_batch_add_damping": (_I, [_P, _I, _I, _D]),
+    "qs_batch_add_pauli_channel": (_I, [_P, _I, _I, _D, _D, _D]),
     "qs_batch_destroy": (_I, [_P]),
     "qs_batch_pool_amps": (_I, [_P, ctypes.POINTER(_S)]),
     "qs_batch_state_offset": (_I, [_P, _I, ctypes.POINTER(_S)]),
@@ -444,18 +452,22 @@ class Circuit:
 
 
 class Batch:
-    """qs_batch_*: many statevectors with their own circuits in one persistent
-    launch.  The amplitude pool is a torch tensor owned by this object."""
+    """qs_batch_*: many statevectors (or density matrices, density[s] true,
+    held as Choi vectors) with their own circuits in one persistent launch.
+    The amplitude pool is a torch tensor owned by this object."""
 
-    def __init__(self, num_qubits, prec=QS_C64, stream=None, device="cuda"):
+    def __init__(self, num_qubits, prec=QS_C64, stream=None, device="cuda", density=None):
         import torch
         self.num_qubits = [int(q) for q in num_qubits]
+        self.density = [bool(d) for d in density] if density is not None else [False] * len(self.num_qubits)
+        self.storage_qubits = [2 * q if d else q for q, d in zip(self.num_qubits, self.density)]
         self.prec = prec
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         q, nq = _ints(self.num_qubits)
+        dens, _ = _ints([1 if d else 0 for d in self.density])
         self.handle = _P()
-        _check(_lib.qs_batch_create(nq, q, prec, _P(self.stream.cuda_stream), ctypes.byref(self.handle)),
-               "qs_batch_create")
+        _check(_lib.qs_batch_create_mixed(nq, q, dens, prec, _P(self.stream.cuda_stream), ctypes.byref(self.handle)),
+               "qs_batch_create_mixed")
         n = _S()
         _check(_lib.qs_batch_pool_amps(self.handle, ctypes.byref(n)), "qs_batch_pool_amps")
         dtype = torch.complex128 if prec == QS_C128 else torch.complex64
@@ -468,7 +480,7 @@ class Batch:
             self.offsets.append(off.value)
 
     def view(self, s):
-        return self.pool[self.offsets[s]:self.offsets[s] + (1 << self.num_qubits[s])]
+        return self.pool[self.offsets[s]:self.offsets[s] + (1 << self.storage_qubits[s])]
 
     def add(self, s, op):
         kind = op["op"]
@@ -486,8 +498,24 @@ class Batch:
             p, _ = _ints(op["paulis"])
             _check(_lib.qs_batch_add_pauli_gadget(self.handle, s, t, p, nt, float(op["theta"])),
                    "qs_batch_add_pauli_gadget")
+        elif kind == "kraus":
+            t, nt = _ints(op["targs"])
+            k = np.ascontiguousarray(np.asarray(op["kraus"], dtype=np.complex128))
+            keep, kp = _doubles(k)
+            _check(_lib.qs_batch_add_kraus(self.handle, s, t, nt, kp, k.shape[0]), "qs_batch_add_kraus")
+        elif kind in ("dephasing", "depolarising", "damping"):
+            fn = getattr(_lib, "qs_batch_add_" + kind)
+            _check(fn(self.handle, s, int(op["targs"][0]), float(op["p"])), "qs_batch_add_" + kind)
+        elif kind in ("dephasing2", "depolarising2"):
+            fn = getattr(_lib, "qs_batch_add_two_qubit_" + kind[:-1])
+            _check(fn(self.handle, s, int(op["targs"][0]), int(op["targs"][1]), float(op["p"])),
+                   "qs_batch_add_two_qubit_" + kind[:-1])
+        elif kind == "pauli_channel":
+            px, py, pz = (float(x) for x in op["probs"])
+            _check(_lib.qs_batch_add_pauli_channel(self.handle, s, int(op["targs"][0]), px, py, pz),
+                   "qs_batch_add_pauli_channel")
         else:
-            raise ValueError("batched circuits take unitary operations only")
+            raise ValueError("operation kind %r is not supported in batches" % kind)
 
     def compile(self, autotune=True):
         _check(_lib.qs_batch_compile(self.handle, 1 if autotune else 0), "qs_batch_compile")

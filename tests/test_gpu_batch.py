@@ -70,3 +70,49 @@ def test_batch_validation(qs):
         batch.add(1, {"op": "unitary", "ctrls": [], "targs": [5], "mat": np.eye(2)})
     with pytest.raises(qs.QSError):
         batch.add(2, {"op": "unitary", "ctrls": [], "targs": [0], "mat": np.eye(2)})
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_batch_density_matrices(qs, prec):
+    """Density matrices in a batch (Choi vectors of 6 to 16 storage qubits,
+    the largest beyond shared memory) next to statevectors: unitaries with
+    controls, diagonals and gadgets as U on t and U* on t + N, Kraus maps and
+    every channel as superoperator passes, against the oracle."""
+    import torch
+    rng = wl.rng_for("batch-dm-%d" % prec)
+    sizes = [3, 4, 5, 6, 7, 8, 5, 6]
+    dens = [True] * 6 + [False] * 2
+    batch = qs.Batch(sizes, prec=prec, density=dens)
+    circuits, inits = [], []
+    for s, (nq, d) in enumerate(zip(sizes, dens)):
+        if d:
+            ops = wl.small_densmatr_circuit(nq, 30, rng)
+            ops += [{"op": "dephasing", "targs": [nq - 1], "p": 0.06},
+                    {"op": "dephasing2", "targs": [0, nq - 1], "p": 0.05},
+                    {"op": "depolarising2", "targs": [nq - 2, 0], "p": 0.04},
+                    {"op": "pauli_channel", "targs": [1], "probs": (0.03, 0.02, 0.01)},
+                    {"op": "diagonal", "targs": [nq - 1, 0],
+                     "diag": np.exp(1j * rng.uniform(0, 2 * np.pi, 4))}]
+            states, w = wl.random_mixed_state_vectors(nq, 2, rng)
+            init = sum(wi * orc.densmatr_from_pure(v) for wi, v in zip(w, states))
+        else:
+            ops = wl.unitary_circuit(nq, 30, rng)
+            init = wl.random_statevector(nq, rng)
+        for op in ops:
+            batch.add(s, op)
+        circuits.append(ops)
+        inits.append(init)
+    with pytest.raises(qs.QSError):
+        batch.add(6, {"op": "damping", "targs": [0], "p": 0.1})      # a statevector takes no channel
+    batch.compile(autotune=True)
+    dtype = np.complex128 if prec == 1 else np.complex64
+    for s, init in enumerate(inits):
+        batch.view(s).copy_(torch.from_numpy(init.astype(dtype)))
+    batch.run()
+    batch.run()
+    torch.cuda.synchronize()
+    for s, (init, ops, d) in enumerate(zip(inits, circuits, dens)):
+        want = orc.run_ops(orc.run_ops(init, ops, d), ops, d)
+        got = batch.view(s).cpu().numpy().astype(np.complex128)
+        err = float(np.max(np.abs(got - want)))
+        assert err <= (1e-12 if prec == 1 else 2e-5), (s, err)
