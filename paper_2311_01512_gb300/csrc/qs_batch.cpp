@@ -25,6 +25,7 @@
 #include "qs.h"
 #include "qs_handle.h"
 #include "qs_internal.h"
+#include "qs_batch_plan.h"
 
 struct qs_batch {
   qs_prec prec = QS_C64;
@@ -133,16 +134,7 @@ qs_status add_channel1(qs_batch* b, int s, int t, double f0, double f1, double f
   if (check_density(b, s) != QS_OK) return check_density(b, s);
   qs_status st = qsapi::check_qubits(b->nlog[s], &t, 1, nullptr, 0);
   if (st != QS_OK) return st;
-  std::vector<double> S(16, 0.0);
-  S[0 * 4 + 0] = f0;  // 00
-  S[0 * 4 + 3] = f1;
-  S[3 * 4 + 3] = f0;  // 11
-  S[3 * 4 + 0] = f1;
-  S[1 * 4 + 1] = f2;  // 01 (bit t set)
-  S[1 * 4 + 2] = f3;
-  S[2 * 4 + 2] = f2;  // 10
-  S[2 * 4 + 1] = f3;
-  return add_superop(b, s, {t}, S);
+  return add_superop(b, s, {t}, qsbatch::channel1_superop(f0, f1, f2, f3));
 }
 
 int smem_qubits_for(qs_prec prec, int ctas_per_sm) {
@@ -171,122 +163,12 @@ struct Plan {
   }
 };
 
-int popc32(uint32_t x) {
-  int n = 0;
-  for (; x; x &= x - 1) ++n;
-  return n;
-}
-
-// qubits an operation pairs amplitudes across
-uint32_t pairing_mask(const qsk::BatchOp& op) {
-  if (op.kind == 0) {
-    uint32_t m = 0;
-    for (int q = 0; q < op.n; ++q) m |= 1u << op.t[q];
-    return m;
-  }
-  return op.kind == 2 ? op.xy : 0u;
-}
-
-// position of qubit t among the tile qubits, -1 if it is not one
-int local_pos(uint32_t qmask, int t) {
-  return ((qmask >> t) & 1u) ? popc32(qmask & ((1u << t) - 1u)) : -1;
-}
-
-qsk::BatchXlat translate(const qsk::BatchOp& op, uint32_t qmask) {
-  qsk::BatchXlat x{};
-  for (int q = 0; q < 4; ++q) x.lt[q] = -1;
-  if (op.kind == 0) {
-    std::vector<int> lins;
-    for (int q = 0; q < op.n; ++q) {
-      x.lt[q] = (int8_t)local_pos(qmask, op.t[q]);
-      lins.push_back(x.lt[q]);
-    }
-    for (int c = 0; c < 32; ++c) {
-      if (!((op.ctrl >> c) & 1u)) continue;
-      const int p = local_pos(qmask, c);
-      if (p >= 0) {
-        x.lctrl |= 1u << p;
-        lins.push_back(p);
-      } else {
-        x.fctrl |= 1u << c;
-      }
-    }
-    std::sort(lins.begin(), lins.end());
-    x.nlins = (int)lins.size();
-    for (int i = 0; i < x.nlins; ++i) x.lins[i] = (int8_t)lins[i];
-  } else if (op.kind == 1) {
-    for (int q = 0; q < op.n; ++q) x.lt[q] = (int8_t)local_pos(qmask, op.t[q]);
-  } else {
-    for (int b = 0; b < 32; ++b) {
-      const int p = local_pos(qmask, b);
-      if ((op.xy >> b) & 1u) x.lxy |= 1u << p;       // every flip qubit is a tile qubit
-      if ((op.yz >> b) & 1u) {
-        if (p >= 0)
-          x.lyz |= 1u << p;
-        else
-          x.fyz |= 1u << b;
-      }
-    }
-    x.lh = (int8_t)(op.xy ? local_pos(qmask, op.h) : 0);
-  }
-  return x;
-}
-
-// Segments of every state larger than 2^L amplitudes.  Greedy: an operation
-// joins the open segment while the union of pairing qubits and the five
-// lowest qubits stays within L; an operation that alone exceeds it runs in
-// global memory.  The tile qubits are that union, filled up with the lowest
-// remaining qubits.
+// Segments of every state larger than 2^L amplitudes (qs_batch_plan.h).
 void build_plan(Plan& P, int L, const std::vector<int>& nq, const std::vector<qsk::BatchState>& base,
                 const std::vector<qsk::BatchOp>& ops) {
   P.L = L;
   P.states = base;
-  P.segs.clear();
-  P.xlat.assign(ops.size(), qsk::BatchXlat{});
-  for (size_t s = 0; s < base.size(); ++s) {
-    qsk::BatchState& st = P.states[s];
-    st.first_seg = (int)P.segs.size();
-    st.nsegs = 0;
-    if (nq[s] <= L) continue;
-    const uint32_t low = (1u << std::min(5, nq[s])) - 1u;
-    auto emit = [&](int first, int n, uint32_t U, bool tiled) {
-      qsk::BatchSeg g{};
-      g.first_op = first;
-      g.nops = n;
-      g.L = tiled ? L : 0;
-      if (tiled) {
-        uint32_t Q = low | U;
-        for (int b = 0; popc32(Q) < L; ++b) Q |= 1u << b;
-        for (int b = 0, i = 0; b < 32; ++b)
-          if ((Q >> b) & 1u) g.q[i++] = (int8_t)b;
-        for (int k = first; k < first + n; ++k) P.xlat[k] = translate(ops[k], Q);
-      }
-      P.segs.push_back(g);
-    };
-    int k0 = st.first_op, cnt = 0;
-    uint32_t U = 0;
-    for (int k = st.first_op; k < st.first_op + st.nops; ++k) {
-      const uint32_t pm = pairing_mask(ops[k]);
-      if (popc32(low | pm) > L) {
-        if (cnt) emit(k0, cnt, U, true);
-        emit(k, 1, 0u, false);
-        k0 = k + 1;
-        cnt = 0;
-        U = 0;
-        continue;
-      }
-      if (popc32(low | U | pm) > L) {
-        emit(k0, cnt, U, true);
-        k0 = k;
-        cnt = 0;
-        U = 0;
-      }
-      U |= pm;
-      ++cnt;
-    }
-    if (cnt) emit(k0, cnt, U, true);
-    st.nsegs = (int)P.segs.size() - st.first_seg;
-  }
+  qsbatch::build_segments(L, nq, P.states, ops, P.segs, P.xlat);
 }
 
 bool upload_plan(Plan& P) {
@@ -313,19 +195,7 @@ qs_status add_channel2(qs_batch* b, int state, int t1, int t2, bool depol, doubl
   const int tt[2] = {t1, t2};
   qs_status st = qsapi::check_qubits(b->nlog[state], tt, 2, nullptr, 0);
   if (st != QS_OK) return st;
-  std::vector<double> S(256, 0.0);
-  for (int m = 0; m < 16; ++m) {
-    const bool same1 = ((m >> 0) & 1) == ((m >> 2) & 1), same2 = ((m >> 1) & 1) == ((m >> 3) & 1);
-    if (!depol) {
-      S[m * 16 + m] = (same1 && same2) ? 1.0 : 1.0 - 4.0 * p / 3.0;
-    } else if (same1 && same2) {
-      S[m * 16 + m] = 1.0 - 4.0 * p / 5.0;
-      for (int f : {0x5, 0xA, 0xF}) S[m * 16 + (m ^ f)] = 4.0 * p / 15.0;   // flip t1 pair, t2 pair, both
-    } else {
-      S[m * 16 + m] = 1.0 - 16.0 * p / 15.0;
-    }
-  }
-  return add_superop(b, state, {t1, t2}, S);
+  return add_superop(b, state, {t1, t2}, qsbatch::channel2_superop(depol, p));
 }
 
 }  // namespace
@@ -468,23 +338,7 @@ qs_status qs_batch_add_kraus(qs_batch* b, int state, const int* targs, int n, co
   if (n > 2) return QS_ERR_TOO_MANY_TARGETS;
   qs_status st = qsapi::check_qubits(b->nlog[state], targs, n, nullptr, 0);
   if (st != QS_OK) return st;
-  // S = sum_m conj(K_m) (x) K_m: K on the ket bits t (low n bits of the member
-  // index), conj(K) on the bra bits t + N (Sec. "Kraus map")
-  const int d = 1 << n, dd = d * d;
-  std::vector<double> m((size_t)2 * dd * dd, 0.0);
-  for (int k = 0; k < num_ops; ++k) {
-    const double* K = kraus + (size_t)2 * d * d * k;
-    for (int ih = 0; ih < d; ++ih)
-      for (int il = 0; il < d; ++il)
-        for (int jh = 0; jh < d; ++jh)
-          for (int jl = 0; jl < d; ++jl) {
-            const double ar = K[2 * (ih * d + jh)], ai = -K[2 * (ih * d + jh) + 1];   // conj(K[ih][jh])
-            const double br = K[2 * (il * d + jl)], bi = K[2 * (il * d + jl) + 1];
-            const size_t e = (size_t)(ih * d + il) * dd + (jh * d + jl);
-            m[2 * e] += ar * br - ai * bi;
-            m[2 * e + 1] += ar * bi + ai * br;
-          }
-  }
+  const std::vector<double> m = qsbatch::kraus_superop(n, kraus, num_ops);
   std::vector<int> t(targs, targs + n);
   for (int q = 0; q < n; ++q) t.push_back(targs[q] + b->nlog[state]);
   return add_dense(b, state, {}, t, m.data());
@@ -512,13 +366,7 @@ qs_status qs_batch_add_damping(qs_batch* b, int state, int t, double p) {
   if (check_density(b, state) != QS_OK) return check_density(b, state);
   qs_status st = qsapi::check_qubits(b->nlog[state], &t, 1, nullptr, 0);
   if (st != QS_OK) return st;
-  std::vector<double> S(16, 0.0);
-  S[0 * 4 + 0] = 1.0;             // 00 -> 00 + p 11
-  S[0 * 4 + 3] = p;
-  S[1 * 4 + 1] = std::sqrt(1.0 - p);
-  S[2 * 4 + 2] = std::sqrt(1.0 - p);
-  S[3 * 4 + 3] = 1.0 - p;
-  return add_superop(b, state, {t}, S);
+  return add_superop(b, state, {t}, qsbatch::damping_superop(p));
 }
 
 qs_status qs_batch_add_two_qubit_dephasing(qs_batch* b, int state, int t1, int t2, double p) {
