@@ -116,3 +116,39 @@ def test_batch_density_matrices(qs, prec):
         got = batch.view(s).cpu().numpy().astype(np.complex128)
         err = float(np.max(np.abs(got - want)))
         assert err <= (1e-12 if prec == 1 else 2e-5), (s, err)
+
+
+def test_batch_edge_cases(qs):
+    """States with no operations (left unchanged, in shared memory and tiled),
+    one-qubit states, and a one-state batch."""
+    import torch
+    rng = wl.rng_for("batch-edge")
+    sizes = [1, 2, 11, 15, 15]
+    nops = [3, 0, 5, 0, 12]
+    batch = qs.Batch(sizes, prec=1)
+    circuits = []
+    for s, (nq, k) in enumerate(zip(sizes, nops)):
+        ops = wl.unitary_circuit(nq, k, rng) if k else []
+        for op in ops:
+            batch.add(s, op)
+        circuits.append(ops)
+    batch.compile(autotune=False)
+    inits = [wl.random_statevector(nq, rng) for nq in sizes]
+    for s, psi in enumerate(inits):
+        batch.view(s).copy_(torch.from_numpy(psi))
+    batch.run()
+    torch.cuda.synchronize()
+    for s, (psi, ops) in enumerate(zip(inits, circuits)):
+        got = batch.view(s).cpu().numpy()
+        want = orc.run_ops(psi, ops, False) if ops else psi
+        assert float(np.max(np.abs(got - want))) <= 1e-13, s
+    one = qs.Batch([3], prec=0)
+    op = {"op": "unitary", "ctrls": [2], "targs": [0, 1], "mat": wl.haar_unitary(4, rng)}
+    one.add(0, op)
+    one.compile(autotune=True)
+    psi = wl.random_statevector(3, rng)
+    one.view(0).copy_(torch.from_numpy(psi.astype(np.complex64)))
+    one.run()
+    torch.cuda.synchronize()
+    want = orc.run_ops(psi, [op], False)
+    assert float(np.max(np.abs(one.view(0).cpu().numpy() - want))) <= 1e-6
