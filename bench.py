@@ -32,6 +32,15 @@ NUM_OPS = 500
 CIRCUIT_TAG = "sv30-circuit"
 STATE_SEED = 2311015121
 CPU_SAMPLE_QUBITS = 26
+ARITH_CODE = {"fx": 2, "df": 0, "f64": 1}     # qs_arith
+DTYPE = {
+    "fx": ("c128 storage; arithmetic at least FP64: one-target gates, diagonals and gadgets in 60-bit block "
+           "fixed point with exact integer products and one rounding per output (error <= 2^-53 |y| + "
+           "2^-55 max|x| max|m|), 2-5-target gates as eight exact 7-bit slices (56-bit operands) on the "
+           "bf16 tensor cores"),
+    "df": "c128 storage, double-float (2xf32, 47-bit) arithmetic",
+    "f64": "c128 storage, native f64 arithmetic",
+}
 
 
 def parse_args(argv=None):
@@ -43,8 +52,10 @@ def parse_args(argv=None):
     ap.add_argument("--qubits", type=int, default=30, help="statevector size (the workload is 30)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--arith", choices=["df", "f64"], default="df",
-                    help="complex128 arithmetic: double-float on the FP32 pipes (default) or native FP64")
+    ap.add_argument("--arith", choices=["fx", "df", "f64"], default="fx",
+                    help="complex128 arithmetic: block fixed point with exact integer products and one "
+                         "rounding, at least the 53 bits of FP64 (default); double-float on the FP32 pipes "
+                         "(47-bit); or native FP64")
     ap.add_argument("--f64-share", type=int, default=0,
                     help="sixteenths of one-target-gate work done in native FP64 beside double-float")
     ap.add_argument("--no-fused", action="store_true", help="skip the fused tensor-core comparison")
@@ -284,7 +295,7 @@ def main_ours(args):
     stream.synchronize()
     st = qs.State(nq, density=False, prec=qs.QS_C128, stream=stream, storage=psi)
     h = st.handle
-    qs.qs_set_arithmetic(h, qs.QS_ARITH_DF if args.arith == "df" else qs.QS_ARITH_F64, args.f64_share)
+    qs.qs_set_arithmetic(h, ARITH_CODE[args.arith], args.f64_share)
     fams = [op_family(op) for op in ops]
     nbytes = [op_bytes(op, nq, 16) for op in ops]
 
@@ -355,7 +366,7 @@ def main_ours(args):
         stream2 = torch.cuda.Stream(device=device)
         psi2 = torch.empty_like(psi)
         st2 = qs.State(nq, density=False, prec=qs.QS_C128, stream=stream2, storage=psi2)
-        qs.qs_set_arithmetic(st2.handle, qs.QS_ARITH_DF if args.arith == "df" else qs.QS_ARITH_F64, args.f64_share)
+        qs.qs_set_arithmetic(st2.handle, ARITH_CODE[args.arith], args.f64_share)
         H, S = [h, st2.handle], [stream, stream2]
         h2d = 16 * (1 << nq) + sum(op_h2d_bytes(op) for op in ops)
         for j in range(2):                         # untimed warm-up step on each state
@@ -418,8 +429,7 @@ def main_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": ("c128 storage, double-float (2xf32, 47-bit) arithmetic" if args.arith == "df"
-                      else "c128 storage, f64 arithmetic"),
+            "dtype": DTYPE[args.arith],
             "data": "synthetic", "config": config_dict(nq, args),
             "hbm_gbs": step_bytes / (ms_per_step * 1e-3) / 1e9,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,

@@ -70,15 +70,31 @@ typedef enum {
 
 typedef enum { QS_C64 = 0, QS_C128 = 1 } qs_prec;
 
-/* Arithmetic of complex128 gate kernels.  GB300 executes FP64 FMA about 58
- * times slower than FP32 FMA, so by default complex128 amplitudes are split
- * into pairs of floats (integer bit operations, 47-bit significand) and
- * combined with error-free FP32 transformations; the result is stored back as
- * IEEE complex128.  Relative error per operation: a few units of 2^-46 for
- * amplitudes of modulus in [2^-80, 2^128) (absolute error below 2^-103 for
- * smaller ones).  QS_ARITH_F64 uses native FP64 throughout.  complex64 states
- * ignore the setting. */
-typedef enum { QS_ARITH_DF = 0, QS_ARITH_F64 = 1 } qs_arith;
+/* Arithmetic of complex128 kernels.  GB300 executes FP64 FMA about 70 times
+ * slower than FP32 FMA, so a plain FP64 gate is bound by the FP64 pipe, not by
+ * memory.  Amplitudes are always stored as IEEE complex128.
+ *
+ * QS_ARITH_FX (default): at least the 53 bits of IEEE double.
+ *   - One-target gates, diagonals, Pauli and phase gadgets, and the channels
+ *     that mix amplitudes (depolarising, damping, Pauli channel) use block
+ *     fixed point.  The doubles that one output combines share an exponent and
+ *     become 60-bit integers.  Products and sums are exact, on 32-bit integer
+ *     multiply-adds, and each output is rounded once.  Error of an output
+ *     y = sum_k x_k m_k: at most 2^-53 |y| + 2^-55 max|x_k| max|m_k|.
+ *     Inputs must be finite; subnormals count as zero.
+ *   - Dense gates with 2..5 targets run on the bf16 tensor cores with eight
+ *     exact 7-bit integer slices of 56-bit operands (rows and columns scaled
+ *     by their largest exponent), exact FP32 level sums, one rounding.
+ *   - Everything else (6-target dense gates, dephasing, superoperators,
+ *     norm, trace, expectation values, partial traces) is native FP64.
+ * QS_ARITH_DF: double-float.  Amplitudes are split into float pairs (47-bit
+ *   significands) and combined with error-free FP32 transformations; dense
+ *   gates use seven 7-bit slices (49 bits).  Relative error per operation: a
+ *   few units of 2^-46 for moduli in [2^-80, 2^128).  Somewhat faster than FX
+ *   on dense gates, but narrower than IEEE double.
+ * QS_ARITH_F64: native FP64 throughout (FP64-pipe bound on GB300).
+ * complex64 states ignore the setting. */
+typedef enum { QS_ARITH_DF = 0, QS_ARITH_F64 = 1, QS_ARITH_FX = 2 } qs_arith;
 
 /* Largest number of storage qubits (N for a statevector, 2N for a density
  * matrix): 2^34 complex64 amplitudes are 128 GiB. */
@@ -109,7 +125,7 @@ qs_status qs_destroy(qs_state* state);
 qs_status qs_get_info(const qs_state* state, int* num_qubits, int* storage_qubits, int* is_density,
                       int* prec);
 
-/* Select the complex128 arithmetic of this handle (default QS_ARITH_DF).
+/* Select the complex128 arithmetic of this handle (default QS_ARITH_FX).
  * f64_share_16ths (0..16): with QS_ARITH_DF, the share of one-target-gate
  * work, in sixteenths, done in native FP64 at the same time (the FP64 pipe is
  * otherwise idle); 0 = none. */
@@ -237,7 +253,7 @@ qs_status qs_expec_pauli_sum(const qs_state* state, const int* paulis, const dou
  * at most max_block_qubits (<= QS_MAX_DENSE_TARGETS) qubits.  Each block of
  * two or more gates is composed on the device into one dense matrix in FP64
  * and applied as a single dense gate (tensor cores for complex64 blocks of
- * 3..5 qubits, double-float arithmetic for complex128); a one-gate block
+ * 3..5 qubits, the handle's complex128 arithmetic otherwise); a one-gate block
  * runs that gate's own kernel.  Not in the paper: this groups the paper's
  * many-target gate updates (Sec. "Many-target gate") so that each pass over
  * the state does more work.  The applied operation is the same up to rounding.
@@ -399,7 +415,8 @@ qs_status qs_batch_info(const qs_batch* batch, int* threads, int* ctas, int* sme
  * looks up that array's device address, so make the first call on each device
  * before capturing any stream.  All calls share the array: calls that overlap
  * on the GPU (other streams, other host threads) race and must be serialised
- * by the caller.  Synchronises cuda_stream. */
+ * by the caller.  complex128 products and sums are native FP64, as with the
+ * default arithmetic of a handle.  Synchronises cuda_stream. */
 qs_status qs_expec_pauli_sum_noalloc(const void* d_amps, int num_qubits, int is_density, qs_prec prec,
                                      const int* paulis, const double* coeffs, int num_terms,
                                      void* cuda_stream, double* out);

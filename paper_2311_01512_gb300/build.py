@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(PKG, "libqsim.so")
 
-SOURCES = ["qs_gates.cu", "qs_gates_df.cu", "qs_tc.cu", "qs_tc_ozaki.cu", "qs_density.cu", "qs_reduce.cu", "qs_api.cpp", "qs_noalloc.cu", "qs_fuse.cu", "qs_circuit.cpp", "qs_mlp.cu", "qs_costmodel.cpp", "qs_batch_kernels.cu", "qs_batch.cpp"]
+SOURCES = ["qs_gates.cu", "qs_gates_df.cu", "qs_gates_fx.cu", "qs_tc.cu", "qs_tc_ozaki.cu", "qs_density.cu", "qs_reduce.cu", "qs_api.cpp", "qs_noalloc.cu", "qs_fuse.cu", "qs_circuit.cpp", "qs_mlp.cu", "qs_costmodel.cpp", "qs_batch_kernels.cu", "qs_batch.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -13,6 +13,7 @@
 
 #include "qs.h"
 #include "qs_df.cuh"
+#include "qs_fx.cuh"
 #include "qs_internal.h"
 
 using qsk::kMaxQ;
@@ -195,6 +196,19 @@ qs_status check_qubits(int nq, const int* targs, int ntarg, const int* ctrls, in
 
 qs_status check_prob(double p) { return (p >= 0.0 && p <= 1.0) ? QS_OK : QS_ERR_ARG; }
 
+// Block fixed-point constants (qs_fx.cuh): the largest biased exponent of a
+// row group, and one constant's 60-bit parts in that group.
+int fx_em(std::initializer_list<double> v) {
+  int e = 0;
+  for (double x : v) e = std::max(e, qsfx::expo_of(x));
+  return e;
+}
+qsk::FxPart fx_part(double v, int em) {
+  const qsfx::Part q = qsfx::fixed_const(v, em);
+  return qsk::FxPart{q.h, q.l};
+}
+bool is_fx(const qs_state* s) { return s->prec == QS_C128 && s->arith == QS_ARITH_FX; }
+
 // One dense or one-target gate pass on storage positions (already shifted).
 qs_status gate_pass(qs_state* s, const std::vector<int>& ctrls, const std::vector<int>& targs, const double* host_mat,
                     const void* dev_mat, int conj, bool force_dense) {
@@ -202,6 +216,27 @@ qs_status gate_pass(qs_state* s, const std::vector<int>& ctrls, const std::vecto
   uint64_t cmask = 0;
   for (int c : ctrls) cmask |= 1ull << c;
   const bool df = s->prec == QS_C128 && s->arith == QS_ARITH_DF;
+  if (n == 1 && is_fx(s) && !force_dense) {
+    // rows (out0.re, out0.im, out1.re, out1.im) over (a.re, a.im, b.re, b.im)
+    double m[8];
+    for (int e = 0; e < 8; ++e) m[e] = (conj && (e & 1)) ? -host_mat[e] : host_mat[e];
+    const double rows[4][4] = {{m[0], -m[1], m[2], -m[3]}, {m[1], m[0], m[3], m[2]},
+                               {m[4], -m[5], m[6], -m[7]}, {m[5], m[4], m[7], m[6]}};
+    qsk::Gate1FxParams p{};
+    p.em[0] = fx_em({m[0], m[1], m[2], m[3]});
+    p.em[1] = fx_em({m[4], m[5], m[6], m[7]});
+    for (int r = 0; r < 4; ++r)
+      for (int c = 0; c < 4; ++c) p.m[r][c] = fx_part(rows[r][c], p.em[r >> 1]);
+    std::vector<int> ins(ctrls);
+    ins.push_back(targs[0]);
+    std::sort(ins.begin(), ins.end());
+    p.nins = (int)ins.size();
+    for (int i = 0; i < p.nins; ++i) p.ins[i] = (int8_t)ins[i];
+    p.t = targs[0];
+    p.ctrl_mask = cmask;
+    p.npairs = 1ull << (s->ns - p.nins);
+    return cuda_status(qsk::launch_gate1_fx(s->amps, p, s->stream));
+  }
   if (n == 1 && df && !force_dense) {
     qsk::Gate1DfParams p{};
     for (int e = 0; e < 8; ++e) {
@@ -246,7 +281,10 @@ qs_status gate_pass(qs_state* s, const std::vector<int>& ctrls, const std::vecto
   // on the lowest free qubit
   const bool tc_n = n <= 5 && (n >= 3 || (n == 2 && nfree >= 1));
   const bool tc64 = s->prec == QS_C64 && s->tensor_cores && (tc_n || n == 6);   // 6: bf16x3 slices
-  const bool tc128 = s->prec == QS_C128 && s->arith == QS_ARITH_DF && s->tensor_cores && tc_n;
+  // complex128: seven integer slices (49 bits) with double-float arithmetic,
+  // eight (56 bits) with block fixed point
+  const bool tc128 = s->prec == QS_C128 && (s->arith == QS_ARITH_DF || s->arith == QS_ARITH_FX) &&
+                     s->tensor_cores && tc_n;
   if (tc64 || tc128) {
     std::vector<int> kt(targs);
     if (n == 2) {
@@ -286,7 +324,7 @@ qs_status gate_pass(qs_state* s, const std::vector<int>& ctrls, const std::vecto
     for (int i = 0; i < p.nhi; ++i) p.hi_ins[i] = (int8_t)hi[i];
     p.ntiles = 1ull << (s->ns - p.nhi);
     return cuda_status(tc64 ? qsk::launch_dense_tc(s->amps, p, s->stream)
-                            : qsk::launch_dense_ozaki(s->amps, p, s->stream));
+                            : qsk::launch_dense_ozaki(s->amps, p, s->arith == QS_ARITH_FX ? 8 : 7, s->stream));
   }
   // Dense tile: P = targets u the lowest free qubits, |P| = min(kTileBits, free + n).
   const int g = std::min(qsk::kTileBits - n, nfree) < 0 ? 0 : std::min(qsk::kTileBits - n, nfree);
@@ -335,6 +373,19 @@ qs_status gadget_pass(qs_state* s, const std::vector<int>& targs, const int* pau
   } else {
     p.h = 0;
     p.nwork = 1ull << s->ns;
+  }
+  if (is_fx(s)) {
+    qsk::GadgetFxParams q{};
+    q.xy = p.xy;
+    q.yz = p.yz;
+    q.nwork = p.nwork;
+    q.em = fx_em({p.c, p.s});
+    q.c = fx_part(p.c, q.em);
+    q.s = fx_part(p.s, q.em);
+    q.ns = fx_part(-p.s, q.em);
+    q.eta = p.eta;
+    q.h = p.h;
+    return cuda_status(qsk::launch_gadget_fx(s->amps, q, s->stream));
   }
   if (s->prec == QS_C128 && s->arith == QS_ARITH_DF) {
     qsk::GadgetDfParams q{};
@@ -415,7 +466,7 @@ qs_status qs_get_info(const qs_state* s, int* num_qubits, int* storage_qubits, i
 }
 
 qs_status qs_set_arithmetic(qs_state* s, qs_arith arith, int f64_share_16ths) {
-  if (!s || (arith != QS_ARITH_DF && arith != QS_ARITH_F64)) return QS_ERR_ARG;
+  if (!s || (arith != QS_ARITH_DF && arith != QS_ARITH_F64 && arith != QS_ARITH_FX)) return QS_ERR_ARG;
   if (f64_share_16ths < 0 || f64_share_16ths > 16) return QS_ERR_ARG;
   s->arith = arith;
   s->f64_share = f64_share_16ths;
@@ -466,7 +517,7 @@ qs_status qs_init_pure_densmatr(qs_state* rho, const qs_state* psi, double weigh
   if (!rho->is_density) return QS_ERR_NOT_DENSMATR;
   if (psi->is_density || psi->nq != rho->nq || psi->prec != rho->prec) return QS_ERR_ARG;
   return cuda_status(qsk::launch_dm_from_pure(rho->prec, rho->amps, psi->amps, rho->nq, weight, accumulate ? 1 : 0,
-                                              rho->stream));
+                                              rho->stream, rho->arith != QS_ARITH_DF));
 }
 
 qs_status qs_apply_ctrl_multi_target(qs_state* s, const int* ctrls, int nctrl, const int* targs, int ntarg,
@@ -488,7 +539,7 @@ qs_status qs_apply_ctrl_multi_target(qs_state* s, const int* ctrls, int nctrl, c
   // U on t and U^* on t + N in one 4-target pass of conj(U) (x) U, the
   // superoperator of the one-operator Kraus map {U} (Sec. "Kraus map"), which
   // reads and writes the Choi vector once instead of twice.
-  const bool tc = s->tensor_cores && (s->prec == QS_C64 || s->arith == QS_ARITH_DF);
+  const bool tc = s->tensor_cores && (s->prec == QS_C64 || s->arith == QS_ARITH_DF || s->arith == QS_ARITH_FX);
   if (s->is_density && nctrl == 0 && ntarg == 2 && tc) {
     void* dsup = nullptr;
     int slot_s = -1;
@@ -569,7 +620,24 @@ qs_status qs_apply_diagonal(qs_state* s, const int* targs, int ntarg, const doub
   }
   for (int q = 0; q < ntarg; ++q) p.tpos[q] = (int8_t)targs[q];
   const bool df = s->prec == QS_C128 && s->arith == QS_ARITH_DF;
-  auto launch = [&]() { return df ? qsk::launch_diag_df(s->amps, p, s->stream) : qsk::launch_diag(s->prec, s->amps, p, s->stream); };
+  auto launch = [&]() {
+    if (is_fx(s)) {
+      qsk::DiagFxParams q{};
+      q.n = p.n;
+      q.namps = p.namps;
+      for (int k = 0; k < p.n; ++k) q.tpos[k] = p.tpos[k];
+      for (int j = 0; j < (1 << p.n); ++j) {
+        const double re = p.d[2 * j], im = p.d[2 * j + 1];
+        qsk::DiagFxEntry& e = q.e[j];
+        e.em = fx_em({re, im});
+        e.re = fx_part(re, e.em);
+        e.im = fx_part(im, e.em);
+        e.nim = fx_part(-im, e.em);
+      }
+      return qsk::launch_diag_fx(s->amps, q, s->stream);
+    }
+    return df ? qsk::launch_diag_df(s->amps, p, s->stream) : qsk::launch_diag(s->prec, s->amps, p, s->stream);
+  };
   st = cuda_status(launch());
   if (st == QS_OK && s->is_density) {
     for (int j = 0; j < (1 << ntarg); ++j) p.d[2 * j + 1] = -diag[2 * j + 1];
@@ -655,6 +723,36 @@ qs_status group_channel(qs_state* s, int op, int t1, int t2, const double* f) {
   // bound by the FP64 pipe, not by memory); dephasing stays on FP64
   if (s->prec == QS_C128 && s->arith == QS_ARITH_DF && op != qsk::G_DEPHASE1 && op != qsk::G_DEPHASE2)
     return cuda_status(qsk::launch_group_df(s->amps, op, p, s->stream));
+  // block fixed point: coefficient slots as stated at k_group_fx (coefficients
+  // that one output combines share an exponent)
+  if (is_fx(s) && op != qsk::G_DEPHASE1 && op != qsk::G_DEPHASE2) {
+    qsk::GroupFxParams q{};
+    q.ngroups = p.ngroups;
+    q.nbits = p.nbits;
+    for (int b = 0; b < 4; ++b) {
+      q.ins[b] = p.ins[b];
+      q.mpos[b] = p.mpos[b];
+    }
+    double c[4] = {p.f[0], p.f[1], p.f[2], p.f[3]};
+    int em[4];
+    if (op == qsk::G_DAMP) {
+      c[0] = 1.0;
+      c[1] = p.f[1];
+      c[2] = p.f[2];
+      c[3] = p.f[0];
+      em[0] = em[1] = fx_em({c[0], c[1]});
+      em[2] = fx_em({c[2]});
+      em[3] = fx_em({c[3]});
+    } else {
+      em[0] = em[1] = fx_em({c[0], c[1]});
+      em[2] = em[3] = op == qsk::G_PAULI1 ? fx_em({c[2], c[3]}) : fx_em({c[2]});
+    }
+    for (int k = 0; k < 4; ++k) {
+      q.em[k] = em[k];
+      q.cf[k] = fx_part(c[k], em[k]);
+    }
+    return cuda_status(qsk::launch_group_fx(s->amps, op, q, s->stream));
+  }
   return cuda_status(qsk::launch_group(s->prec, s->amps, op, p, s->stream));
 }
 
@@ -773,9 +871,10 @@ qs_status qs_expec_pauli_sum(const qs_state* cs, const int* paulis, const double
     if (s->is_density)
       e = qsk::launch_expec_dm(s->prec, s->amps, s->nq, dt, cnt, s->d_partials, s->stream);
     else if (first < ndiag)
-      e = qsk::launch_expec_sv_diag(s->prec, s->amps, s->nq, dt, cnt, s->d_partials, s->stream);
+      e = qsk::launch_expec_sv_diag(s->prec, s->amps, s->nq, dt, cnt, s->d_partials, s->stream,
+                                       s->arith != QS_ARITH_DF);
     else
-      e = qsk::launch_expec_sv(s->prec, s->amps, s->nq, dt, cnt, s->d_partials, s->stream);
+      e = qsk::launch_expec_sv(s->prec, s->amps, s->nq, dt, cnt, s->d_partials, s->stream, s->arith != QS_ARITH_DF);
     if (e == cudaSuccess) e = qsk::launch_reduce_final(s->d_partials, s->d_result, first > 0, s->stream);
     first += cnt;
     st = ring_done(s, slot);
@@ -790,7 +889,8 @@ qs_status qs_calc_norm_or_trace(const qs_state* cs, double* out) {
   qs_state* s = const_cast<qs_state*>(cs);
   if (!s || !out) return QS_ERR_ARG;
   cudaError_t e = s->is_density ? qsk::launch_trace(s->prec, s->amps, s->nq, s->d_partials, s->stream)
-                                : qsk::launch_norm(s->prec, s->amps, s->ns, s->d_partials, s->stream);
+                                : qsk::launch_norm(s->prec, s->amps, s->ns, s->d_partials, s->stream,
+                                                   s->arith != QS_ARITH_DF);
   if (e == cudaSuccess)
     e = qsk::launch_reduce_final(s->d_partials, s->d_result, 0, s->stream,
                                  s->is_density ? qsk::kReduceBlocks : qsk::kNormBlocks);

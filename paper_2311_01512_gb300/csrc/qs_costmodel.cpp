@@ -137,10 +137,11 @@ qs_status qs_costmodel_encode(int kind, int width, unsigned long long qmask, int
   out[47] = (float)s->ns / 34.0f;
   out[48] = s->prec == QS_C128 ? 1.0f : 0.0f;
   out[49] = s->is_density ? 1.0f : 0.0f;
-  out[50] = (s->prec == QS_C128 && s->arith == QS_ARITH_DF) ? 1.0f : 0.0f;
+  // complex128 off the FP64 pipe (double-float or block fixed point)
+  out[50] = (s->prec == QS_C128 && s->arith != QS_ARITH_F64) ? 1.0f : 0.0f;
   // dense launches that run on the tensor-core kernels (complex64: 2..6 targets;
-  // complex128 with double-float: 2..5)
-  const bool tc_prec = s->prec == QS_C64 || s->arith == QS_ARITH_DF;
+  // complex128 with double-float or block fixed point: 2..5)
+  const bool tc_prec = s->prec == QS_C64 || s->arith != QS_ARITH_F64;
   const int tc_max = s->prec == QS_C64 ? 6 : 5;
   out[51] = (tc_prec && s->tensor_cores && (kind == QS_COST_FUSED_DENSE || kind == QS_COST_DENSE) && width >= 2 &&
              width <= tc_max)

@@ -249,9 +249,12 @@ cudaError_t launch_superop(const double* kraus, int num_ops, int n, double* sup,
 }
 
 cudaError_t launch_dm_from_pure(qs_prec prec, void* rho, const void* psi, int nq, double weight,
-                                int accumulate, cudaStream_t st) {
+                                int accumulate, cudaStream_t st, bool f64) {
   const unsigned g = grid_for(1ull << (2 * nq), 256, num_sms() * kStreamBlocksPerSM);
-  if (prec == QS_C128)
+  if (prec == QS_C128 && f64)
+    k_dm_from_pure<double><<<g, 256, 0, st>>>(static_cast<double2*>(rho), static_cast<const double2*>(psi), nq,
+                                              weight, accumulate);
+  else if (prec == QS_C128)
     k_dm_from_pure_df<<<g, 256, 0, st>>>(static_cast<double2*>(rho), static_cast<const double2*>(psi), nq,
                                          qsdf::split_const(weight), accumulate);
   else

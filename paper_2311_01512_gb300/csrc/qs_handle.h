@@ -22,7 +22,7 @@ struct qs_state {
   int ns = 0;          // storage qubits
   int is_density = 0;
   qs_prec prec = QS_C128;
-  qs_arith arith = QS_ARITH_DF;
+  qs_arith arith = QS_ARITH_FX;
   int f64_share = 0;     // sixteenths of one-target-gate chunks run in native FP64
   int tensor_cores = 1;  // complex64 dense gates with 3..5 targets on tcgen05
   int* d_err = nullptr;  // device error word (bounded waits that ran out)

@@ -110,6 +110,46 @@ struct GadgetDfParams {
   int h;
 };
 
+// complex128 kernels in block fixed-point arithmetic (qs_fx.cuh): constants
+// prepared on the host as 60-bit fixed-point parts of their row group.
+struct FxPart {
+  int32_t h, l;          // M = h 2^30 + l, 0 <= l < 2^30
+};
+
+// One-target gate: rows r = (out0.re, out0.im, out1.re, out1.im) over the
+// columns (a.re, a.im, b.re, b.im) of the pair (a, b); rows 0-1 share the
+// exponent em[0] (of m00, m01), rows 2-3 em[1] (of m10, m11).
+struct Gate1FxParams {
+  FxPart m[4][4];
+  int em[2];
+  uint64_t npairs;
+  uint64_t ctrl_mask;
+  int t;
+  int nins;
+  int8_t ins[kMaxQ];
+};
+
+// Diagonal entry d_j: parts of Re, Im and -Im with their shared exponent.
+struct DiagFxEntry {
+  FxPart re, im, nim;
+  int em;
+};
+struct DiagFxParams {
+  DiagFxEntry e[64];
+  uint64_t namps;
+  int n;
+  int8_t tpos[kMaxDense];
+};
+
+// Pauli / phase gadget: cos(phi), sin(phi), -sin(phi) with their shared exponent.
+struct GadgetFxParams {
+  uint64_t xy, yz, nwork;
+  FxPart c, s, ns;
+  int em;
+  int eta;
+  int h;
+};
+
 // Density-matrix channels acting on groups of 4 (one qubit: bits t, t+N) or 16
 // (two qubits: t1, t2, t1+N, t2+N) Choi amplitudes.
 enum GroupOp { G_DEPHASE1 = 0, G_DEPHASE2 = 1, G_DEPOL1 = 2, G_DEPOL2 = 3, G_DAMP = 4, G_PAULI1 = 5 };
@@ -119,6 +159,17 @@ struct GroupParams {
   int8_t ins[4];         // sorted member positions
   int8_t mpos[4];        // member bit b -> qubit position
   double f[4];           // channel coefficients (see the kernel)
+};
+
+// The same channels in block fixed point: coefficient slots with their own
+// exponents (which slots an operation uses is stated at its kernel).
+struct GroupFxParams {
+  uint64_t ngroups;
+  int nbits;
+  int8_t ins[4];
+  int8_t mpos[4];
+  FxPart cf[6];
+  int em[6];
 };
 
 // Partial trace (Sec. "Partial trace").
@@ -213,10 +264,17 @@ cudaError_t launch_gate1_df(void* amps, const Gate1DfParams& p, cudaStream_t st)
 cudaError_t launch_dense_df(void* amps, const DenseParams& p, cudaStream_t st);
 cudaError_t launch_diag_df(void* amps, const DiagParams& p, cudaStream_t st);
 cudaError_t launch_gadget_df(void* amps, const GadgetDfParams& p, cudaStream_t st);
+// complex128 in block fixed point (qs_gates_fx.cu)
+cudaError_t launch_gate1_fx(void* amps, const Gate1FxParams& p, cudaStream_t st);
+cudaError_t launch_diag_fx(void* amps, const DiagFxParams& p, cudaStream_t st);
+cudaError_t launch_gadget_fx(void* amps, const GadgetFxParams& p, cudaStream_t st);
+// G_DEPOL1, G_DEPOL2, G_DAMP, G_PAULI1
+cudaError_t launch_group_fx(void* amps, int op, const GroupFxParams& p, cudaStream_t st);
 // complex64 dense gates on the tensor cores, 3 <= n <= 5 (qs_tc.cu)
 cudaError_t launch_dense_tc(void* amps, const TcParams& p, cudaStream_t st);
-// complex128 dense gates on the bf16 tensor cores, exact integer slices, 3 <= n <= 5 kernel targets (qs_tc_ozaki.cu)
-cudaError_t launch_dense_ozaki(void* amps, const TcParams& p, cudaStream_t st);
+// complex128 dense gates on the bf16 tensor cores, exact integer slices, 3 <= n <= 5 kernel targets (qs_tc_ozaki.cu);
+// slices: 7 (49-bit operands, with double-float arithmetic) or 8 (56-bit, with block fixed point)
+cudaError_t launch_dense_ozaki(void* amps, const TcParams& p, int slices, cudaStream_t st);
 cudaError_t launch_block_compose(const ComposeBlock* blocks, int nblocks, const ComposeInstr* instrs,
                                  const double* data, double* out, cudaStream_t st);
 // cost-model network (qs_mlp.cu)
@@ -238,21 +296,24 @@ cudaError_t launch_group_df(void* amps, int op, const GroupParams& p, cudaStream
 cudaError_t launch_ptrace(qs_prec prec, const void* in, void* out, const PtraceParams& p,
                           cudaStream_t st);
 cudaError_t launch_superop(const double* kraus, int num_ops, int n, double* sup, cudaStream_t st);
+// f64: complex128 in native FP64 (FP64 and block fixed-point arithmetic) instead of double-float
 cudaError_t launch_dm_from_pure(qs_prec prec, void* rho, const void* psi, int nq, double weight,
-                                int accumulate, cudaStream_t st);
+                                int accumulate, cudaStream_t st, bool f64);
 cudaError_t launch_init_zero(qs_prec prec, void* amps, int ns, cudaStream_t st);
 
 // Reductions: stage one writes kReduceBlocks complex128 partial sums, stage two
 // sums them in a fixed order into result[0] (added to result[0] if accumulate).
-cudaError_t launch_norm(qs_prec prec, const void* amps, int ns, double2* partials, cudaStream_t st);
+// f64: complex128 products and sums in native FP64 (FP64 and block fixed-point
+// arithmetic) instead of double-float.
+cudaError_t launch_norm(qs_prec prec, const void* amps, int ns, double2* partials, cudaStream_t st, bool f64);
 cudaError_t launch_trace(qs_prec prec, const void* amps, int nq, double2* partials, cudaStream_t st);
 cudaError_t launch_expec_dm(qs_prec prec, const void* amps, int nq, const PauliTerm* terms,
                             int nterms, double2* partials, cudaStream_t st);
 cudaError_t launch_expec_sv(qs_prec prec, const void* amps, int nq, const PauliTerm* terms,
-                            int nterms, double2* partials, cudaStream_t st);
+                            int nterms, double2* partials, cudaStream_t st, bool f64);
 // the diagonal (I/Z) terms of a statevector Pauli sum by warp Walsh-Hadamard transforms; N >= 5
 cudaError_t launch_expec_sv_diag(qs_prec prec, const void* amps, int nq, const PauliTerm* terms, int nterms,
-                                 double2* partials, cudaStream_t st);
+                                 double2* partials, cudaStream_t st, bool f64);
 cudaError_t launch_reduce_final(const double2* partials, double2* result, int accumulate, cudaStream_t st,
                                 int nblocks = kReduceBlocks);
 

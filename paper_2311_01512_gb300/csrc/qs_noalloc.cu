@@ -10,6 +10,7 @@
 // This entry point takes a raw device pointer and uses a fixed scratch array
 // that lives in the library's own device image (g_noalloc_scratch below).
 // Every GPU that loads the library keeps that array until the process exits.
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -84,6 +85,10 @@ extern "C" qs_status qs_expec_pauli_sum_noalloc(const void* d_amps, int num_qubi
     t.eta = num_y & 3;
     terms[n] = t;
   }
+  // Terms with equal flip masks next to each other: the kernel shares one
+  // partner load per run of equal masks.
+  std::stable_sort(terms, terms + num_terms,
+                   [](const qsk::PauliTerm& x, const qsk::PauliTerm& y) { return x.xy < y.xy; });
 
   unsigned char* scratch = nullptr;
   qs_status st = scratch_for_current_device(&scratch);
@@ -99,7 +104,7 @@ extern "C" qs_status qs_expec_pauli_sum_noalloc(const void* d_amps, int num_qubi
       cudaSuccess)
     return QS_ERR_CUDA;
   cudaError_t e = is_density ? qsk::launch_expec_dm(prec, d_amps, num_qubits, d_terms, num_terms, d_partials, stream)
-                             : qsk::launch_expec_sv(prec, d_amps, num_qubits, d_terms, num_terms, d_partials, stream);
+                             : qsk::launch_expec_sv(prec, d_amps, num_qubits, d_terms, num_terms, d_partials, stream, true);
   if (e == cudaSuccess) e = qsk::launch_reduce_final(d_partials, d_result, 0, stream);
   double2 result;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&result, d_result, sizeof(double2), cudaMemcpyDeviceToHost, stream);

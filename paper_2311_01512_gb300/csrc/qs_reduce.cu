@@ -47,6 +47,21 @@ __global__ void __launch_bounds__(256) k_norm(const typename Cplx<R>::T* __restr
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// The same sum in native FP64 (complex128 with FP64 or block fixed-point
+// arithmetic): one FMA per square, a per-thread FP64 sum.
+__global__ void __launch_bounds__(256) k_norm_f64(const double2* __restrict__ psi, uint64_t n,
+                                                  double2* __restrict__ partials) {
+  double acc = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double2 a = psi[i];
+    acc = fma(a.x, a.x, acc);
+    acc = fma(a.y, a.y, acc);
+  }
+  const double2 s = block_sum(make_double2(acc, 0.0));
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
 // Tr rho = sum_j beta_{j (2^N + 1)} (Sec. "Pauli string expectation value").
 template <typename R>
 __global__ void __launch_bounds__(256) k_trace(const typename Cplx<R>::T* __restrict__ rho, int nq,
@@ -225,6 +240,86 @@ __global__ void __launch_bounds__(256) k_expec_sv(const typename Cplx<R>::T* __r
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// The same one-pass expectation in native FP64 (complex128 with FP64 or block
+// fixed-point arithmetic): products and the per-thread sum in FP64.
+template <int E>
+__global__ void __launch_bounds__(256) k_expec_sv_f64(const double2* __restrict__ psi, int nq,
+                                                      const PauliTerm* __restrict__ terms, int nterms,
+                                                      double2* __restrict__ partials) {
+  extern __shared__ unsigned char sm_raw[];
+  PauliTerm* ts = reinterpret_cast<PauliTerm*>(sm_raw);
+  GroupDf* gs = reinterpret_cast<GroupDf*>(ts + nterms);
+  __shared__ int ngroups;
+  for (int n = threadIdx.x; n < nterms; n += blockDim.x) ts[n] = terms[n];
+  __syncthreads();
+  if (threadIdx.x == 0) {                 // runs of equal xy, in order
+    int ng = 0;
+    for (int n = 0; n < nterms; ++n) {
+      if (n == 0 || ts[n].xy != ts[n - 1].xy) {
+        const uint64_t xy = ts[n].xy;
+        gs[ng] = GroupDf{xy, xy ? 1ull << (63 - __clzll((long long)xy)) : 0ull, n, 0};
+        ++ng;
+      }
+      ++gs[ng - 1].count;
+    }
+    ngroups = ng;
+  }
+  __syncthreads();
+  const int ng = ngroups;
+  double acc = 0.0;
+  constexpr uint64_t kTile = 256ull * E;
+  const uint64_t dim = 1ull << nq;
+  const uint64_t ntiles = dim > kTile ? dim / kTile : 1;
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint64_t base = tile * kTile;
+    uint64_t iu[E];
+    bool ok[E];
+    double2 a[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      iu[e] = base + (uint64_t)(e * 256 + threadIdx.x);
+      ok[e] = iu[e] < dim;
+      a[e] = ok[e] ? psi[iu[e]] : make_double2(0.0, 0.0);
+    }
+    for (int g = 0; g < ng; ++g) {
+      const GroupDf G = gs[g];
+      if (G.xy == 0) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          if (!ok[e]) continue;
+          const double p2 = fma(a[e].x, a[e].x, a[e].y * a[e].y);
+          for (int n = G.first; n < G.first + G.count; ++n)
+            acc = fma(parity64(iu[e] & ts[n].yz) ? -ts[n].h : ts[n].h, p2, acc);
+        }
+        continue;
+      }
+      if (G.hb >= kTile && (base & G.hb)) continue;     // the whole tile is the upper half
+      bool vis[E];
+      double2 b[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        vis[e] = ok[e] && !(iu[e] & G.hb);
+        b[e] = vis[e] ? psi[iu[e] ^ G.xy] : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        if (!vis[e]) continue;
+        const uint64_t ip = iu[e] ^ G.xy;
+        // q = conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
+        const double qr = fma(a[e].x, b[e].x, a[e].y * b[e].y);
+        const double qi = fma(a[e].x, b[e].y, -(a[e].y * b[e].x));
+        for (int n = G.first; n < G.first + G.count; ++n) {
+          const int eta = ts[n].eta;
+          const bool neg = parity64(ip & ts[n].yz) != (eta == 1 || eta == 2);
+          acc = fma(neg ? -2.0 * ts[n].h : 2.0 * ts[n].h, (eta & 1) ? qi : qr, acc);
+        }
+      }
+    }
+  }
+  const double2 s = block_sum(make_double2(acc, 0.0));
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
 // The diagonal (I/Z) terms of a statevector Pauli sum, many at a time:
 // sum_n h_n sum_i |alpha_i|^2 (-1)^{popc(i & z_n)}.  A warp holds 32
 // consecutive amplitudes i = base + m; a Walsh-Hadamard transform over its
@@ -306,6 +401,56 @@ __global__ void __launch_bounds__(256) k_expec_sv_diag(const typename Cplx<R>::T
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// The diagonal-term kernel in native FP64 (butterflies and the sum in FP64).
+struct ZTerm64 {
+  uint64_t z;
+  double h;
+};
+template <int U>
+__global__ void __launch_bounds__(256) k_expec_sv_diag_f64(const double2* __restrict__ psi, int nq,
+                                                           const PauliTerm* __restrict__ terms, int nterms,
+                                                           double2* __restrict__ partials) {
+  extern __shared__ ZTerm64 tz64[];
+  for (int n = threadIdx.x; n < nterms; n += blockDim.x) tz64[n] = ZTerm64{terms[n].yz, terms[n].h};
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  double acc = 0.0;
+  const uint64_t ntiles = (1ull << nq) / (32 * U);
+  const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t tile = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tile < ntiles;
+       tile += nwarps) {
+    const uint64_t base = tile * (32 * U);
+    double2 a[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) a[k] = psi[base + 32 * k + lane];
+    double w[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      w[k] = fma(a[k].x, a[k].x, a[k].y * a[k].y);
+#pragma unroll
+      for (int b = 1; b < 32; b <<= 1) {
+        const double o = __shfl_xor_sync(0xFFFFFFFFu, w[k], b);
+        w[k] = (lane & b) ? o - w[k] : w[k] + o;
+      }
+    }
+    for (int n0 = 0; n0 < nterms; n0 += 32) {
+      const int n = n0 + lane;
+      ZTerm64 t{0, 0.0};
+      if (n < nterms) t = tz64[n];
+      const int src = (int)(t.z & 31u);
+      const bool odd = parity64(base & t.z);
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const double wz = __shfl_sync(0xFFFFFFFFu, w[k], src);
+        const bool neg = odd ^ (bool)(__popc((unsigned)(32 * k) & (unsigned)t.z) & 1);
+        acc = fma(neg ? -t.h : t.h, wz, acc);
+      }
+    }
+  }
+  const double2 s = block_sum(make_double2(acc, 0.0));
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
 template <typename R, int U>
 static cudaError_t launch_diag(const void* amps, int nq, const PauliTerm* terms, int nterms, double2* partials,
                                cudaStream_t st) {
@@ -322,8 +467,28 @@ static cudaError_t launch_diag(const void* amps, int nq, const PauliTerm* terms,
 }
 
 cudaError_t launch_expec_sv_diag(qs_prec prec, const void* amps, int nq, const PauliTerm* terms, int nterms,
-                                 double2* partials, cudaStream_t st) {
+                                 double2* partials, cudaStream_t st, bool f64) {
   if (nq < 5 || nterms > kTermChunk) return cudaErrorInvalidValue;
+  if (prec == QS_C128 && f64) {
+    static bool attr_done = false;
+    if (!attr_done) {
+      cudaError_t e = cudaFuncSetAttribute(k_expec_sv_diag_f64<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(ZTerm64) * kTermChunk));
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_expec_sv_diag_f64<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(ZTerm64) * kTermChunk));
+      if (e != cudaSuccess) return e;
+      attr_done = true;
+    }
+    const size_t sm = sizeof(ZTerm64) * (size_t)nterms;
+    if (nq >= 7)
+      k_expec_sv_diag_f64<4><<<kReduceBlocks, 256, sm, st>>>(static_cast<const double2*>(amps), nq, terms, nterms,
+                                                              partials);
+    else
+      k_expec_sv_diag_f64<1><<<kReduceBlocks, 256, sm, st>>>(static_cast<const double2*>(amps), nq, terms, nterms,
+                                                              partials);
+    return cudaGetLastError();
+  }
   if (prec == QS_C128)
     return nq >= 7 ? launch_diag<double, 4>(amps, nq, terms, nterms, partials, st)
                    : launch_diag<double, 1>(amps, nq, terms, nterms, partials, st);
@@ -352,9 +517,11 @@ __global__ void __launch_bounds__(1024) k_reduce_final(const double2* __restrict
 
 // Stage-one kernels always run exactly kReduceBlocks blocks; blocks with no
 // work write a zero partial.
-cudaError_t launch_norm(qs_prec prec, const void* amps, int ns, double2* partials, cudaStream_t st) {
+cudaError_t launch_norm(qs_prec prec, const void* amps, int ns, double2* partials, cudaStream_t st, bool f64) {
   const uint64_t n = 1ull << ns;
-  if (prec == QS_C128)
+  if (prec == QS_C128 && f64)
+    k_norm_f64<<<kNormBlocks, 256, 0, st>>>(static_cast<const double2*>(amps), n, partials);
+  else if (prec == QS_C128)
     k_norm<double><<<kNormBlocks, 256, 0, st>>>(static_cast<const double2*>(amps), n, partials);
   else
     k_norm<float><<<kNormBlocks, 256, 0, st>>>(static_cast<const float2*>(amps), n, partials);
@@ -396,8 +563,21 @@ static cudaError_t expec_sv_u(const void* amps, int nq, const PauliTerm* terms, 
 }
 
 cudaError_t launch_expec_sv(qs_prec prec, const void* amps, int nq, const PauliTerm* terms, int nterms,
-                            double2* partials, cudaStream_t st) {
+                            double2* partials, cudaStream_t st, bool f64) {
   if (nterms > kTermChunk) return cudaErrorInvalidValue;
+  if (prec == QS_C128 && f64) {
+    static bool attr_done = false;
+    const size_t per = sizeof(PauliTerm) + sizeof(GroupDf);
+    if (!attr_done) {
+      const cudaError_t e = cudaFuncSetAttribute(k_expec_sv_f64<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(per * kTermChunk));
+      if (e != cudaSuccess) return e;
+      attr_done = true;
+    }
+    k_expec_sv_f64<4><<<kReduceBlocks, 256, per * (size_t)nterms, st>>>(static_cast<const double2*>(amps), nq, terms,
+                                                                         nterms, partials);
+    return cudaGetLastError();
+  }
   // tiles of 1024 amplitudes (28 qubits, 8 random terms: 6.9 ms against 7.5
   // and 8.0 ms for tiles of 512 and 2048)
   return prec == QS_C128 ? expec_sv_u<double, 4>(amps, nq, terms, nterms, partials, st)

@@ -39,7 +39,6 @@ namespace {
 using namespace tcptx;
 
 constexpr int kRows = 128;
-constexpr int kS = qsoz::kSlices;
 constexpr uint32_t kWaitLimit = 1u << 26;
 
 __host__ __device__ constexpr uint32_t tmem_cols(uint32_t n) {
@@ -53,13 +52,28 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return r;
 }
 
-// seven packed (re, im) digit pairs of one amplitude (words of re and im)
+// KS (7 or 8) digits of a double as floats
+template <int KS>
+__device__ __forceinline__ void digits(uint32_t hw, uint32_t lw, int emax, float* f) {
+  if constexpr (KS == 8)
+    qsoz::digit_floats_t8(qsoz::fixed_t8(hw, lw, emax), f);
+  else
+    qsoz::digit_floats_t(qsoz::fixed_t(hw, lw, emax), f);
+}
+
+// lower bound of a row or column exponent maximum: zeros and subnormals
+// (their implicit bit wrongly set) then shift out entirely
+template <int KS>
+__host__ __device__ constexpr int emax_floor() { return KS == 8 ? 58 : qsoz::kEmaxFloor; }
+
+// KS packed (re, im) digit pairs of one amplitude (words of re and im)
+template <int KS>
 __device__ __forceinline__ void slice_amp(const uint32_t* w, int emax, uint32_t* out) {
-  float fr[kS], fi[kS];
-  qsoz::digit_floats_t(qsoz::fixed_t(w[0], w[1], emax), fr);
-  qsoz::digit_floats_t(qsoz::fixed_t(w[2], w[3], emax), fi);
+  float fr[KS], fi[KS];
+  digits<KS>(w[0], w[1], emax, fr);
+  digits<KS>(w[2], w[3], emax, fi);
 #pragma unroll
-  for (int s = 0; s < kS; ++s) out[s] = pack_bf16(fr[s], fi[s]);
+  for (int s = 0; s < KS; ++s) out[s] = pack_bf16(fr[s], fi[s]);
 }
 
 // bounded wait on an mbarrier phase; true when it ran out
@@ -94,15 +108,15 @@ __device__ __forceinline__ double realified(const TcParams& p, int D, int k, int
 // 256-column MMAs.  The first MMA (s = 0, first K chunk) initialises all
 // levels.  adesc / bdesc: descriptors of slice 0 of A and B; K chunks are
 // 256 bytes apart, 8-row groups of B kdim * 16 bytes (encoded address >> 4).
-template <int N, int KCH>
+template <int N, int KCH, int KS>
 __device__ __forceinline__ void mma_tile(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t abytes) {
   constexpr int K = 16 * KCH;
 #pragma unroll
-  for (int s = 0; s < kS; ++s) {
+  for (int s = 0; s < KS; ++s) {
     constexpr int kMax = 256;
 #pragma unroll
-    for (int c0 = 0; c0 < (kS - s) * N; c0 += kMax) {
-      const int w = (kS - s) * N - c0 < kMax ? (kS - s) * N - c0 : kMax;
+    for (int c0 = 0; c0 < (KS - s) * N; c0 += kMax) {
+      const int w = (KS - s) * N - c0 < kMax ? (KS - s) * N - c0 : kMax;
       const uint32_t idesc = idesc_bf16(kRows, w);
 #pragma unroll
       for (int kk = 0; kk < KCH; ++kk)
@@ -114,8 +128,9 @@ __device__ __forceinline__ void mma_tile(uint32_t d_tmem, uint64_t adesc, uint64
 
 }  // namespace
 
-template <int NT, int THREADS, int NBUF, int CTAS>
+template <int NT, int THREADS, int NBUF, int CTAS, int KS>
 __global__ void __launch_bounds__(THREADS, CTAS) k_dense_ozaki(double2* __restrict__ psi, const __grid_constant__ TcParams p) {
+  constexpr int kS = KS;
   constexpr int D = 1 << NT;
   constexpr int K = 2 * D, N = 2 * D;
   constexpr int CG = THREADS / kRows;         // threads per row
@@ -142,7 +157,7 @@ __global__ void __launch_bounds__(THREADS, CTAS) k_dense_ozaki(double2* __restri
 
   // B: column maxima of the exponents, then the digit slices (once per CTA)
   for (int n = tid; n < N; n += THREADS) {
-    int e = qsoz::kEmaxFloor;
+    int e = emax_floor<KS>();
     for (int k = 0; k < K; ++k) e = max(e, qsoz::biased_exp((uint32_t)__double2hiint(realified(p, D, k, n))));
     csc[n] = e;
   }
@@ -151,7 +166,7 @@ __global__ void __launch_bounds__(THREADS, CTAS) k_dense_ozaki(double2* __restri
     const int n = idx / K, k = idx % K;
     const double v = realified(p, D, k, n);
     float f[kS];
-    qsoz::digit_floats_t(qsoz::fixed_t((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v), csc[n]), f);
+    digits<KS>((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v), csc[n], f);
     const uint32_t off = canon_off16(n, k, K);
 #pragma unroll
     for (int s = 0; s < kS; ++s)
@@ -177,8 +192,11 @@ __global__ void __launch_bounds__(THREADS, CTAS) k_dense_ozaki(double2* __restri
     rowexp[kRows + g] = 0;
   }
   __syncthreads();
-  // scale 2^(Ea + Eb - 54) with biased Ea, Eb, as an exponent-field increment
-  for (int n = tid; n < N; n += THREADS) csc[n] = (int)((unsigned)(csc[n] - 2046 - 54) << 20);
+  // scale 2^(Ea + Eb - 2046 - 54) (seven slices) or 2^(Ea + Eb - 2046 - 53)
+  // (eight: the recombined sum is kept divided by 2^8) with biased Ea, Eb,
+  // as an exponent-field increment
+  constexpr int kScaleOff = KS == 8 ? 53 : 54;
+  for (int n = tid; n < N; n += THREADS) csc[n] = (int)((unsigned)(csc[n] - 2046 - kScaleOff) << 20);
   if (tid == 0) {
     tile_base[0] = insert_zeros(blockIdx.x, p.hi_ins, p.nhi) | p.ctrl_mask;
 #pragma unroll
@@ -227,7 +245,7 @@ __global__ void __launch_bounds__(THREADS, CTAS) k_dense_ozaki(double2* __restri
   // row maximum of the exponents (the CG threads of a row are in different warps)
   // (exponent fields compared in place: 0x7FF00000 of the high words)
   auto row_max = [&](int slot) {
-    uint32_t em = (uint32_t)qsoz::kEmaxFloor << 20;
+    uint32_t em = (uint32_t)emax_floor<KS>() << 20;
 #pragma unroll
     for (int i = 0; i < EPT; ++i) em = max(em, max(R[i][0] & 0x7FF00000u, R[i][2] & 0x7FF00000u));
     atomicMax(rowexp + slot * kRows + g, (int)em);
@@ -251,7 +269,7 @@ __global__ void __launch_bounds__(THREADS, CTAS) k_dense_ozaki(double2* __restri
           uint32_t bits[kS];
 #pragma unroll
           for (int L = 0; L < kS; ++L) bits[L] = __float_as_uint(v[L][q] + 12582912.0f);
-          const double r = __ll2double_rn(qsoz::combine_levels(bits));
+          const double r = __ll2double_rn(KS == 8 ? qsoz::combine_levels8(bits) : qsoz::combine_levels(bits));
           const int hi = __double2hiint(r);                // 0 only for r = 0, which stays 0
           o[q] = __hiloint2double(hi + (hi != 0 ? egs + scl[q] : 0), __double2loint(r));
         }
@@ -286,7 +304,7 @@ __global__ void __launch_bounds__(THREADS, CTAS) k_dense_ozaki(double2* __restri
     for (int i = 0; i < EPT; i += 4) {
       uint32_t pk[4][kS];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) slice_amp(R[i + e], eg, pk[e]);
+      for (int e = 0; e < 4; ++e) slice_amp<KS>(R[i + e], eg, pk[e]);
       const uint32_t off = canon_off16(g, 2 * (l0 + i), K);
 #pragma unroll
       for (int s = 0; s < kS; ++s)
@@ -297,7 +315,7 @@ __global__ void __launch_bounds__(THREADS, CTAS) k_dense_ozaki(double2* __restri
     if (tid == 0) {
       fence_after_sync();
       const uint64_t ad = smem_desc(smem_u32(A), 128, sbo), bd = smem_desc(smem_u32(b_dig), 128, sbo);
-      mma_tile<N, K / 16>(tmem + (uint32_t)(b * LCOLS), ad, bd, ABYTES);
+      mma_tile<N, K / 16, KS>(tmem + (uint32_t)(b * LCOLS), ad, bd, ABYTES);
       mma_commit(mbar + b);
     }
     if (cg == 0) rowexp[par * kRows + g] = 0;   // read by every thread of the row before the barrier
@@ -341,7 +359,7 @@ __global__ void __launch_bounds__(THREADS, CTAS) k_dense_ozaki(double2* __restri
   if (warp == 0) tmem_dealloc(tmem, TCOLS);
 }
 
-template <int NT, int THREADS, int NBUF, int CTAS>
+template <int NT, int THREADS, int NBUF, int CTAS, int kS>
 static cudaError_t dense_ozaki_nt(void* amps, const TcParams& p, cudaStream_t st) {
   constexpr int D = 1 << NT, K = 2 * D, N = 2 * D;
   constexpr size_t smem = (size_t)NBUF * kS * (kRows * K * 2) + (size_t)kS * (N * K * 2) + 8 * (D + kRows + 4) +
@@ -350,7 +368,7 @@ static cudaError_t dense_ozaki_nt(void* amps, const TcParams& p, cudaStream_t st
   static_assert(CTAS * tmem_cols(NBUF * kS * N) <= 512, "tensor memory");
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_dense_ozaki<NT, THREADS, NBUF, CTAS>,
+    cudaError_t e = cudaFuncSetAttribute(k_dense_ozaki<NT, THREADS, NBUF, CTAS, kS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_done = true;
@@ -359,7 +377,7 @@ static cudaError_t dense_ozaki_nt(void* amps, const TcParams& p, cudaStream_t st
   // the SMs' tile counts at the end of the pass (7% and 2% faster measured)
   const uint64_t maxb = (uint64_t)num_sms() * CTAS * (NT <= 4 ? 8 : 1);
   const unsigned g = (unsigned)(p.ntiles < maxb ? p.ntiles : maxb);
-  k_dense_ozaki<NT, THREADS, NBUF, CTAS><<<g, THREADS, smem, st>>>(static_cast<double2*>(amps), p);
+  k_dense_ozaki<NT, THREADS, NBUF, CTAS, kS><<<g, THREADS, smem, st>>>(static_cast<double2*>(amps), p);
   return cudaGetLastError();
 }
 
@@ -369,11 +387,19 @@ static cudaError_t dense_ozaki_nt(void* amps, const TcParams& p, cudaStream_t st
 // double-buffered 256-thread CTAs; 4 targets 11.2 ms as two 256-thread CTAs
 // against 13.9 ms as one double-buffered 512-thread CTA).  Tensor memory
 // (seven levels of N columns per buffer) bounds the CTAs per SM.
-cudaError_t launch_dense_ozaki(void* amps, const TcParams& p, cudaStream_t st) {
+cudaError_t launch_dense_ozaki(void* amps, const TcParams& p, int slices, cudaStream_t st) {
+  if (slices == 8) {
+    switch (p.n) {
+      case 3: return dense_ozaki_nt<3, 128, 1, 4, 8>(amps, p, st);
+      case 4: return dense_ozaki_nt<4, 256, 1, 2, 8>(amps, p, st);
+      case 5: return dense_ozaki_nt<5, 512, 1, 1, 8>(amps, p, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (p.n) {
-    case 3: return dense_ozaki_nt<3, 128, 1, 4>(amps, p, st);
-    case 4: return dense_ozaki_nt<4, 256, 1, 2>(amps, p, st);
-    case 5: return dense_ozaki_nt<5, 512, 1, 1>(amps, p, st);
+    case 3: return dense_ozaki_nt<3, 128, 1, 4, 7>(amps, p, st);
+    case 4: return dense_ozaki_nt<4, 256, 1, 2, 7>(amps, p, st);
+    case 5: return dense_ozaki_nt<5, 512, 1, 1, 7>(amps, p, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -22,6 +22,7 @@ QS_C64 = 0
 QS_C128 = 1
 QS_ARITH_DF = 0
 QS_ARITH_F64 = 1
+QS_ARITH_FX = 2
 
 STATUS = {
     0: "QS_OK", 1: "QS_ERR_ARG", 2: "QS_ERR_QUBIT_RANGE", 3: "QS_ERR_DUP_QUBIT",

@@ -2,7 +2,8 @@
 // (qs_slices.cuh): digits reconstruct the rounded fixed-point value exactly,
 // stay within their bounds and are exact in bf16; slice-product levels stay
 // exact in FP32; the level recombination is exact; a full dot product of K
-// terms stays within (K + 1) 2^-47 of the row-max x column-max scale.
+// terms stays within (K + 1) 2^-47 of the row-max x column-max scale with
+// seven slices, (K + 1) 2^-54 with eight.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -164,6 +165,125 @@ int main() {
     CHECK(rel < (K + 1) * std::ldexp(1.0, -47), "dot product error %.3g of the scale (K = %d)", rel, K);
   }
   std::printf("worst dot-product error / (row max * column max) = %.3g (2^%.1f)\n", worst, std::log2(worst));
+
+  // ---- eight slices (qsoz::*8: 56-bit operands) ----
+  // 5. digits: exact reconstruction of x 2^(55 - Emax) rounded half up, bounds, bf16
+  constexpr int kS8 = qsoz::kSlices8;
+  constexpr int kFloor8 = 58;
+  for (int it = 0; it < 3000000; ++it) {
+    double x = std::ldexp(u(rng), ex(rng));
+    if (it % 97 == 0) x = 0.0;
+    if (it % 101 == 0) x = -0.0;
+    if (it % 103 == 0) x = std::ldexp(u(rng), -1040);
+    if (it % 107 == 0) x = std::ldexp(u(rng), -990);
+    int emax = (x == 0.0 ? 1000 : bexp(x)) + (it % 3 == 0 ? 0 : gap(rng) % (it % 5 == 0 ? 70 : 4));
+    if (it % 7 == 0) emax = bexp(x);
+    if (it % 11 == 0) emax += 1100;
+    emax = std::max(emax, kFloor8);
+    uint32_t hw, lw;
+    words(x, hw, lw);
+    const uint64_t w = qsoz::fixed_t8(hw, lw, emax);
+    long long v = 0;
+    for (int s = 0; s < kS8; ++s) {
+      const int d = qsoz::digit_t8(w, s);
+      if (s == 0)
+        CHECK(d >= -128 && d <= 128, "8: d0 = %d", d);
+      else
+        CHECK(d >= -64 && d <= 63, "8: d%d = %d", s, d);
+      v += (long long)d * (1ll << (49 - 7 * s));
+    }
+    const long double y = std::ldexp((long double)x, 55 - (emax - 1023));
+    const long long ref = (long long)std::floor(y + 0.5L);
+    CHECK(v == ref, "8: x = %.17g emax = %d: V = %lld, expected %lld", x, emax, v, ref);
+    float f[kS8];
+    qsoz::digit_floats_t8(w, f);
+    for (int s = 0; s < kS8; ++s) {
+      CHECK(f[s] == (float)qsoz::digit_t8(w, s), "8: float digit %d", s);
+      CHECK((qsdf::f2u(f[s]) & 0xFFFFu) == 0u, "8: digit %d not exact in bf16", s);
+    }
+  }
+
+  // 6. levels 0..7 of extreme digits stay below 2^22 and are exact in FP32
+  for (int it = 0; it < 20000; ++it) {
+    const int K = 64;
+    int a[kS8][64], b[kS8][64];
+    for (int s = 0; s < kS8; ++s)
+      for (int k = 0; k < K; ++k) {
+        const int mag = s == 0 ? 128 : 64;
+        const bool sgn = it < 4 ? ((it >> (s == 0)) & 1) : (rng() & 1);
+        a[s][k] = sgn ? -mag : (s == 0 ? mag : 63);
+        b[s][k] = (it < 4 ? (it & 1) : (rng() & 1)) ? -mag : (s == 0 ? mag : 63);
+      }
+    for (int L = 0; L < kS8; ++L) {
+      long long exact = 0;
+      float acc = 0.0f;
+      for (int s = 0; s <= L; ++s)
+        for (int k = 0; k < K; ++k) {
+          const long long p = (long long)a[s][k] * b[L - s][k];
+          exact += p;
+          acc += (float)p;
+        }
+      CHECK(std::llabs(exact) < (1ll << 22), "8: level %d = %lld", L, exact);
+      CHECK((long long)acc == exact, "8: level %d not exact in FP32", L);
+    }
+  }
+
+  // 7. recombination: floor(sum_L level_L 2^(7(7-L)) / 2^8), whenever the true
+  // value fits in 63 bits (levels up to 2.5 2^20, level 0 up to 2^20)
+  std::uniform_int_distribution<int> lev8(-(5 << 19), 5 << 19);
+  for (int it = 0; it < 2000000; ++it) {
+    uint32_t bits[8];
+    __int128 sum = 0;
+    for (int L = 0; L < kS8; ++L) {
+      const int top = L == 0 ? (1 << 20) : (5 << 19);
+      const int v = it < 3 ? (it == 0 ? top : (it == 1 ? -top : 0)) : (L == 0 ? lev0(rng) : lev8(rng));
+      bits[L] = qsdf::f2u((float)v + 12582912.0f);
+      sum += (__int128)v * ((__int128)1 << (7 * (7 - L)));
+    }
+    // floor division by 2^8
+    __int128 ref = sum >> 8;
+    const long long got = qsoz::combine_levels8(bits);
+    CHECK((__int128)got == ref, "8: combine %lld", got);
+  }
+
+  // 8. full dot products through eight digits: within (K + 1) 2^-54 of the scale
+  double worst8 = 0.0;
+  for (int it = 0; it < 20000; ++it) {
+    const int K = 2 << (it % 5 + 1);  // 4 .. 64
+    double a[64], b[64];
+    const int spread = it % 4 == 0 ? 40 : 3;
+    std::uniform_int_distribution<int> es(-spread, 0);
+    for (int k = 0; k < K; ++k) {
+      a[k] = std::ldexp(gauss(rng), es(rng) - 15);
+      b[k] = std::ldexp(gauss(rng), es(rng));
+    }
+    int ea = kFloor8, eb = kFloor8;
+    for (int k = 0; k < K; ++k) {
+      ea = std::max(ea, bexp(a[k]));
+      eb = std::max(eb, bexp(b[k]));
+    }
+    long long lv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < K; ++k) {
+      uint32_t h1, l1, h2, l2;
+      words(a[k], h1, l1);
+      words(b[k], h2, l2);
+      const uint64_t wa = qsoz::fixed_t8(h1, l1, ea), wb = qsoz::fixed_t8(h2, l2, eb);
+      for (int s = 0; s < kS8; ++s)
+        for (int t = 0; s + t < kS8; ++t) lv[s + t] += (long long)qsoz::digit_t8(wa, s) * qsoz::digit_t8(wb, t);
+    }
+    uint32_t bits[8];
+    for (int L = 0; L < kS8; ++L) bits[L] = qsdf::f2u((float)lv[L] + 12582912.0f);
+    const long long acc = qsoz::combine_levels8(bits);
+    const long double got = std::ldexp((long double)acc, (ea - 1023) + (eb - 1023) - 53);
+    long double exact = 0;
+    for (int k = 0; k < K; ++k) exact += (long double)a[k] * b[k];
+    const long double scale = std::ldexp(1.0L, (ea - 1023) + (eb - 1023) + 1);
+    const double rel = (double)(std::fabs(got - exact) / scale);
+    worst8 = std::max(worst8, rel);
+    CHECK(rel < (K + 1) * std::ldexp(1.0, -54), "8: dot product error %.3g of the scale (K = %d)", rel, K);
+  }
+  std::printf("eight slices: worst dot-product error / (row max * column max) = %.3g (2^%.1f)\n", worst8,
+              std::log2(worst8));
 
   std::printf("ok (%d failures)\n", failures);
   return failures ? 1 : 0;

@@ -2,11 +2,21 @@
 
 Sizes span several shared-memory tiles (a tile is 2^10 amplitudes) and ragged
 cases (states with fewer free qubits than a tile, gates with no free qubits
-at all).  Tolerances: complex128 single operations 1e-13 absolute (amplitudes
-are at most 1 in modulus), circuits 1e-12 per 1000 operations; complex64
-single operations 2e-6 absolute, circuits scaled by the number of operations.
-Integer-valued results (which amplitudes an operation touches) are checked
-exactly through the parity of untouched amplitudes.
+at all).  Integer-valued results (which amplitudes an operation touches) are
+checked exactly through the parity of untouched amplitudes.
+
+Tolerances (amplitudes are at most 1 in modulus):
+* complex128, block fixed point (the default) and native FP64: 1e-14 absolute
+  per operation.  One output of either is within a few units of 2^-53 of the
+  largest amplitude it combines (fixed point: 2^-53 |y| + 2^-55 max|x| max|m|
+  for K <= 4 terms; 8-slice dense gates (K + 1) 2^-54 of the row and column
+  maxima), and so is the oracle's own FP64 result; 1e-14 leaves a factor of
+  about 10 over 2^-53 for the K <= 64 terms of a 6-target gate.  Circuits of
+  300-500 operations: 2e-14 (errors of successive unitary operations add at
+  most, and mostly cancel).
+* complex128, double-float (47-bit): 1e-13 per operation, 1e-12 per 1000
+  operations.
+* complex64: 2e-6 per operation, circuits scaled by the number of operations.
 """
 
 import numpy as np
@@ -17,9 +27,14 @@ from paper_2311_01512_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-# precision modes: 1 = complex128 with the default double-float arithmetic,
-# 2 = complex128 with native FP64 arithmetic, 0 = complex64
-ATOL = {1: 1e-13, 2: 1e-13, 0: 2e-6}
+# precision modes: 1 = complex128 with the default block fixed-point arithmetic,
+# 3 = complex128 with double-float, 2 = complex128 with native FP64, 0 = complex64
+ATOL = {1: 1e-14, 3: 1e-13, 2: 1e-14, 0: 2e-6}
+# scalar results (norm, trace, expectation values) per unit of sum |h| or of
+# the trace
+STOL = {1: 1e-14, 3: 1e-12, 2: 1e-14, 0: 1e-5}
+# circuits of 300-500 operations, max |delta amp|
+CTOL = {1: 2e-14, 3: 0.5e-12, 2: 2e-14}
 
 
 @pytest.fixture(scope="module")
@@ -32,6 +47,8 @@ def make_state(qs, nq, density, mode):
     st = qs.State(nq, density=density, prec=0 if mode == 0 else 1)
     if mode == 2:
         qs.qs_set_arithmetic(st.handle, qs.QS_ARITH_F64)
+    if mode == 3:
+        qs.qs_set_arithmetic(st.handle, qs.QS_ARITH_DF)
     return st
 
 
@@ -58,7 +75,7 @@ def close(got, want, prec, scale=1.0):
     return err
 
 
-PRECS = [1, 2, 0]
+PRECS = [1, 3, 2, 0]
 
 
 # ---------------------------------------------------------------------------
@@ -168,11 +185,11 @@ def test_norm_and_statevector_expectation(qs, prec):
     psi = wl.random_statevector(nq, rng) * 0.7
     st = new_sv(qs, nq, prec, psi)
     norm = qs.qs_calc_norm_or_trace(st.handle)
-    assert abs(norm - orc.calc_norm(psi)) < (1e-13 if prec else 1e-6)
+    assert abs(norm - orc.calc_norm(psi)) < STOL[prec]
     paulis, coeffs = wl.random_pauli_sum(nq, 13, rng)
     got = qs.qs_expec_pauli_sum(st.handle, paulis, coeffs)
     want = orc.expec_pauli_sum_statevector(psi, paulis, coeffs)
-    assert abs(got - want) < (1e-12 if prec else 1e-5)
+    assert abs(got - want) < STOL[prec] * np.abs(coeffs).sum()
     # terms that share flip masks (grouped by the kernel), diagonal runs, masks whose
     # highest bit is below and above a warp's index span, and repeated strings
     base = wl.random_pauli_sum(nq, 6, rng)[0]
@@ -187,7 +204,7 @@ def test_norm_and_statevector_expectation(qs, prec):
     coeffs2 = rng.standard_normal(len(rows))
     got = qs.qs_expec_pauli_sum(st.handle, paulis2, coeffs2)
     want = orc.expec_pauli_sum_statevector(psi, paulis2, coeffs2)
-    assert abs(got - want) < (1e-12 if prec else 1e-5) * np.abs(coeffs2).sum()
+    assert abs(got - want) < STOL[prec] * np.abs(coeffs2).sum()
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -208,10 +225,10 @@ def test_statevector_expectation_many_diagonal_terms(qs, prec, nq):
     coeffs = rng.standard_normal(len(paulis))
     got = qs.qs_expec_pauli_sum(st.handle, paulis, coeffs)
     want = orc.expec_pauli_sum_statevector(psi, paulis, coeffs)
-    assert abs(got - want) < (1e-12 if prec else 1e-5) * np.abs(coeffs).sum()
+    assert abs(got - want) < STOL[prec] * np.abs(coeffs).sum()
     got_d = qs.qs_expec_pauli_sum(st.handle, zs, coeffs[:40])
     want_d = orc.expec_pauli_sum_statevector(psi, zs, coeffs[:40])
-    assert abs(got_d - want_d) < (1e-12 if prec else 1e-5) * np.abs(coeffs[:40]).sum()
+    assert abs(got_d - want_d) < STOL[prec] * np.abs(coeffs[:40]).sum()
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -226,12 +243,12 @@ def test_statevector_circuit(qs, prec):
         qs.apply_op(st.handle, op)
     want = orc.run_ops(psi, ops, is_density=False)
     got = st.get_amps()
-    if prec in (1, 2):
+    if prec:
         err = float(np.max(np.abs(got - want)))
-        assert err <= 0.5e-12, err        # 1e-12 per 1000 operations
+        assert err <= CTOL[prec], err
     else:
         close(got, want, prec, scale=50)
-    assert abs(qs.qs_calc_norm_or_trace(st.handle) - 1.0) < (1e-12 if prec else 1e-4)
+    assert abs(qs.qs_calc_norm_or_trace(st.handle) - 1.0) < (50 * STOL[prec] if prec else 1e-4)
 
 
 # ---------------------------------------------------------------------------
@@ -252,7 +269,7 @@ def test_densmatr_init_pure_and_trace(qs, prec):
     want = sum(wi * orc.densmatr_from_pure(s) for wi, s in zip(w, states))
     close(dm.get_amps(), want, prec)
     tr = qs.qs_calc_norm_or_trace(dm.handle)
-    assert abs(tr - orc.calc_trace(want)) < (1e-13 if prec else 1e-6)
+    assert abs(tr - orc.calc_trace(want)) < STOL[prec]
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -334,7 +351,7 @@ def test_channels(qs, prec, name, gpu_fn, orc_fn, nt):
         want = orc_fn(want, t, p)
     close(dm.get_amps(), want, prec, scale=4)
     tr = qs.qs_calc_norm_or_trace(dm.handle)
-    assert abs(tr - orc.calc_trace(want)) < (1e-13 if prec else 1e-5)
+    assert abs(tr - orc.calc_trace(want)) < STOL[prec]
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -358,7 +375,7 @@ def test_densmatr_expectation(qs, prec):
     paulis, coeffs = wl.random_pauli_sum(nq, 20, rng)
     got = qs.qs_expec_pauli_sum(dm.handle, paulis, coeffs)
     want = orc.expec_pauli_sum_densmatr(beta, paulis, coeffs)
-    assert abs(got - want) < (1e-13 if prec else 1e-5)
+    assert abs(got - want) < STOL[prec] * np.abs(coeffs).sum()
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -386,10 +403,10 @@ def test_small_density_workload(qs, prec):
     want = orc.run_ops(beta, ops, is_density=True)
     want_red = orc.partial_trace(want, traced)
     want_e = orc.expec_pauli_sum_densmatr(want_red, paulis, coeffs)
-    if prec in (1, 2):
-        assert float(np.max(np.abs(dm.get_amps() - want))) <= 0.3e-12
-        assert float(np.max(np.abs(red.get_amps() - want_red))) <= 0.3e-12
-        assert abs(got_e - want_e) <= 1e-12
+    if prec:
+        assert float(np.max(np.abs(dm.get_amps() - want))) <= CTOL[prec]
+        assert float(np.max(np.abs(red.get_amps() - want_red))) <= CTOL[prec]
+        assert abs(got_e - want_e) <= 2 * CTOL[prec] * np.abs(coeffs).sum()
     else:
         close(dm.get_amps(), want, prec, scale=100)
         assert abs(got_e - want_e) <= 1e-4
@@ -477,10 +494,12 @@ def test_tensor_core_gate_matches_cuda_cores(qs, nq, n, s, place):
                                      (3, 2, 0), (4, 2, 1), (9, 2, 3), (13, 2, 0), (16, 5, 1), (17, 3, 1)])
 @pytest.mark.parametrize("kind", ["haar", "wide", "sparse"])
 @pytest.mark.parametrize("place", ["random", "lowest", "highest"])
-def test_complex128_tensor_core_gate(qs, nq, n, s, kind, place):
+@pytest.mark.parametrize("arith", ["fx", "df"])
+def test_complex128_tensor_core_gate(qs, nq, n, s, kind, place, arith):
     """Against the oracle and the CUDA-core double-float kernel.  'wide' uses a
     non-unitary matrix whose entries span 1e-8..1e3 (row and column scaling),
-    'sparse' a state that is zero on most groups (all-zero tile rows).  Two
+    'sparse' a state that is zero on most groups (all-zero tile rows).  Block
+    fixed point runs eight slices (56-bit operands), double-float seven.  Two
     targets run on the three-target kernel with an identity on a free qubit;
     (3, 2, 0) and (4, 2, 1) leave a single free qubit, so the tile has one row."""
     rng = np.random.default_rng(900 + 31 * nq + 7 * n + s + len(kind) + 3 * len(place))
@@ -501,13 +520,17 @@ def test_complex128_tensor_core_gate(qs, nq, n, s, kind, place):
     outs = {}
     for tc in (0, 1):
         st = qs.State(nq, prec=1)
+        qs.qs_set_arithmetic(st.handle, qs.QS_ARITH_FX if arith == "fx" else qs.QS_ARITH_DF)
         qs.qs_set_tensor_cores(st.handle, tc)
         st.set_amps(psi)
         qs.qs_apply_ctrl_multi_target(st.handle, ctrls, targs, mat)
         qs.qs_synchronize(st.handle)
         outs[tc] = st.get_amps()
-    # error bound of a dot product: a few 2^-46 of sum |m| |x| over its terms
-    bound = 2.0 ** -44 * (np.abs(mat).max() * (1 << n) * np.abs(psi).max()) + 1e-300
+    # error bound of a dot product over K = 2^(n+1) real terms: (K + 1) 2^-54
+    # (eight slices) or 2^-47 (seven) of the row and column maxima, here
+    # bounded by 2^n max|m| max|psi| times 2^-51 or 2^-44
+    ex = -51 if arith == "fx" else -44
+    bound = 2.0 ** ex * (np.abs(mat).max() * (1 << n) * np.abs(psi).max()) + 1e-300
     for tc in (0, 1):
         err = float(np.max(np.abs(outs[tc] - want)))
         assert err <= bound, (tc, err, bound)
