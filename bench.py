@@ -31,7 +31,7 @@ UNIT = "gates/s"
 NUM_OPS = 500
 CIRCUIT_TAG = "sv30-circuit"
 STATE_SEED = 2311015121
-CPU_SAMPLE_QUBITS = 26
+CPU_SAMPLE_QUBITS = 20
 ARITH_CODE = {"fx": 2, "df": 0, "f64": 1}     # qs_arith
 DTYPE = {
     "fx": ("c128 storage; arithmetic at least FP64: one-target gates, diagonals and gadgets in 60-bit block "
@@ -122,7 +122,33 @@ def config_dict(nq, args):
 # CPU oracle sample (runs in a fresh process; never imports torch or CUDA)
 # ---------------------------------------------------------------------------
 
+def host_cpu_info():
+    """nproc and the CPU model of this host (from /proc/cpuinfo or lscpu)."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.startswith("Model name:"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"nproc": os.cpu_count(), "model": model or platform.machine(), "arch": platform.machine()}
+
+
 def cpu_sample_main(num_ops):
+    """The oracle on the first num_ops operations of the circuit recipe (all
+    500: the whole circuit) at CPU_SAMPLE_QUBITS, one thread."""
     import numpy as np
     from oracle import qsim_oracle as orc
     from paper_2311_01512_gb300 import workloads as wl
@@ -133,28 +159,32 @@ def cpu_sample_main(num_ops):
     psi = orc.run_ops(psi, ops, is_density=False)
     dt = time.perf_counter() - t0
     scale = 2.0 ** (nq - 30)
-    print(json.dumps({"ops": num_ops, "seconds": dt, "qubits": nq,
-                      "value_30q_equiv": num_ops / dt * scale,
+    print(json.dumps({"ops": len(ops), "seconds": dt, "qubits": nq,
+                      "value_30q_equiv": len(ops) / dt * scale,
                       "norm": float(np.sum(np.abs(psi) ** 2))}))
 
 
-def run_cpu_sample(num_ops):
+def one_thread_env():
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[k] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
+    return env
+
+
+def run_cpu_sample(num_ops):
     out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(num_ops)],
-                         capture_output=True, text=True, env=env, cwd=ROOT, timeout=900)
+                         capture_output=True, text=True, env=one_thread_env(), cwd=ROOT, timeout=900)
     if out.returncode != 0:
         raise RuntimeError("cpu sample failed: " + out.stderr[-2000:])
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline_dict(res):
+def cpu_baseline_dict(res, sample):
+    info = host_cpu_info()
     return {"value": res["value_30q_equiv"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "first %d ops of the same circuit recipe on a %d-qubit complex128 state "
-                      "(%.1f s, one thread); gates/s scaled to 30 qubits by 2^(%d-30)"
-                      % (res["ops"], res["qubits"], res["seconds"], res["qubits"])}
+            "host_nproc": info["nproc"], "host_cpu": info["model"], "host_arch": info["arch"],
+            "sample": sample}
 
 
 # ---------------------------------------------------------------------------
@@ -282,7 +312,7 @@ def main_ours(args):
     world, rank, local = dist_setup(args)
     cpu_res = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu_res = run_cpu_sample(6)       # before the first GPU call; a separate process
+        cpu_res = run_cpu_sample(NUM_OPS)   # before the first GPU call; a separate process
     import torch
     from paper_2311_01512_gb300 import qs
     torch.cuda.set_device(local)
@@ -445,7 +475,11 @@ def main_ours(args):
         if fused is not None:
             line["fused_tc"] = fused
         if cpu_res is not None:
-            line["cpu_baseline"] = cpu_baseline_dict(cpu_res)
+            line["cpu_baseline"] = cpu_baseline_dict(
+                cpu_res, "the whole %d-op circuit of the same recipe on a %d-qubit complex128 state "
+                         "(oracle/qsim_oracle.py, numpy, one thread; %.1f s); gates/s scaled to 30 qubits "
+                         "by 2^(%d-30), the ratio of the bytes each operation streams"
+                % (cpu_res["ops"], cpu_res["qubits"], cpu_res["seconds"], cpu_res["qubits"]))
         print(json.dumps(line), flush=True)
         detail = {f: {"launches": fam_count[f], "ms_total": fam_time[f],
                       "share": fam_time[f] / sum(fam_time.values()),
@@ -574,22 +608,48 @@ def fused_comparison(args, device):
 # Reference arm: the CPU oracle on a bounded sample, on the host cores
 # ---------------------------------------------------------------------------
 
+REF_OPS_PER_STEP = 100
+
+
 def main_reference(args):
+    """The CPU oracle as it stands on the host cores, one thread: the same
+    500-op circuit recipe at CPU_SAMPLE_QUBITS, REF_OPS_PER_STEP successive
+    operations per step (step k applies operations k*100 .. k*100+99 of the
+    circuit, cycling through it), on one evolving state."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    ops_per_step = 3
-    for _ in range(args.warmup):
-        run_cpu_sample(ops_per_step)
-    res = [run_cpu_sample(ops_per_step) for _ in range(args.steps)]
-    secs = sum(r["seconds"] for r in res)
-    value = ops_per_step * args.steps / secs * 2.0 ** (CPU_SAMPLE_QUBITS - 30)
-    cb = cpu_baseline_dict({"ops": ops_per_step * args.steps, "qubits": CPU_SAMPLE_QUBITS,
-                            "seconds": secs, "value_30q_equiv": value})
+    for k, v in one_thread_env().items():
+        os.environ[k] = v
+    from oracle import qsim_oracle as orc
+    from paper_2311_01512_gb300 import workloads as wl
+    nq = CPU_SAMPLE_QUBITS
+    ops = make_ops(nq)
+    psi = wl.random_statevector(nq, wl.rng_for("cpu-sample"))
+    m = REF_OPS_PER_STEP
+
+    def step(k):
+        first = (k * m) % NUM_OPS
+        return orc.run_ops(psi, ops[first:first + m], is_density=False)
+
+    for k in range(args.warmup):
+        psi = step(k)
+    secs = 0.0
+    for k in range(args.warmup, args.warmup + args.steps):
+        t0 = time.perf_counter()
+        psi = step(k)
+        secs += time.perf_counter() - t0
+    value = m * args.steps / secs * 2.0 ** (nq - 30)
+    first_op = (args.warmup * m) % NUM_OPS
+    sample = ("%d timed steps of %d successive operations each (operations %d onward of the %d-op circuit, "
+              "cycling) on a %d-qubit complex128 state after %d warm-up steps; oracle/qsim_oracle.py, numpy, "
+              "one thread, %.1f s; gates/s scaled to 30 qubits by 2^(%d-30)"
+              % (args.steps, m, first_op, NUM_OPS, nq, args.warmup, secs, nq))
+    cb = cpu_baseline_dict({"value_30q_equiv": value}, sample)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (numpy f64)",
             "data": "synthetic", "config": config_dict(30, args), "cpu_baseline": cb,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

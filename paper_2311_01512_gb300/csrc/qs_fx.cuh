@@ -14,13 +14,16 @@
 //     X_k = trunc(x_k 2^(1082 - ex)),   |X_k| < 2^60,
 // exact for every x_k within 7 binades of the largest (the largest itself
 // has 53 significant bits and 7 zero bits below them), truncated toward zero
-// by less than one unit 2^(ex - 1082) otherwise.  Zeros and subnormals
-// (biased exponent 0) become 0.  The constants of a row group (gate-matrix
-// entries, cos/sin of a gadget, channel coefficients) share their largest
-// biased exponent em in the same way, rounded to nearest on the host:
-//     M = round(m 2^(1082 - em)),   |M| <= 2^60.
-// Every integer is split as X = h 2^30 + l with h = floor(X / 2^30) in
-// [-2^30, 2^30) and l = X mod 2^30 in [0, 2^30).
+// by less than one unit 2^(ex - 1082) otherwise.  Subnormals (below
+// 2^-1022) carry an error of at most their own size.  The constants of a row
+// group (gate-matrix entries, cos/sin of a gadget, channel coefficients) share
+// their largest biased exponent em in the same way, rounded to nearest on the
+// host:
+//     M = round(m 2^(1082 - em)),   |M| < 2^60.
+// Every integer is split into two 30-bit parts, X = h 2^30 + l: a constant as
+// h = floor(M / 2^30) in [-2^30, 2^30), l = M mod 2^30 in [0, 2^30); an
+// amplitude's integer as its magnitude's parts, both carrying its sign
+// (|h|, |l| < 2^30).  Every product of parts is below 2^60 in magnitude.
 //
 // Products.  x m = X M 2^(ex + em - 2164) and
 //     X M = h_x h_m 2^60 + (h_x l_m + l_x h_m) 2^30 + l_x l_m.
@@ -56,7 +59,7 @@ constexpr int kShift = 1082;   // x = X 2^(ex - kShift)
 constexpr int kFinish = 2104;  // y = V 2^(ex + em - kFinish)
 
 struct Part {
-  int32_t h, l;   // X = h 2^30 + l, 0 <= l < 2^30
+  int32_t h, l;   // X = h 2^30 + l, |h|, |l| <= 2^30
 };
 
 // 64-bit accumulators A (h h) and B (cross terms).
@@ -79,14 +82,35 @@ QS_HD Part split64(int64_t X) {
   return p;
 }
 
-// x (words hw:lw) in the block of largest biased exponent ex >= its own.
+QS_HD uint64_t shr_u64(uint64_t x, uint32_t d) {
+#if defined(__CUDA_ARCH__)
+  uint64_t r;
+  asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(d));   // amounts above 63 give 0
+  return r;
+#else
+  return d > 63 ? 0ull : x >> d;
+#endif
+}
+
+// x (words hw:lw, exponent field ef = hw & 0x7FF00000) in the block whose
+// largest exponent field is exf >= ef.  The sign is kept on both parts
+// (|h|, |l| < 2^30; the product bounds are those of the floor split).  A zero
+// gets no implicit bit; a subnormal is read with exponent 0 instead of 1 (half
+// its value; it only matters when the whole block is below 2^-964).
+QS_HD Part fixed_f(uint32_t hw, uint32_t lw, uint32_t ef, uint32_t exf) {
+  const uint32_t hid = ef < 0x100000u ? ef : 0x100000u;   // implicit bit, none for zeros
+  const uint64_t m = ((uint64_t)((hw & 0xFFFFFu) | hid) << 39) | ((uint64_t)lw << 7);
+  const uint64_t mag = shr_u64(m, (exf - ef) >> 20);
+  const int32_t sg = ((int32_t)hw >> 31) | 1;             // +1 or -1
+  Part p;
+  p.h = (int32_t)(uint32_t)(mag >> 30) * sg;
+  p.l = (int32_t)((uint32_t)mag & 0x3FFFFFFFu) * sg;
+  return p;
+}
+
+// x in the block of largest biased exponent ex >= its own.
 QS_HD Part fixed(uint32_t hw, uint32_t lw, int ex) {
-  const int e = expo(hw);
-  const uint64_t m = ((uint64_t)((hw & 0xFFFFFu) | 0x100000u) << 39) | ((uint64_t)lw << 7);
-  const int d = ex - e;
-  const uint64_t mag = (d < 60 && e != 0) ? (m >> d) : 0ull;
-  const int64_t X = (int32_t)hw < 0 ? -(int64_t)mag : (int64_t)mag;
-  return split64(X);
+  return fixed_f(hw, lw, hw & 0x7FF00000u, (uint32_t)ex << 20);
 }
 
 QS_HD Part fixed_d(double x, int ex) {
@@ -151,17 +175,33 @@ QS_HD double i64_to_double(int64_t v) {
 #endif
 }
 
-// The accumulated sum as a double: V rounded once, times 2^(ex + em - 2104)
-// (an exponent-field increment; results below the normal range flush to 0).
-QS_HD double finish(const Acc& a, int ex, int em) {
+// Scaling of an output block: y = V 2^sc, sc = ex + em - 2104, applied as an
+// exponent-field increment inc = sc 2^20 to the rounded V; results whose
+// exponent field would fall to 0 or below (|y| < 2^-1022) are flushed to 0,
+// which the single test |hw| > thr does (thr = max(-sc, 0) 2^20 + 2^20 - 1;
+// it also keeps V = 0 at 0).
+struct Scale {
+  uint32_t inc, thr;
+};
+QS_HD Scale scale_for(int ex, int em) {
+  const int sc = ex + em - kFinish;
+  Scale s;
+  s.inc = (uint32_t)sc * (1u << 20);
+  const int under = sc < 0 ? (-sc < 2047 ? -sc : 2047) : 0;
+  s.thr = ((uint32_t)under << 20) | 0xFFFFFu;
+  return s;
+}
+
+QS_HD double finish_s(const Acc& a, Scale s) {
   const double r = i64_to_double(acc_value(a));
   uint32_t hw, lw;
   qsdf::d2w(r, hw, lw);
-  const int sc = ex + em - kFinish;
-  const int f = expo(hw);
-  if (f == 0 || f + sc <= 0) return 0.0;
-  return qsdf::w2d(hw + (uint32_t)sc * (1u << 20), lw);
+  const bool ok = (hw & 0x7FFFFFFFu) > s.thr;
+  return qsdf::w2d(ok ? hw + s.inc : 0u, ok ? lw : 0u);
 }
+
+// The accumulated sum as a double: V rounded once, times 2^(ex + em - 2104).
+QS_HD double finish(const Acc& a, int ex, int em) { return finish_s(a, scale_for(ex, em)); }
 
 // Largest biased exponent of a set of doubles (exponent fields compared in
 // place, on the high words).

@@ -15,34 +15,42 @@ namespace {
 
 __device__ __forceinline__ Part part(const FxPart& p) { return Part{p.h, p.l}; }
 
-__device__ __forceinline__ uint32_t efield(double x) { return (uint32_t)__double2hiint(x) & 0x7FF00000u; }
-__device__ __forceinline__ int ex_of(double2 v) { return (int)(max(efield(v.x), efield(v.y)) >> 20); }
-__device__ __forceinline__ int ex_of(double2 a, double2 b) {
-  return (int)(max(max(efield(a.x), efield(a.y)), max(efield(b.x), efield(b.y))) >> 20);
+// the words of a double and its exponent field (hw & 0x7FF00000)
+struct Wd {
+  uint32_t hw, lw, ef;
+};
+__device__ __forceinline__ Wd words(double x) {
+  Wd w;
+  w.hw = (uint32_t)__double2hiint(x);
+  w.lw = (uint32_t)__double2loint(x);
+  w.ef = w.hw & 0x7FF00000u;
+  return w;
 }
+__device__ __forceinline__ Part fx(const Wd& w, uint32_t exf) { return qsfx::fixed_f(w.hw, w.lw, w.ef, exf); }
 
 struct CPart {
   Part re, im;
 };
-__device__ __forceinline__ CPart cfixed(double2 v, int ex) {
-  return CPart{qsfx::fixed_d(v.x, ex), qsfx::fixed_d(v.y, ex)};
-}
+// a complex amplitude in the block of exponent field exf
+__device__ __forceinline__ CPart cfx(const Wd& r, const Wd& i, uint32_t exf) { return CPart{fx(r, exf), fx(i, exf)}; }
+__device__ __forceinline__ uint32_t emax2(const Wd& a, const Wd& b) { return max(a.ef, b.ef); }
 
-__device__ __forceinline__ double lin1(Part x, Part f, int ex, int em) {
+__device__ __forceinline__ double lin1(Part x, Part f, qsfx::Scale sc) {
   Acc a = qsfx::acc_zero();
   qsfx::mac(a, x, f);
-  return qsfx::finish(a, ex, em);
+  return qsfx::finish_s(a, sc);
 }
-__device__ __forceinline__ double lin2(Part x0, Part f0, Part x1, Part f1, int ex, int em) {
+__device__ __forceinline__ double lin2(Part x0, Part f0, Part x1, Part f1, qsfx::Scale sc) {
   Acc a = qsfx::acc_zero();
   qsfx::mac(a, x0, f0);
   qsfx::mac(a, x1, f1);
-  return qsfx::finish(a, ex, em);
+  return qsfx::finish_s(a, sc);
 }
 
 // c x for a complex constant c = (re, im, -im parts) and a complex value x
-__device__ __forceinline__ double2 cmul(const Part& cr, const Part& ci, const Part& nci, const CPart& x, int ex, int em) {
-  return make_double2(lin2(x.re, cr, x.im, nci, ex, em), lin2(x.re, ci, x.im, cr, ex, em));
+__device__ __forceinline__ double2 cmul(const Part& cr, const Part& ci, const Part& nci, const CPart& x,
+                                        qsfx::Scale sc) {
+  return make_double2(lin2(x.re, cr, x.im, nci, sc), lin2(x.re, ci, x.im, cr, sc));
 }
 
 }  // namespace
@@ -54,6 +62,8 @@ __device__ __forceinline__ double2 cmul(const Part& cr, const Part& ci, const Pa
 //   alpha_i0 -> m00 alpha_i0 + m01 alpha_i1,  alpha_i1 -> m10 alpha_i0 + m11 alpha_i1,
 // as four real rows over (Re a, Im a, Re b, Im b), the pair sharing one exponent.
 // ---------------------------------------------------------------------------
+// SINGLE: no controls (one zero bit inserted at t).
+template <bool SINGLE>
 __global__ void __launch_bounds__(256) k_gate1_fx(double2* __restrict__ psi, const __grid_constant__ Gate1FxParams p) {
   Part m[4][4];
 #pragma unroll
@@ -63,18 +73,21 @@ __global__ void __launch_bounds__(256) k_gate1_fx(double2* __restrict__ psi, con
   const uint64_t tbit = 1ull << p.t;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < p.npairs; k += stride) {
-    const uint64_t i0 = insert_zeros(k, p.ins, p.nins) | p.ctrl_mask;
+    const uint64_t i0 = SINGLE ? insert_zero(k, p.t) : (insert_zeros(k, p.ins, p.nins) | p.ctrl_mask);
     const uint64_t i1 = i0 | tbit;
     const double2 a = psi[i0], b = psi[i1];
-    const int ex = ex_of(a, b);
-    const Part x[4] = {qsfx::fixed_d(a.x, ex), qsfx::fixed_d(a.y, ex), qsfx::fixed_d(b.x, ex), qsfx::fixed_d(b.y, ex)};
+    const Wd w[4] = {words(a.x), words(a.y), words(b.x), words(b.y)};
+    const uint32_t exf = max(emax2(w[0], w[1]), emax2(w[2], w[3]));
+    const Part x[4] = {fx(w[0], exf), fx(w[1], exf), fx(w[2], exf), fx(w[3], exf)};
+    const int ex = (int)(exf >> 20);
+    const qsfx::Scale sc[2] = {qsfx::scale_for(ex, p.em[0]), qsfx::scale_for(ex, p.em[1])};
     double y[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       Acc acc = qsfx::acc_zero();
 #pragma unroll
       for (int c = 0; c < 4; ++c) qsfx::mac(acc, x[c], m[r][c]);
-      y[r] = qsfx::finish(acc, ex, p.em[r >> 1]);
+      y[r] = qsfx::finish_s(acc, sc[r >> 1]);
     }
     psi[i0] = make_double2(y[0], y[1]);
     psi[i1] = make_double2(y[2], y[3]);
@@ -93,9 +106,10 @@ __global__ void __launch_bounds__(256) k_diag_fx(double2* __restrict__ psi, cons
     int j = 0;
     for (int q = 0; q < p.n; ++q) j |= (int)((i >> p.tpos[q]) & 1) << q;
     const double2 v = psi[i];
-    const int ex = ex_of(v);
+    const Wd wr = words(v.x), wi = words(v.y);
+    const uint32_t exf = emax2(wr, wi);
     const DiagFxEntry e = d[j];
-    psi[i] = cmul(part(e.re), part(e.im), part(e.nim), cfixed(v, ex), ex, e.em);
+    psi[i] = cmul(part(e.re), part(e.im), part(e.nim), cfx(wr, wi, exf), qsfx::scale_for((int)(exf >> 20), e.em));
   }
 }
 
@@ -111,21 +125,24 @@ __global__ void __launch_bounds__(256) k_gadget_fx(double2* __restrict__ psi, co
   // i^q (re, im) = (sr * (odd ? im : re), si * (odd ? re : im))
   const bool odd = q & 1;
   const bool neg_re = q == 1 || q == 2, neg_im = q == 2 || q == 3;
+  const bool pxy = parity64(p.xy & p.yz);     // parity(j & yz) = parity(i & yz) xor this
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < p.nwork; k += stride) {
     const uint64_t i = insert_zero(k, p.h);
     const uint64_t j = i ^ p.xy;
     const double2 va = psi[i], vb = psi[j];
-    const int ex = ex_of(va, vb);
-    const CPart a = cfixed(va, ex), b = cfixed(vb, ex);
-    const bool pj = parity64(j & p.yz), pi = parity64(i & p.yz);
+    const Wd w[4] = {words(va.x), words(va.y), words(vb.x), words(vb.y)};
+    const uint32_t exf = max(emax2(w[0], w[1]), emax2(w[2], w[3]));
+    const CPart a = cfx(w[0], w[1], exf), b = cfx(w[2], w[3], exf);
+    const qsfx::Scale sc = qsfx::scale_for((int)(exf >> 20), p.em);
+    const bool pi = parity64(i & p.yz), pj = pi != pxy;
     // output i: c a + s_j (i^q b)
     const Part bre = odd ? b.im : b.re, bim = odd ? b.re : b.im;
     const Part are = odd ? a.im : a.re, aim = odd ? a.re : a.im;
-    const double2 oi = make_double2(lin2(a.re, c, bre, (pj != neg_re) ? ns : s, ex, p.em),
-                                    lin2(a.im, c, bim, (pj != neg_im) ? ns : s, ex, p.em));
-    const double2 oj = make_double2(lin2(b.re, c, are, (pi != neg_re) ? ns : s, ex, p.em),
-                                    lin2(b.im, c, aim, (pi != neg_im) ? ns : s, ex, p.em));
+    const double2 oi = make_double2(lin2(a.re, c, bre, (pj != neg_re) ? ns : s, sc),
+                                    lin2(a.im, c, bim, (pj != neg_im) ? ns : s, sc));
+    const double2 oj = make_double2(lin2(b.re, c, are, (pi != neg_re) ? ns : s, sc),
+                                    lin2(b.im, c, aim, (pi != neg_im) ? ns : s, sc));
     psi[i] = oi;
     psi[j] = oj;
   }
@@ -137,10 +154,11 @@ __global__ void __launch_bounds__(256) k_phase_fx(double2* __restrict__ psi, con
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.nwork; i += stride) {
     const double2 v = psi[i];
-    const int ex = ex_of(v);
+    const Wd wr = words(v.x), wi = words(v.y);
+    const uint32_t exf = emax2(wr, wi);
     const bool odd = parity64(i & p.yz);
     const Part si = odd ? ns : s, nsi = odd ? s : ns;
-    psi[i] = cmul(c, si, nsi, cfixed(v, ex), ex, p.em);
+    psi[i] = cmul(c, si, nsi, cfx(wr, wi, exf), qsfx::scale_for((int)(exf >> 20), p.em));
   }
 }
 
@@ -170,27 +188,34 @@ __global__ void __launch_bounds__(256) k_group_fx(double2* __restrict__ rho, con
       const uint64_t b0 = 1ull << p.mpos[0], b1 = 1ull << p.mpos[1];
       const uint64_t i00 = base, i01 = base | b0, i10 = base | b1, i11 = base | b0 | b1;
       const double2 va = rho[i00], vb = rho[i01], vc = rho[i10], vd = rho[i11];
-      const int ead = ex_of(va, vd);
-      const CPart a = cfixed(va, ead), d = cfixed(vd, ead);
+      const Wd ar = words(va.x), ai = words(va.y), br = words(vb.x), bi = words(vb.y);
+      const Wd cr = words(vc.x), ci = words(vc.y), dr = words(vd.x), di = words(vd.y);
+      const uint32_t ead = max(emax2(ar, ai), emax2(dr, di));
+      const CPart a = cfx(ar, ai, ead), d = cfx(dr, di, ead);
+      const qsfx::Scale s0 = qsfx::scale_for((int)(ead >> 20), p.em[0]);
       if (OP == G_DAMP) {
-        rho[i00] = make_double2(lin2(a.re, f[0], d.re, f[1], ead, p.em[0]), lin2(a.im, f[0], d.im, f[1], ead, p.em[0]));
-        const int ed = ex_of(vd);
-        const CPart dd = cfixed(vd, ed);
-        rho[i11] = make_double2(lin1(dd.re, f[3], ed, p.em[3]), lin1(dd.im, f[3], ed, p.em[3]));
+        rho[i00] = make_double2(lin2(a.re, f[0], d.re, f[1], s0), lin2(a.im, f[0], d.im, f[1], s0));
+        const uint32_t ed = emax2(dr, di);
+        const CPart dd = cfx(dr, di, ed);
+        const qsfx::Scale s3 = qsfx::scale_for((int)(ed >> 20), p.em[3]);
+        rho[i11] = make_double2(lin1(dd.re, f[3], s3), lin1(dd.im, f[3], s3));
       } else {
-        rho[i00] = make_double2(lin2(a.re, f[0], d.re, f[1], ead, p.em[0]), lin2(a.im, f[0], d.im, f[1], ead, p.em[0]));
-        rho[i11] = make_double2(lin2(d.re, f[0], a.re, f[1], ead, p.em[0]), lin2(d.im, f[0], a.im, f[1], ead, p.em[0]));
+        rho[i00] = make_double2(lin2(a.re, f[0], d.re, f[1], s0), lin2(a.im, f[0], d.im, f[1], s0));
+        rho[i11] = make_double2(lin2(d.re, f[0], a.re, f[1], s0), lin2(d.im, f[0], a.im, f[1], s0));
       }
       if (OP == G_PAULI1) {
-        const int ebc = ex_of(vb, vc);
-        const CPart b = cfixed(vb, ebc), c = cfixed(vc, ebc);
-        rho[i01] = make_double2(lin2(b.re, f[2], c.re, f[3], ebc, p.em[2]), lin2(b.im, f[2], c.im, f[3], ebc, p.em[2]));
-        rho[i10] = make_double2(lin2(c.re, f[2], b.re, f[3], ebc, p.em[2]), lin2(c.im, f[2], b.im, f[3], ebc, p.em[2]));
+        const uint32_t ebc = max(emax2(br, bi), emax2(cr, ci));
+        const CPart b = cfx(br, bi, ebc), c = cfx(cr, ci, ebc);
+        const qsfx::Scale s2 = qsfx::scale_for((int)(ebc >> 20), p.em[2]);
+        rho[i01] = make_double2(lin2(b.re, f[2], c.re, f[3], s2), lin2(b.im, f[2], c.im, f[3], s2));
+        rho[i10] = make_double2(lin2(c.re, f[2], b.re, f[3], s2), lin2(c.im, f[2], b.im, f[3], s2));
       } else {
-        const int eb = ex_of(vb), ec = ex_of(vc);
-        const CPart b = cfixed(vb, eb), c = cfixed(vc, ec);
-        rho[i01] = make_double2(lin1(b.re, f[2], eb, p.em[2]), lin1(b.im, f[2], eb, p.em[2]));
-        rho[i10] = make_double2(lin1(c.re, f[2], ec, p.em[2]), lin1(c.im, f[2], ec, p.em[2]));
+        const uint32_t eb = emax2(br, bi), ec = emax2(cr, ci);
+        const CPart b = cfx(br, bi, eb), c = cfx(cr, ci, ec);
+        const qsfx::Scale sb = qsfx::scale_for((int)(eb >> 20), p.em[2]);
+        const qsfx::Scale sc = qsfx::scale_for((int)(ec >> 20), p.em[2]);
+        rho[i01] = make_double2(lin1(b.re, f[2], sb), lin1(b.im, f[2], sb));
+        rho[i10] = make_double2(lin1(c.re, f[2], sc), lin1(c.im, f[2], sc));
       }
     } else {  // two-qubit depolarising
       uint64_t idx[16];
@@ -202,12 +227,20 @@ __global__ void __launch_bounds__(256) k_group_fx(double2* __restrict__ rho, con
           if ((m >> bb) & 1) v |= 1ull << p.mpos[bb];
         idx[m] = v;
       }
-      const double2 w[4] = {rho[idx[0]], rho[idx[5]], rho[idx[10]], rho[idx[15]]};
-      const int ex = max(ex_of(w[0], w[1]), ex_of(w[2], w[3]));
+      constexpr int mem[4] = {0, 5, 10, 15};
+      Wd wr[4], wi[4];
+      uint32_t ex = 0;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const double2 v = rho[idx[mem[m]]];
+        wr[m] = words(v.x);
+        wi[m] = words(v.y);
+        ex = max(ex, emax2(wr[m], wi[m]));
+      }
       CPart s[4];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) s[m] = cfixed(w[m], ex);
-      constexpr int mem[4] = {0, 5, 10, 15};
+      for (int m = 0; m < 4; ++m) s[m] = cfx(wr[m], wi[m], ex);
+      const qsfx::Scale s0 = qsfx::scale_for((int)(ex >> 20), p.em[0]);
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         Acc re = qsfx::acc_zero(), im = qsfx::acc_zero();
@@ -219,15 +252,17 @@ __global__ void __launch_bounds__(256) k_group_fx(double2* __restrict__ rho, con
           qsfx::mac(re, s[o].re, f[1]);
           qsfx::mac(im, s[o].im, f[1]);
         }
-        rho[idx[mem[m]]] = make_double2(qsfx::finish(re, ex, p.em[0]), qsfx::finish(im, ex, p.em[0]));
+        rho[idx[mem[m]]] = make_double2(qsfx::finish_s(re, s0), qsfx::finish_s(im, s0));
       }
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
         if (m == 0 || m == 5 || m == 10 || m == 15) continue;
         const double2 v = rho[idx[m]];
-        const int e = ex_of(v);
-        const CPart x = cfixed(v, e);
-        rho[idx[m]] = make_double2(lin1(x.re, f[2], e, p.em[2]), lin1(x.im, f[2], e, p.em[2]));
+        const Wd vr = words(v.x), vi = words(v.y);
+        const uint32_t e = emax2(vr, vi);
+        const CPart x = cfx(vr, vi, e);
+        const qsfx::Scale se = qsfx::scale_for((int)(e >> 20), p.em[2]);
+        rho[idx[m]] = make_double2(lin1(x.re, f[2], se), lin1(x.im, f[2], se));
       }
     }
   }
@@ -238,7 +273,10 @@ __global__ void __launch_bounds__(256) k_group_fx(double2* __restrict__ rho, con
 // ---------------------------------------------------------------------------
 cudaError_t launch_gate1_fx(void* amps, const Gate1FxParams& p, cudaStream_t st) {
   const unsigned g = grid_for(p.npairs, 256, num_sms() * kStreamBlocksPerSM);
-  k_gate1_fx<<<g, 256, 0, st>>>(static_cast<double2*>(amps), p);
+  if (p.nins == 1)
+    k_gate1_fx<true><<<g, 256, 0, st>>>(static_cast<double2*>(amps), p);
+  else
+    k_gate1_fx<false><<<g, 256, 0, st>>>(static_cast<double2*>(amps), p);
   return cudaGetLastError();
 }
 
