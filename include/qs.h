@@ -395,6 +395,25 @@ qs_status qs_batch_compile(qs_batch* batch, int autotune);
 qs_status qs_batch_run(qs_batch* batch);
 qs_status qs_batch_info(const qs_batch* batch, int* threads, int* ctas, int* smem_qubits, long* total_ops);
 
+/* ---------------------------------------------------------------------------
+ * Test hooks (not in the paper).  Failures are made on the host, never on
+ * the GPU.
+ * ------------------------------------------------------------------------ */
+
+/* Make library allocations fail: after this call the next `skip` device or
+ * pinned-host allocations the library makes for itself (handle scratch and
+ * staging ring, recorded-program arenas, circuit matrices, batch tables)
+ * succeed and the `count` after them fail as if out of memory, without
+ * calling CUDA.  The caller then returns QS_ERR_OOM having freed what it had
+ * taken.  count = 0 turns the injection off.  Process-wide; QS_ERR_ARG for
+ * negative arguments. */
+qs_status qs_test_fail_allocations(int skip, int count);
+
+/* Set the handle's device error word, as a tensor-core kernel does when one
+ * of its bounded waits runs out, so that the next qs_synchronize reports
+ * QS_ERR_TIMEOUT (once) and clears it.  Synchronises the stream. */
+qs_status qs_test_set_error_word(qs_state* state);
+
 /* Largest number of terms qs_expec_pauli_sum_noalloc accepts. */
 #define QS_NOALLOC_MAX_TERMS 256
 

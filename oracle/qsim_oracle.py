@@ -639,3 +639,82 @@ def sample_swap(get, t1, t2, out_idx):
     differ = ((idx >> t1) & 1) != ((idx >> t2) & 1)
     src = np.where(differ, idx ^ ((1 << t1) | (1 << t2)), idx)
     return get(src)
+
+
+def _sample_bits(idx, t, nq):
+    """Bits t and t + N of each Choi index in idx (column and row bit of qubit t)."""
+    return (idx >> t) & 1, (idx >> (t + nq)) & 1
+
+
+def sample_densmatr_dephasing(get, nq, t, p, out_idx):
+    """New Choi amplitudes at out_idx after one-qubit dephasing (Sec.
+    "Dephasing channel"): scaled by (1 - 2p) where bits t and t + N differ."""
+    idx = np.asarray(out_idx, dtype=np.int64)
+    lo, hi = _sample_bits(idx, t, nq)
+    return np.where(lo != hi, 1.0 - 2.0 * p, 1.0) * get(idx)
+
+
+def sample_densmatr_two_qubit_dephasing(get, nq, t1, t2, p, out_idx):
+    """Two-qubit dephasing (Sec. "Dephasing channel"): scaled by (1 - 4p/3)
+    where bits t1, t1 + N or bits t2, t2 + N differ."""
+    idx = np.asarray(out_idx, dtype=np.int64)
+    a_lo, a_hi = _sample_bits(idx, t1, nq)
+    b_lo, b_hi = _sample_bits(idx, t2, nq)
+    return np.where((a_lo != a_hi) | (b_lo != b_hi), 1.0 - 4.0 * p / 3.0, 1.0) * get(idx)
+
+
+def sample_densmatr_depolarising(get, nq, t, p, out_idx):
+    """One-qubit depolarising (Sec. "Depolarising channel"): where bits t and
+    t + N agree, (1 - 2p/3) beta_i + (2p/3) beta_{i with both flipped}; where
+    they differ, (1 - 4p/3) beta_i."""
+    idx = np.asarray(out_idx, dtype=np.int64)
+    lo, hi = _sample_bits(idx, t, nq)
+    partner = idx ^ ((1 << t) | (1 << (t + nq)))
+    same = (1.0 - 2.0 * p / 3.0) * get(idx) + (2.0 * p / 3.0) * get(partner)
+    return np.where(lo == hi, same, (1.0 - 4.0 * p / 3.0) * get(idx))
+
+
+def sample_densmatr_two_qubit_depolarising(get, nq, t1, t2, p, out_idx):
+    """Two-qubit depolarising (Sec. "Depolarising channel", the equation):
+    where both bit pairs agree, (1 - 4p/5) beta_i + (4p/15) times the sum of
+    the three partners with one or both pairs flipped; otherwise
+    (1 - 16p/15) beta_i."""
+    idx = np.asarray(out_idx, dtype=np.int64)
+    a_lo, a_hi = _sample_bits(idx, t1, nq)
+    b_lo, b_hi = _sample_bits(idx, t2, nq)
+    f1 = (1 << t1) | (1 << (t1 + nq))
+    f2 = (1 << t2) | (1 << (t2 + nq))
+    mixed = (1.0 - 4.0 * p / 5.0) * get(idx) + (4.0 * p / 15.0) * (get(idx ^ f1) + get(idx ^ f2) + get(idx ^ f1 ^ f2))
+    return np.where((a_lo == a_hi) & (b_lo == b_hi), mixed, (1.0 - 16.0 * p / 15.0) * get(idx))
+
+
+def sample_densmatr_damping(get, nq, t, p, out_idx):
+    """Amplitude damping (Sec. "Damping channel"): bits (t, t + N) = (0, 0):
+    beta_i + p beta_{both flipped}; bits differ: sqrt(1 - p) beta_i; bits
+    (1, 1): (1 - p) beta_i."""
+    idx = np.asarray(out_idx, dtype=np.int64)
+    lo, hi = _sample_bits(idx, t, nq)
+    partner = idx ^ ((1 << t) | (1 << (t + nq)))
+    return np.where((lo == 0) & (hi == 0), get(idx) + p * get(partner),
+                    np.where(lo != hi, np.sqrt(1.0 - p) * get(idx), (1.0 - p) * get(idx)))
+
+
+def sample_densmatr_pauli_channel(get, nq, t, px, py, pz, out_idx):
+    """One-qubit Pauli channel (1 - px - py - pz) rho + px X rho X + py Y rho Y
+    + pz Z rho Z, one output at a time: sigma rho sigma^dagger has Choi
+    amplitudes sigma[r', r] conj(sigma[c', c]) beta_{partner} with
+    (c, r) = bits (t, t + N) of i and the partner's bits (c', r') fixed by
+    sigma's single non-zero entry per row."""
+    idx = np.asarray(out_idx, dtype=np.int64)
+    c, r = _sample_bits(idx, t, nq)
+    out = (1.0 - px - py - pz) * get(idx)
+    both = (1 << t) | (1 << (t + nq))
+    # X: <r|X|r'> = 1 for r' = 1 - r, same for the column
+    out = out + px * get(idx ^ both)
+    # Y: Y[r, 1-r] = -i (r = 0) or i (r = 1); conj(Y[c, 1-c]) = i (c = 0) or -i (c = 1)
+    yr = np.where(r == 0, -1j, 1j)
+    yc = np.where(c == 0, 1j, -1j)
+    out = out + py * yr * yc * get(idx ^ both)
+    # Z: Z[r, r] Z[c, c] = (-1)^(r + c)
+    out = out + pz * np.where(r == c, 1.0, -1.0) * get(idx)
+    return out

@@ -3,6 +3,7 @@
 // amplitudes runs in the CUDA kernels; this file only computes index masks,
 // sorted positions, cos/sin of gadget angles and channel coefficients.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -14,6 +15,7 @@
 #include "qs.h"
 #include "qs_df.cuh"
 #include "qs_fx.cuh"
+#include "qs_alloc.h"
 #include "qs_internal.h"
 
 using qsk::kMaxQ;
@@ -28,6 +30,20 @@ namespace qsapi {
 size_t amp_bytes(qs_prec p) { return p == QS_C128 ? 16 : 8; }
 
 qs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? QS_OK : QS_ERR_CUDA; }
+
+// Injected allocation failures (qs_test_fail_allocations): the next
+// g_alloc_skip allocations succeed, the g_alloc_fail after them fail.
+std::atomic<int> g_alloc_skip{0}, g_alloc_fail{0};
+
+bool injected_failure() {
+  if (g_alloc_fail.load() <= 0) return false;
+  if (g_alloc_skip.load() > 0) {
+    --g_alloc_skip;
+    return false;
+  }
+  --g_alloc_fail;
+  return true;
+}
 
 void release(qs_state* s) {
   if (!s) return;
@@ -55,9 +71,10 @@ qs_status create(int nq, int ns, int is_density, qs_prec prec, void* d_amps, voi
   s->prec = prec;
   s->stream = static_cast<cudaStream_t>(stream);
   const size_t scratch = sizeof(double2) * (qsk::kPartials + 2);
-  if (cudaMalloc(&s->d_partials, scratch) != cudaSuccess || cudaMalloc(&s->d_ring, kRingSlots * kSlotBytes) != cudaSuccess ||
-      cudaMallocHost(&s->h_result, sizeof(double2) * 2) != cudaSuccess ||
-      cudaMallocHost(&s->h_ring, kRingSlots * kSlotBytes) != cudaSuccess) {
+  if (qsalloc::device(reinterpret_cast<void**>(&s->d_partials), scratch) != cudaSuccess ||
+      qsalloc::device(reinterpret_cast<void**>(&s->d_ring), kRingSlots * kSlotBytes) != cudaSuccess ||
+      qsalloc::pinned(reinterpret_cast<void**>(&s->h_result), sizeof(double2) * 2) != cudaSuccess ||
+      qsalloc::pinned(reinterpret_cast<void**>(&s->h_ring), kRingSlots * kSlotBytes) != cudaSuccess) {
     cudaGetLastError();
     release(s);
     return QS_ERR_OOM;
@@ -101,7 +118,7 @@ void* rec_alloc(qs_program* p, size_t bytes) {
   if (p->chunks.empty() || p->used + bytes > p->cap) {
     const size_t cap = std::max<size_t>(bytes, size_t(4) << 20);
     void* c = nullptr;
-    if (cudaMalloc(&c, cap) != cudaSuccess) {
+    if (qsalloc::device(&c, cap) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
@@ -417,8 +434,37 @@ qs_status reduce_to_host(qs_state* s, double* out) {
 
 using namespace qsapi;
 
+cudaError_t qsalloc::device(void** p, size_t bytes) {
+  *p = nullptr;
+  if (injected_failure()) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t qsalloc::pinned(void** p, size_t bytes) {
+  *p = nullptr;
+  if (injected_failure()) return cudaErrorMemoryAllocation;
+  return cudaMallocHost(p, bytes);
+}
+
 
 extern "C" {
+
+qs_status qs_test_fail_allocations(int skip, int count) {
+  if (skip < 0 || count < 0) return QS_ERR_ARG;
+  g_alloc_fail.store(0);
+  g_alloc_skip.store(skip);
+  g_alloc_fail.store(count);
+  return QS_OK;
+}
+
+qs_status qs_test_set_error_word(qs_state* s) {
+  if (!s || s->rec) return QS_ERR_ARG;
+  const int one = 1;
+  if (cudaMemcpyAsync(s->d_err, &one, sizeof(int), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+      cudaStreamSynchronize(s->stream) != cudaSuccess)
+    return QS_ERR_CUDA;
+  return QS_OK;
+}
 
 const char* qs_status_str(qs_status status) {
   switch (status) {

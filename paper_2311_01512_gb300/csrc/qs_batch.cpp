@@ -24,6 +24,7 @@
 
 #include "qs.h"
 #include "qs_handle.h"
+#include "qs_alloc.h"
 #include "qs_internal.h"
 #include "qs_batch_plan.h"
 
@@ -173,9 +174,9 @@ void build_plan(Plan& P, int L, const std::vector<int>& nq, const std::vector<qs
 
 bool upload_plan(Plan& P) {
   const size_t S = P.states.size();
-  if (cudaMalloc(&P.d_states, sizeof(qsk::BatchState) * S) != cudaSuccess ||
-      cudaMalloc(&P.d_segs, sizeof(qsk::BatchSeg) * std::max<size_t>(1, P.segs.size())) != cudaSuccess ||
-      cudaMalloc(&P.d_xlat, sizeof(qsk::BatchXlat) * std::max<size_t>(1, P.xlat.size())) != cudaSuccess) {
+  if (qsalloc::device(reinterpret_cast<void**>(&P.d_states), sizeof(qsk::BatchState) * S) != cudaSuccess ||
+      qsalloc::device(reinterpret_cast<void**>(&P.d_segs), sizeof(qsk::BatchSeg) * std::max<size_t>(1, P.segs.size())) != cudaSuccess ||
+      qsalloc::device(reinterpret_cast<void**>(&P.d_xlat), sizeof(qsk::BatchXlat) * std::max<size_t>(1, P.xlat.size())) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
@@ -407,10 +408,10 @@ qs_status qs_batch_compile(qs_batch* b, int autotune) {
     return ((double)(1ull << b->nq[x]) * (1 + b->progs[x].size())) >
            ((double)(1ull << b->nq[y]) * (1 + b->progs[y].size()));
   });
-  if (cudaMalloc(&b->d_order, sizeof(int) * S) != cudaSuccess ||
-      cudaMalloc(&b->d_ops, sizeof(qsk::BatchOp) * std::max<size_t>(1, ops.size())) != cudaSuccess ||
-      cudaMalloc(&b->d_consts, sizeof(double) * std::max<size_t>(1, consts.size())) != cudaSuccess ||
-      cudaMalloc(&b->d_counter, sizeof(int)) != cudaSuccess) {
+  if (qsalloc::device(reinterpret_cast<void**>(&b->d_order), sizeof(int) * S) != cudaSuccess ||
+      qsalloc::device(reinterpret_cast<void**>(&b->d_ops), sizeof(qsk::BatchOp) * std::max<size_t>(1, ops.size())) != cudaSuccess ||
+      qsalloc::device(reinterpret_cast<void**>(&b->d_consts), sizeof(double) * std::max<size_t>(1, consts.size())) != cudaSuccess ||
+      qsalloc::device(reinterpret_cast<void**>(&b->d_counter), sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     free_device(b);
     return QS_ERR_OOM;

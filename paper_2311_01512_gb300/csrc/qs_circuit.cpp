@@ -19,6 +19,7 @@
 
 #include "qs.h"
 #include "qs_handle.h"
+#include "qs_alloc.h"
 #include "qs_internal.h"
 
 namespace {
@@ -119,10 +120,10 @@ qs_status compose(qs_circuit* c) {
   qsk::ComposeInstr* d_ins = nullptr;
   double* d_data = nullptr;
   qs_status st = QS_OK;
-  if (cudaMalloc(&c->d_mats, out_doubles * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&d_cb, cb.size() * sizeof(qsk::ComposeBlock)) != cudaSuccess ||
-      cudaMalloc(&d_ins, ins.size() * sizeof(qsk::ComposeInstr)) != cudaSuccess ||
-      cudaMalloc(&d_data, std::max<size_t>(1, data.size()) * sizeof(double)) != cudaSuccess) {
+  if (qsalloc::device(reinterpret_cast<void**>(&c->d_mats), out_doubles * sizeof(double)) != cudaSuccess ||
+      qsalloc::device(reinterpret_cast<void**>(&d_cb), cb.size() * sizeof(qsk::ComposeBlock)) != cudaSuccess ||
+      qsalloc::device(reinterpret_cast<void**>(&d_ins), ins.size() * sizeof(qsk::ComposeInstr)) != cudaSuccess ||
+      qsalloc::device(reinterpret_cast<void**>(&d_data), std::max<size_t>(1, data.size()) * sizeof(double)) != cudaSuccess) {
     st = QS_ERR_OOM;
   }
   if (st == QS_OK) {

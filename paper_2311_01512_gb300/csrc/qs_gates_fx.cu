@@ -97,14 +97,19 @@ __global__ void __launch_bounds__(256) k_gate1_fx(double2* __restrict__ psi, con
 // ---------------------------------------------------------------------------
 // Diagonal: alpha_i -> d_j alpha_i, j = the target bits of i.
 // ---------------------------------------------------------------------------
+template <int N>
 __global__ void __launch_bounds__(256) k_diag_fx(double2* __restrict__ psi, const __grid_constant__ DiagFxParams p) {
-  __shared__ DiagFxEntry d[64];
-  for (int j = threadIdx.x; j < (1 << p.n); j += blockDim.x) d[j] = p.e[j];
+  __shared__ DiagFxEntry d[1 << N];
+  for (int j = threadIdx.x; j < (1 << N); j += blockDim.x) d[j] = p.e[j];
+  int tp[N];
+#pragma unroll
+  for (int q = 0; q < N; ++q) tp[q] = p.tpos[q];
   __syncthreads();
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.namps; i += stride) {
     int j = 0;
-    for (int q = 0; q < p.n; ++q) j |= (int)((i >> p.tpos[q]) & 1) << q;
+#pragma unroll
+    for (int q = 0; q < N; ++q) j |= (int)((i >> tp[q]) & 1) << q;
     const double2 v = psi[i];
     const Wd wr = words(v.x), wi = words(v.y);
     const uint32_t exf = emax2(wr, wi);
@@ -282,7 +287,16 @@ cudaError_t launch_gate1_fx(void* amps, const Gate1FxParams& p, cudaStream_t st)
 
 cudaError_t launch_diag_fx(void* amps, const DiagFxParams& p, cudaStream_t st) {
   const unsigned g = grid_for(p.namps, 256, num_sms() * kStreamBlocksPerSM);
-  k_diag_fx<<<g, 256, 0, st>>>(static_cast<double2*>(amps), p);
+  double2* a = static_cast<double2*>(amps);
+  switch (p.n) {
+    case 1: k_diag_fx<1><<<g, 256, 0, st>>>(a, p); break;
+    case 2: k_diag_fx<2><<<g, 256, 0, st>>>(a, p); break;
+    case 3: k_diag_fx<3><<<g, 256, 0, st>>>(a, p); break;
+    case 4: k_diag_fx<4><<<g, 256, 0, st>>>(a, p); break;
+    case 5: k_diag_fx<5><<<g, 256, 0, st>>>(a, p); break;
+    case 6: k_diag_fx<6><<<g, 256, 0, st>>>(a, p); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -43,6 +43,8 @@ SIGNATURES = {
     "qs_create_densmatr": (_I, [_I, _I, _P, _P, ctypes.POINTER(_P)]),
     "qs_destroy": (_I, [_P]),
     "qs_get_info": (_I, [_P, _IP, _IP, _IP, _IP]),
+    "qs_test_fail_allocations": (_I, [_I, _I]),
+    "qs_test_set_error_word": (_I, [_P]),
     "qs_device_ptr": (_I, [_P, ctypes.POINTER(_P)]),
     "qs_set_arithmetic": (_I, [_P, _I, _I]),
     "qs_set_tensor_cores": (_I, [_P, _I]),
@@ -273,9 +275,19 @@ def qs_partial_trace(h, targs, d_out):
     return out
 
 
+def _check_paulis(p, c, num_qubits, name):
+    """The C side reads paulis[n * num_qubits + q]: the array must be T x N."""
+    if c.ndim != 1 or p.shape != (c.shape[0], num_qubits):
+        raise ValueError("%s: paulis must have shape (len(coeffs), num_qubits) = (%d, %d), got %s"
+                         % (name, c.shape[0] if c.ndim == 1 else -1, num_qubits, p.shape))
+
+
 def qs_expec_pauli_sum(h, paulis, coeffs):
     p = np.ascontiguousarray(np.asarray(paulis, dtype=np.int32))
     c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+    nq = ctypes.c_int()
+    _check(_lib.qs_get_info(h, ctypes.byref(nq), None, None, None), "qs_get_info")
+    _check_paulis(p, c, nq.value, "qs_expec_pauli_sum")
     out = (ctypes.c_double * 2)()
     _check(_lib.qs_expec_pauli_sum(h, p.ctypes.data_as(_IP), c.ctypes.data_as(_DP), c.shape[0], out),
            "qs_expec_pauli_sum")
@@ -290,11 +302,24 @@ def qs_expec_pauli_sum_noalloc(d_amps, num_qubits, is_density, prec, paulis, coe
     c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
     if c.shape[0] > NOALLOC_MAX_TERMS:
         raise ValueError("qs_expec_pauli_sum_noalloc takes at most %d terms, got %d" % (NOALLOC_MAX_TERMS, c.shape[0]))
+    _check_paulis(p, c, num_qubits, "qs_expec_pauli_sum_noalloc")
     out = (ctypes.c_double * 2)()
     _check(_lib.qs_expec_pauli_sum_noalloc(_P(d_amps), num_qubits, 1 if is_density else 0, prec,
                                            p.ctypes.data_as(_IP), c.ctypes.data_as(_DP), c.shape[0],
                                            _P(stream), out), "qs_expec_pauli_sum_noalloc")
     return complex(out[0], out[1])
+
+
+def qs_test_fail_allocations(skip, count):
+    """Test hook: the next `skip` library allocations succeed, the `count`
+    after them fail on the host (see include/qs.h)."""
+    _check(_lib.qs_test_fail_allocations(int(skip), int(count)), "qs_test_fail_allocations")
+
+
+def qs_test_set_error_word(h):
+    """Test hook: set the handle's device error word (the next
+    qs_synchronize reports QS_ERR_TIMEOUT once)."""
+    _check(_lib.qs_test_set_error_word(h), "qs_test_set_error_word")
 
 
 def qs_calc_norm_or_trace(h):

@@ -522,3 +522,33 @@ def test_single_amplitude_oracle_matches_whole_state():
     targs, paulis = wl.random_pauli_string(nq, 1, nq, rng)
     np.testing.assert_allclose(orc.sample_pauli_gadget(get, targs, paulis, 0.9, out_idx),
                                orc.apply_pauli_gadget(psi, targs, paulis, 0.9)[out_idx], atol=1e-15)
+
+
+@pytest.mark.parametrize("nq", [2, 3, 4])
+def test_sampled_channels_match_full_channels(nq):
+    """The single-output channel forms (used where a Choi vector is too large
+    for the whole-vector oracle) give the whole-vector channels' result at
+    every index, for every qubit placement."""
+    rng = np.random.default_rng(40 + nq)
+    beta = rng.standard_normal(1 << (2 * nq)) + 1j * rng.standard_normal(1 << (2 * nq))
+    get = lambda ix: beta[np.asarray(ix)]
+    idx = np.arange(beta.size)
+    p = float(rng.uniform(0, 1))
+    probs = rng.uniform(0, 0.3, 3)
+    for t in range(nq):
+        pairs = [
+            (orc.densmatr_apply_dephasing(beta, t, p), orc.sample_densmatr_dephasing(get, nq, t, p, idx)),
+            (orc.densmatr_apply_depolarising(beta, t, p), orc.sample_densmatr_depolarising(get, nq, t, p, idx)),
+            (orc.densmatr_apply_damping(beta, t, p), orc.sample_densmatr_damping(get, nq, t, p, idx)),
+            (orc.densmatr_apply_pauli_channel(beta, t, *probs),
+             orc.sample_densmatr_pauli_channel(get, nq, t, *probs, idx)),
+        ]
+        for t2 in range(nq):
+            if t2 == t:
+                continue
+            pairs.append((orc.densmatr_apply_two_qubit_dephasing(beta, t, t2, p),
+                          orc.sample_densmatr_two_qubit_dephasing(get, nq, t, t2, p, idx)))
+            pairs.append((orc.densmatr_apply_two_qubit_depolarising(beta, t, t2, p),
+                          orc.sample_densmatr_two_qubit_depolarising(get, nq, t, t2, p, idx)))
+        for full, sampled in pairs:
+            np.testing.assert_allclose(sampled, full, rtol=0, atol=1e-14)
