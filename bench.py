@@ -59,6 +59,10 @@ def parse_args(argv=None):
     ap.add_argument("--f64-share", type=int, default=0,
                     help="sixteenths of one-target-gate work done in native FP64 beside double-float")
     ap.add_argument("--no-fused", action="store_true", help="skip the fused tensor-core comparison")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other workloads (15- and 6-qubit density matrices, the 4096-state batch, "
+                         "the 31-qubit complex128 fused case)")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="steps of the end-to-end leg (at most --steps)")
     ap.add_argument("--fused-qubits", type=int, default=32,
                     help="qubits of the fused comparison (32: the complex64 fused workload's size)")
     ap.add_argument("--fused-max-block", type=int, default=6,
@@ -292,6 +296,25 @@ def device_random_state(nq, device):
     return psi
 
 
+def fill_random_state(dst, nq, device, seed=STATE_SEED + 7):
+    """Seeded complex Gaussian amplitudes written into dst (complex64 or
+    complex128) in chunks of 2^26, then normalised: no state-sized temporary
+    (input generation)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    step = 1 << min(26, nq)
+    ss = 0.0
+    for i in range(0, 1 << nq, step):
+        c = torch.randn(step, dtype=torch.complex128, device=device, generator=g)
+        ss += float(torch.vdot(c, c).real.item())
+        dst[i:i + step].copy_(c)
+        del c
+    scale = 1.0 / ss ** 0.5
+    for i in range(0, 1 << nq, step):
+        dst[i:i + step] *= scale
+
+
 def load_traffic(family):
     """DRAM bytes per launch measured by ncu for a kernel family, if the record
     matches the current kernel sources (profiles/dram_traffic.json)."""
@@ -311,8 +334,12 @@ def load_traffic(family):
 def main_ours(args):
     world, rank, local = dist_setup(args)
     cpu_res = None
+    sections = {}
+    t_sec = time.perf_counter()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu_res = run_cpu_sample(NUM_OPS)   # before the first GPU call; a separate process
+    sections["cpu_baseline"] = time.perf_counter() - t_sec
+    t_sec = time.perf_counter()
     import torch
     from paper_2311_01512_gb300 import qs
     torch.cuda.set_device(local)
@@ -383,55 +410,42 @@ def main_ours(args):
 
     e2e = None
     if not args.no_e2e:
-        # Two device states on two streams: step k+1's upload (into the state
-        # step k-1 used) runs while step k's circuit runs on the other one.
-        # Every step still uploads its whole input from pinned host memory and
-        # reads its result back inside the timed region.
+        # Each step uploads its whole input from pinned host memory through
+        # qs_set_amps, runs the circuit and reads the norm back, one after the
+        # other.  (Overlapping the next upload with the circuit on a second
+        # state was slower on GB300: measured with a 16 GiB upload, the copy
+        # engine gets under 20 GB/s while the streaming kernels saturate HBM,
+        # and beside the whole circuit the upload took 674 ms and lengthened
+        # the circuit by 601 ms, against 81 ms for the upload alone.)
         pinned = torch.empty(1 << nq, dtype=torch.complex128, pin_memory=True)
         with torch.cuda.stream(stream):
             fresh = device_random_state(nq, device)
         stream.synchronize()
         pinned.copy_(fresh)
         del fresh
-        stream2 = torch.cuda.Stream(device=device)
-        psi2 = torch.empty_like(psi)
-        st2 = qs.State(nq, density=False, prec=qs.QS_C128, stream=stream2, storage=psi2)
-        qs.qs_set_arithmetic(st2.handle, ARITH_CODE[args.arith], args.f64_share)
-        H, S = [h, st2.handle], [stream, stream2]
         h2d = 16 * (1 << nq) + sum(op_h2d_bytes(op) for op in ops)
-        for j in range(2):                         # untimed warm-up step on each state
-            qs.qs_set_amps_ptr(H[j], pinned.data_ptr(), 0, 1 << nq)
-            for op in ops:
-                qs.apply_op(H[j], op)
-            qs.qs_calc_norm_or_trace(H[j])
-        K = args.steps
+        qs.qs_set_amps_ptr(h, pinned.data_ptr(), 0, 1 << nq)      # untimed warm-up step
+        for op in ops:
+            qs.apply_op(h, op)
+        qs.qs_calc_norm_or_trace(h)
+        K = max(1, min(args.steps, args.e2e_steps))
         ev_u0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
         ev_u1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
         e_start = torch.cuda.Event(enable_timing=True)
         e_end = torch.cuda.Event(enable_timing=True)
-
-        def upload(k):
-            j = k % 2
-            ev_u0[k].record(S[j])
-            qs.qs_set_amps_ptr(H[j], pinned.data_ptr(), 0, 1 << nq)
-            ev_u1[k].record(S[j])
-
         e_clocks = ClockSampler(local)
         e_clocks.start()
         barrier(world)
         torch.cuda.synchronize()
-        e_start.record(S[0])
-        upload(0)
-        for op in ops:
-            qs.apply_op(H[0], op)
+        e_start.record(stream)
         for k in range(K):
-            if k + 1 < K:
-                upload(k + 1)
-            out_norm = qs.qs_calc_norm_or_trace(H[k % 2])    # device -> host read; waits for step k
-            if k + 1 < K:
-                for op in ops:
-                    qs.apply_op(H[(k + 1) % 2], op)
-        e_end.record(S[(K - 1) % 2])
+            ev_u0[k].record(stream)
+            qs.qs_set_amps_ptr(h, pinned.data_ptr(), 0, 1 << nq)
+            ev_u1[k].record(stream)
+            for op in ops:
+                qs.apply_op(h, op)
+            out_norm = qs.qs_calc_norm_or_trace(h)     # device -> host read of the step's result
+        e_end.record(stream)
         e_end.synchronize()
         barrier(world)
         e_clk = e_clocks.stop()
@@ -439,20 +453,26 @@ def main_ours(args):
         up_ms = [ev_u0[k].elapsed_time(ev_u1[k]) for k in range(K)]
         e2e = {"value": world * NUM_OPS * K / (e_total * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16,
-               "upload_ms_per_step": sum(up_ms) / len(up_ms), "ms_per_step": e_total / K,
+               "upload_ms_per_step": sum(up_ms) / len(up_ms), "ms_per_step": e_total / K, "steps": K,
                "clocks": e_clk,
-               "note": ("pinned host state uploaded through qs_set_amps every step, %d ops, norm read back; "
-                        "two device states, so step k+1's upload overlaps step k's circuit" % NUM_OPS),
+               "note": ("pinned host state uploaded through qs_set_amps every step, %d ops, norm read back, "
+                        "in sequence on one device state" % NUM_OPS),
                "final_norm": out_norm.real}
-        st2.close()
-        del psi2
 
     fused = None
-    if not args.no_fused and rank == 0:
+    extra = None
+    sections["main_and_e2e"] = time.perf_counter() - t_sec
+    single = rank == 0 and world == 1          # the comparisons run on one GPU only
+    if (not args.no_fused or not args.no_extra) and single:
         st.close()
         del psi
         torch.cuda.empty_cache()
+    if not args.no_fused and single:
+        t_sec = time.perf_counter()
         fused = fused_comparison(args, device)
+        sections["fused_c64_32q"] = time.perf_counter() - t_sec
+    if not args.no_extra and single:
+        extra = other_workloads(args, device, sections)
 
     if rank == 0:
         line = {
@@ -474,6 +494,9 @@ def main_ours(args):
             line["e2e"] = e2e
         if fused is not None:
             line["fused_tc"] = fused
+        if extra is not None:
+            line["other_workloads"] = extra
+        line["bench_sections_s"] = sections
         if cpu_res is not None:
             line["cpu_baseline"] = cpu_baseline_dict(
                 cpu_res, "the whole %d-op circuit of the same recipe on a %d-qubit complex128 state "
@@ -492,7 +515,7 @@ def main_ours(args):
                                          for k in range(args.steps)],
                            "ops": [{"op": op["op"], "targs": op["targs"], "ctrls": op.get("ctrls", []),
                                     "family": fams[i]} for i, op in enumerate(ops)]}, f)
-    if fused is None:
+    if not ((not args.no_fused or not args.no_extra) and single):
         st.close()
     if world > 1:
         import torch.distributed as dist
@@ -506,21 +529,23 @@ def main_ours(args):
 FUSED_OPS = 1000
 
 
-def fused_comparison(args, device):
+def fused_comparison(args, device, nq=None, prec=None, max_block=None):
     """The 1000-gate unitary circuit of the fused workload (1q Haar; 1-2-target
     Haar with 0-3 controls; gadgets of weight 1-6) on one random state: the
-    plain per-gate form (complex128, native FP64 and double-float) against
-    cost-model-planned fused blocks on the tensor cores (complex64 with 3xTF32
-    blocks, or complex128 with bf16 integer-slice blocks).  Reports times,
-    speedup, max |delta amp| and 1 - fidelity of the fused result against the
-    per-gate complex128 result.  States are regenerated from their seed instead
-    of kept as copies, and the comparison runs in slices, so that the 32-qubit
-    case needs three state-sized buffers at most."""
+    plain per-gate form in complex128 (native FP64, and block fixed point,
+    which is at least FP64-accurate) against cost-model-planned fused blocks
+    on the tensor cores (complex64 with 3xTF32 blocks, or complex128 with
+    eight-slice integer blocks).  Every timed run starts from the seeded
+    initial state; times are medians of three runs after a warm-up on the
+    first 20 gates, except native FP64 (one warmed run: about a minute at 32
+    qubits).  The plan (cost-model DP and FP64 block composition) is timed
+    apart from the fused runs.  1 - fidelity and max |delta amp| of the fused
+    result are taken against both complex128 per-gate results."""
     import torch
     from paper_2311_01512_gb300 import costmodel, qs
     from paper_2311_01512_gb300 import workloads as wl
-    nq = args.fused_qubits
-    c64 = args.fused_prec == "c64"
+    nq = nq or args.fused_qubits
+    c64 = (prec or args.fused_prec) == "c64"
     ops = wl.unitary_circuit(nq, FUSED_OPS, wl.rng_for("fused-tc-circuit"))
     stream = torch.cuda.Stream(device=device)
 
@@ -536,71 +561,137 @@ def fused_comparison(args, device):
     def reset(dst):
         # the seeded initial state, written on the circuit's stream
         with torch.cuda.stream(stream):
-            src = device_random_state(nq, device)
-            dst.copy_(src)
-            del src
+            fill_random_state(dst, nq, device)
         stream.synchronize()
 
+    def runs(dst, fn, n):
+        out = []
+        for _ in range(n):
+            reset(dst)
+            out.append(timed(fn))
+        return out
+
+    def per_gate(handle, tensor, arith, n):
+        qs.qs_set_arithmetic(handle, arith)
+        warm = qs.Circuit(nq, ops[:20])
+        warm.plan(qs.QS_PLAN_NONE, 1)
+        warm.apply(handle)
+        warm.close()
+        circ = qs.Circuit(nq, ops)
+        circ.plan(qs.QS_PLAN_NONE, 1)
+        t = runs(tensor, lambda: circ.apply(handle), n)
+        circ.close()
+        return t
+
     out = {"qubits": nq, "ops": FUSED_OPS, "fused_amp": "complex64" if c64 else "complex128"}
-    # per-gate complex128, native FP64 and double-float
     with torch.cuda.stream(stream):
-        t128 = device_random_state(nq, device)
+        r64 = torch.empty(1 << nq, dtype=torch.complex128, device=device)
+        rfx = torch.empty_like(r64)
     stream.synchronize()
-    st = qs.State(nq, prec=qs.QS_C128, stream=stream, storage=t128)
-    circ = qs.Circuit(nq, ops)
-    circ.plan(qs.QS_PLAN_NONE, 1)
-    qs.qs_set_arithmetic(st.handle, qs.QS_ARITH_F64)
-    out["per_gate_f64_ms"] = timed(lambda: circ.apply(st.handle))
-    reset(t128)
-    qs.qs_set_arithmetic(st.handle, qs.QS_ARITH_DF)
-    out["per_gate_df_ms"] = timed(lambda: circ.apply(st.handle))
+    s64 = qs.State(nq, prec=qs.QS_C128, stream=stream, storage=r64)
+    sfx = qs.State(nq, prec=qs.QS_C128, stream=stream, storage=rfx)
+    out["per_gate_f64_ms_runs"] = per_gate(s64.handle, r64, qs.QS_ARITH_F64, 1)
+    out["per_gate_f64_ms"] = out["per_gate_f64_ms_runs"][0]
+    out["per_gate_fx_ms_runs"] = per_gate(sfx.handle, rfx, qs.QS_ARITH_FX, 3)
+    out["per_gate_fx_ms"] = statistics.median(out["per_gate_fx_ms_runs"])
     # fused form, planned by the learned cost model
     with torch.cuda.stream(stream):
-        src = device_random_state(nq, device)
-        tf = src.to(torch.complex64) if c64 else src
-        del src
-    stream.synchronize()
+        tf = torch.empty(1 << nq, dtype=torch.complex64 if c64 else torch.complex128, device=device)
     sf = qs.State(nq, prec=qs.QS_C64 if c64 else qs.QS_C128, stream=stream, storage=tf)
     model, meta = costmodel.load()
     circf = qs.Circuit(nq, ops)
-    width = min(args.fused_max_block, 6 if c64 else 5)
+    width = min(max_block or args.fused_max_block, 6 if c64 else 5)
+    t0 = time.perf_counter()
     plan = circf.plan_cost(model, sf.handle, max_block_qubits=width, window=24)
+    out["plan_ms"] = (time.perf_counter() - t0) * 1e3
     plan["max_block_qubits"] = width
-    out["fused_ms"] = timed(lambda: circf.apply(sf.handle))
+    reset(tf)
+    circf.apply(sf.handle)                                  # warm-up
+    out["fused_ms_runs"] = runs(tf, lambda: circf.apply(sf.handle), 3)
+    out["fused_ms"] = statistics.median(out["fused_ms_runs"])
     out["plan"] = plan
+    out["plan_note"] = ("plan_ms: cost-model DP over the circuit and FP64 composition of the fused blocks on "
+                        "the device, done once per circuit, outside fused_ms")
     out["costmodel_holdout_median_time_error"] = meta.get("holdout_median_abs_rel_time_error")
-    # unfused, same precision as the fused form
-    reset(tf)
-    circn = qs.Circuit(nq, ops)
-    circn.plan(qs.QS_PLAN_NONE, 1)
-    out["per_gate_same_prec_ms"] = timed(lambda: circn.apply(sf.handle))
-    reset(tf)
-    circf.apply(sf.handle)
-    stream.synchronize()
-    # max |delta amp| and fidelity, in slices of 2^26 amplitudes
-    dmax, ov, na, nb = 0.0, 0.0 + 0.0j, 0.0, 0.0
-    step = 1 << min(26, nq)
-    with torch.cuda.stream(stream):
-        for i in range(0, 1 << nq, step):
-            a = t128[i:i + step]
-            b = tf[i:i + step].to(torch.complex128)
-            dmax = max(dmax, float((a - b).abs().max().item()))
-            ov += complex(torch.vdot(a, b).item())
-            na += float(torch.vdot(a, a).real.item())
-            nb += float(torch.vdot(b, b).real.item())
-    stream.synchronize()
-    out["max_abs_delta_amp"] = dmax
-    out["one_minus_fidelity"] = 1.0 - abs(ov) ** 2 / (na * nb)
-    out["reference"] = "per-gate complex128 double-float result (oracle-checked at small sizes)"
+    out["costmodel_test_median_time_error"] = meta.get("test_median_abs_rel_time_error")
+    # max |delta amp| and fidelity of the fused result (tf, one application
+    # from the initial state) against both per-gate complex128 results, in
+    # slices of 2^26 amplitudes
+    for name, ref in (("f64", r64), ("fx", rfx)):
+        dmax, ov, na, nb = 0.0, 0.0 + 0.0j, 0.0, 0.0
+        step = 1 << min(26, nq)
+        with torch.cuda.stream(stream):
+            for i in range(0, 1 << nq, step):
+                a = ref[i:i + step]
+                b = tf[i:i + step].to(torch.complex128)
+                dmax = max(dmax, float((a - b).abs().max().item()))
+                ov += complex(torch.vdot(a, b).item())
+                na += float(torch.vdot(a, a).real.item())
+                nb += float(torch.vdot(b, b).real.item())
+        stream.synchronize()
+        out["max_abs_delta_amp_vs_" + name] = dmax
+        out["one_minus_fidelity_vs_" + name] = 1.0 - abs(ov) ** 2 / (na * nb)
+    out["one_minus_fidelity"] = out["one_minus_fidelity_vs_f64"]
+    out["max_abs_delta_amp"] = out["max_abs_delta_amp_vs_f64"]
+    out["reference"] = ("per-gate complex128 results from the same initial state: native FP64 (f64) and block "
+                        "fixed point (fx, at least FP64; both oracle-checked at small sizes)")
+    # unfused, same precision as the fused form (complex128: that is fx)
+    if c64:
+        circn = qs.Circuit(nq, ops)
+        circn.plan(qs.QS_PLAN_NONE, 1)
+        out["per_gate_same_prec_ms_runs"] = runs(tf, lambda: circn.apply(sf.handle), 3)
+        out["per_gate_same_prec_ms"] = statistics.median(out["per_gate_same_prec_ms_runs"])
+        circn.close()
+    else:
+        out["per_gate_same_prec_ms"] = out["per_gate_fx_ms"]
     out["speedup_vs_per_gate_f64"] = out["per_gate_f64_ms"] / out["fused_ms"]
-    out["speedup_vs_per_gate_df"] = out["per_gate_df_ms"] / out["fused_ms"]
-    for h in (st, sf):
+    out["speedup_vs_per_gate_fx"] = out["per_gate_fx_ms"] / out["fused_ms"]
+    for h in (s64, sfx, sf):
         h.close()
-    for c in (circ, circf, circn):
-        c.close()
+    circf.close()
     model.close()
-    del t128, tf
+    del r64, rfx, tf
     torch.cuda.empty_cache()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# The other workloads, each on its own (after the main state is freed)
+# ---------------------------------------------------------------------------
+
+def other_workloads(args, device, sections):
+    """The density-matrix workloads (15 qubits: 400 operations, GB/s by kind;
+    6 qubits: microseconds per operation, per call, recorded and batched),
+    the 4096-state batch in complex64 and complex128 (gates/s, speedup over
+    launching each circuit separately, 1 - fidelity of 8 sampled states), and
+    the 31-qubit complex128 fused case.  A workload that fails is reported
+    with its error instead of stopping the run."""
+    import traceback
+    import torch
+    from paper_2311_01512_gb300 import batch_bench, dm_bench, qs
+    from paper_2311_01512_gb300 import workloads as wl
+    peak = None
+    try:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs")
+    except Exception:
+        pass
+    jobs = [
+        ("densmatr_15q_400ops", lambda: dm_bench.large(qs, wl, torch, peak, reps=3)),
+        ("densmatr_6q_300ops", lambda: dm_bench.small(qs, wl, torch, 20)),
+        ("batch_4096_c64", lambda: batch_bench.run(0, 4096, 3, True, 8)),
+        ("batch_4096_c128", lambda: batch_bench.run(1, 4096, 3, True, 8)),
+        ("fused_c128_31q", lambda: fused_comparison(args, device, nq=31, prec="c128", max_block=5)),
+    ]
+    out = {}
+    for name, fn in jobs:
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as e:          # reported, not hidden: the error text goes into the line
+            out[name] = {"error": "%s: %s" % (type(e).__name__, e), "trace": traceback.format_exc()[-1500:]}
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        sections[name] = time.perf_counter() - t0
     return out
 
 

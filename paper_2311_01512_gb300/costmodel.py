@@ -110,22 +110,30 @@ def collect(samples, configs, seed=2311015122, device="cuda"):
     return X, y, meta
 
 
-def train(X, y, epochs=300, batch=512, lr=2e-3, seed=7, holdout=0.2):
-    """Train a fresh model on the GPU; returns (model, metrics)."""
+def split(n, seed=7, validation=0.15, test=0.15):
+    """Row indices of the training, validation (model selection) and test
+    (reported only, never used for a choice) sets."""
+    perm = np.random.default_rng(seed).permutation(n)
+    nv, nt = int(n * validation), int(n * test)
+    return perm[nv + nt:], perm[:nv], perm[nv:nv + nt]
+
+
+def _errors(model, X, y):
+    err = model.predict(X) - y
+    return float(np.sqrt(np.mean(err ** 2))), float(np.median(np.abs(np.expm1(err))))
+
+
+def train(X, y, epochs=300, batch=512, lr=2e-3, seed=7):
+    """Train a fresh model on the GPU on the training rows; returns (model,
+    metrics on the validation rows)."""
     from . import qs
-    n = X.shape[0]
-    rng = np.random.default_rng(seed)
-    perm = rng.permutation(n)
-    nh = int(n * holdout)
-    hold, tr = perm[:nh], perm[nh:]
+    tr, va, _ = split(X.shape[0], seed)
     model = qs.CostModel(seed=seed)
     train_loss = model.train(X[tr], y[tr], epochs=epochs, batch=batch, lr=lr, seed=seed)
-    pred = model.predict(X[hold]) if nh else np.zeros(0)
-    err = pred - y[hold]
-    metrics = {"train_mse_log": float(train_loss),
-               "holdout_rmse_log": float(np.sqrt(np.mean(err ** 2))) if nh else None,
-               "holdout_median_abs_rel_time_error": float(np.median(np.abs(np.expm1(err)))) if nh else None,
-               "train_rows": int(len(tr)), "holdout_rows": int(nh)}
+    rmse, med = _errors(model, X[va], y[va])
+    metrics = {"train_mse_log": float(train_loss), "holdout_rmse_log": rmse,
+               "holdout_median_abs_rel_time_error": med, "train_rows": int(len(tr)), "holdout_rows": int(len(va)),
+               "holdout_role": "validation: chooses among the epoch settings"}
     return model, metrics
 
 
@@ -146,7 +154,8 @@ def main():
     ap.add_argument("--samples", type=int, default=20000)
     ap.add_argument("--out", default=WEIGHTS_PATH)
     ap.add_argument("--epochs", type=int, nargs="+", default=[300],
-                    help="train once per value; the model with the lowest hold-out error is saved")
+                    help="train once per value; the model with the lowest validation error is saved and its "
+                         "error on the separate test rows reported")
     ap.add_argument("--data-out", help="also save the timed rows (X, log ms) here")
     ap.add_argument("--data-in", help="train on rows saved by --data-out instead of timing new ones")
     args = ap.parse_args()
@@ -170,6 +179,10 @@ def main():
         else:
             model.close()
     meta.update(best[1])
+    # the test rows were used for nothing above: the reported error of the chosen model
+    _, _, te = split(X.shape[0])
+    rmse, med = _errors(best[0], X[te], y[te])
+    meta.update({"test_rmse_log": rmse, "test_median_abs_rel_time_error": med, "test_rows": int(len(te))})
     save(best[0], args.out, meta)
     print(json.dumps(meta))
 

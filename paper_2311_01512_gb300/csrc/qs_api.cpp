@@ -920,7 +920,8 @@ qs_status qs_expec_pauli_sum(const qs_state* cs, const int* paulis, const double
       e = qsk::launch_expec_sv_diag(s->prec, s->amps, s->nq, dt, cnt, s->d_partials, s->stream,
                                        s->arith != QS_ARITH_DF);
     else
-      e = qsk::launch_expec_sv(s->prec, s->amps, s->nq, dt, cnt, s->d_partials, s->stream, s->arith != QS_ARITH_DF);
+      e = qsk::launch_expec_sv(s->prec, s->amps, s->nq, dt, cnt, s->d_partials, s->stream, s->arith != QS_ARITH_DF,
+                               qsk::make_tile_order(terms.data() + first, cnt));
     if (e == cudaSuccess) e = qsk::launch_reduce_final(s->d_partials, s->d_result, first > 0, s->stream);
     first += cnt;
     st = ring_done(s, slot);

@@ -190,6 +190,51 @@ struct PauliTerm {
   int pad;
 };
 
+// Order in which the statevector expectation visits its tiles of
+// 2^kExpecTileBits amplitudes.  The tile-index parts of all flip masks
+// (xy >> kExpecTileBits) span a subspace with a reduced basis basis[0..r):
+// basis[j] has its highest bit at piv[j] (ascending) and no other pivot bit.
+// Virtual tile v = c 2^r + e visits the tile whose pivot bits are e and whose
+// other bits are those of c XOR the basis combination e selects: each coset
+// of the span is visited in one run of consecutive v, and every partner tile
+// (tile xor xy >> kExpecTileBits) lies in the same coset, so it is read while
+// the coset is in L2 (when the span is small enough to fit).
+constexpr int kExpecTileBits = 10;
+struct TileOrder {
+  int r;
+  int8_t piv[32];
+  uint32_t basis[32];
+};
+
+inline TileOrder make_tile_order(const PauliTerm* terms, int n) {
+  TileOrder o{};
+  uint32_t b[32];
+  int r = 0;
+  for (int k = 0; k < n; ++k) {
+    uint32_t v = (uint32_t)(terms[k].xy >> kExpecTileBits);
+    for (int j = 0; j < r; ++j)
+      if ((v >> (31 - __builtin_clz(b[j]))) & 1u) v ^= b[j];
+    if (!v) continue;
+    const int p = 31 - __builtin_clz(v);
+    for (int j = 0; j < r; ++j)
+      if ((b[j] >> p) & 1u) b[j] ^= v;
+    b[r++] = v;
+  }
+  // ascending pivots
+  for (int i = 1; i < r; ++i)
+    for (int j = i; j > 0 && b[j - 1] > b[j]; --j) {
+      const uint32_t t = b[j];
+      b[j] = b[j - 1];
+      b[j - 1] = t;
+    }
+  o.r = r;
+  for (int j = 0; j < r; ++j) {
+    o.basis[j] = b[j];
+    o.piv[j] = (int8_t)(31 - __builtin_clz(b[j]));
+  }
+  return o;
+}
+
 // Block composition (qs_fuse.cu): one gate of a block, on block-local bits.
 struct ComposeInstr {
   int kind;              // 0 dense with controls, 1 diagonal, 2 Pauli gadget
@@ -309,8 +354,9 @@ cudaError_t launch_norm(qs_prec prec, const void* amps, int ns, double2* partial
 cudaError_t launch_trace(qs_prec prec, const void* amps, int nq, double2* partials, cudaStream_t st);
 cudaError_t launch_expec_dm(qs_prec prec, const void* amps, int nq, const PauliTerm* terms,
                             int nterms, double2* partials, cudaStream_t st);
+// order: from make_tile_order on the same terms (host copy)
 cudaError_t launch_expec_sv(qs_prec prec, const void* amps, int nq, const PauliTerm* terms,
-                            int nterms, double2* partials, cudaStream_t st, bool f64);
+                            int nterms, double2* partials, cudaStream_t st, bool f64, const TileOrder& order);
 // the diagonal (I/Z) terms of a statevector Pauli sum by warp Walsh-Hadamard transforms; N >= 5
 cudaError_t launch_expec_sv_diag(qs_prec prec, const void* amps, int nq, const PauliTerm* terms, int nterms,
                                  double2* partials, cudaStream_t st, bool f64);

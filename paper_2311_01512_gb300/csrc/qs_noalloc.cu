@@ -104,7 +104,8 @@ extern "C" qs_status qs_expec_pauli_sum_noalloc(const void* d_amps, int num_qubi
       cudaSuccess)
     return QS_ERR_CUDA;
   cudaError_t e = is_density ? qsk::launch_expec_dm(prec, d_amps, num_qubits, d_terms, num_terms, d_partials, stream)
-                             : qsk::launch_expec_sv(prec, d_amps, num_qubits, d_terms, num_terms, d_partials, stream, true);
+                             : qsk::launch_expec_sv(prec, d_amps, num_qubits, d_terms, num_terms, d_partials, stream, true,
+                                                    qsk::make_tile_order(terms, num_terms));
   if (e == cudaSuccess) e = qsk::launch_reduce_final(d_partials, d_result, 0, stream);
   double2 result;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&result, d_result, sizeof(double2), cudaMemcpyDeviceToHost, stream);

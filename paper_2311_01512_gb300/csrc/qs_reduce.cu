@@ -134,6 +134,21 @@ struct GroupDf {
   int first, count;
 };
 
+// Tile visited at virtual position v (TileOrder in qs_internal.h): zero bits
+// inserted at the pivots into c = v >> r, then the basis vectors selected by
+// the low r bits of v.
+__device__ __forceinline__ uint64_t ordered_tile(uint64_t v, const TileOrder& o) {
+  const int r = o.r;
+  uint64_t t = v >> r;
+  for (int j = 0; j < r; ++j) {
+    const int p = o.piv[j];
+    t = ((t >> p) << (p + 1)) | (t & ((1ull << p) - 1));
+  }
+  for (int j = 0; j < r; ++j)
+    if ((v >> j) & 1) t ^= o.basis[j];
+  return t;
+}
+
 // Work mapping: a block takes tiles of 256 E consecutive amplitudes (thread t
 // holds amplitudes t, t + 256, ... of the tile) and runs every group over the
 // tile.  A group whose highest flip bit lies above the tile either visits the
@@ -142,7 +157,7 @@ struct GroupDf {
 template <typename R, int E>
 __global__ void __launch_bounds__(256) k_expec_sv(const typename Cplx<R>::T* __restrict__ psi, int nq,
                                                   const PauliTerm* __restrict__ terms, int nterms,
-                                                  double2* __restrict__ partials) {
+                                                  double2* __restrict__ partials, const __grid_constant__ TileOrder ord) {
   using qsdf::df;
   using T2 = typename Cplx<R>::T;
   extern __shared__ unsigned char sm_raw[];
@@ -173,8 +188,8 @@ __global__ void __launch_bounds__(256) k_expec_sv(const typename Cplx<R>::T* __r
   constexpr uint64_t kTile = 256ull * E;
   const uint64_t dim = 1ull << nq;
   const uint64_t ntiles = dim > kTile ? dim / kTile : 1;
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const uint64_t base = tile * kTile;
+  for (uint64_t vt = blockIdx.x; vt < ntiles; vt += gridDim.x) {
+    const uint64_t base = ordered_tile(vt, ord) * kTile;
     uint64_t iu[E];
     bool ok[E];
     df ar[E], ai[E];
@@ -245,7 +260,8 @@ __global__ void __launch_bounds__(256) k_expec_sv(const typename Cplx<R>::T* __r
 template <int E>
 __global__ void __launch_bounds__(256) k_expec_sv_f64(const double2* __restrict__ psi, int nq,
                                                       const PauliTerm* __restrict__ terms, int nterms,
-                                                      double2* __restrict__ partials) {
+                                                      double2* __restrict__ partials,
+                                                      const __grid_constant__ TileOrder ord) {
   extern __shared__ unsigned char sm_raw[];
   PauliTerm* ts = reinterpret_cast<PauliTerm*>(sm_raw);
   GroupDf* gs = reinterpret_cast<GroupDf*>(ts + nterms);
@@ -270,8 +286,8 @@ __global__ void __launch_bounds__(256) k_expec_sv_f64(const double2* __restrict_
   constexpr uint64_t kTile = 256ull * E;
   const uint64_t dim = 1ull << nq;
   const uint64_t ntiles = dim > kTile ? dim / kTile : 1;
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const uint64_t base = tile * kTile;
+  for (uint64_t vt = blockIdx.x; vt < ntiles; vt += gridDim.x) {
+    const uint64_t base = ordered_tile(vt, ord) * kTile;
     uint64_t iu[E];
     bool ok[E];
     double2 a[E];
@@ -547,9 +563,26 @@ cudaError_t launch_expec_dm(qs_prec prec, const void* amps, int nq, const PauliT
   return cudaGetLastError();
 }
 
+// Blocks of the statevector expectation kernels: as many as are resident at
+// once (at most kReduceBlocks), so that the blocks walk consecutive virtual
+// tiles together and a coset of the tile order is processed while it is in
+// L2.  The other partial slots are zeroed (the final sum stays in a fixed
+// order for a given kernel and GPU).
+template <typename K>
+static cudaError_t resident_grid(K kernel, size_t smem, double2* partials, cudaStream_t st, unsigned* grid) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem);
+  if (e != cudaSuccess) return e;
+  const int g = per_sm > 0 ? per_sm * num_sms() : 1;
+  *grid = (unsigned)(g < kReduceBlocks ? g : kReduceBlocks);
+  if (*grid < (unsigned)kReduceBlocks)
+    return cudaMemsetAsync(partials + *grid, 0, sizeof(double2) * (kReduceBlocks - *grid), st);
+  return cudaSuccess;
+}
+
 template <typename R, int E>
 static cudaError_t expec_sv_u(const void* amps, int nq, const PauliTerm* terms, int nterms, double2* partials,
-                              cudaStream_t st) {
+                              cudaStream_t st, const TileOrder& ord) {
   static bool attr_done = false;
   if (!attr_done) {
     const cudaError_t e = cudaFuncSetAttribute(k_expec_sv<R, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -557,13 +590,18 @@ static cudaError_t expec_sv_u(const void* amps, int nq, const PauliTerm* terms, 
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  k_expec_sv<R, E><<<kReduceBlocks, 256, (sizeof(TermDf) + sizeof(GroupDf)) * (size_t)nterms, st>>>(
-      static_cast<const typename Cplx<R>::T*>(amps), nq, terms, nterms, partials);
+  const size_t smem = (sizeof(TermDf) + sizeof(GroupDf)) * (size_t)nterms;
+  unsigned grid = kReduceBlocks;
+  const cudaError_t e = resident_grid(k_expec_sv<R, E>, smem, partials, st, &grid);
+  if (e != cudaSuccess) return e;
+  k_expec_sv<R, E><<<grid, 256, smem, st>>>(static_cast<const typename Cplx<R>::T*>(amps), nq, terms, nterms,
+                                            partials, ord);
   return cudaGetLastError();
 }
 
 cudaError_t launch_expec_sv(qs_prec prec, const void* amps, int nq, const PauliTerm* terms, int nterms,
-                            double2* partials, cudaStream_t st, bool f64) {
+                            double2* partials, cudaStream_t st, bool f64, const TileOrder& ord) {
+  static_assert(256 * 4 == (1 << kExpecTileBits), "tiles of the expectation kernels");
   if (nterms > kTermChunk) return cudaErrorInvalidValue;
   if (prec == QS_C128 && f64) {
     static bool attr_done = false;
@@ -574,14 +612,17 @@ cudaError_t launch_expec_sv(qs_prec prec, const void* amps, int nq, const PauliT
       if (e != cudaSuccess) return e;
       attr_done = true;
     }
-    k_expec_sv_f64<4><<<kReduceBlocks, 256, per * (size_t)nterms, st>>>(static_cast<const double2*>(amps), nq, terms,
-                                                                         nterms, partials);
+    unsigned grid = kReduceBlocks;
+    const cudaError_t e = resident_grid(k_expec_sv_f64<4>, per * (size_t)nterms, partials, st, &grid);
+    if (e != cudaSuccess) return e;
+    k_expec_sv_f64<4><<<grid, 256, per * (size_t)nterms, st>>>(static_cast<const double2*>(amps), nq, terms, nterms,
+                                                                partials, ord);
     return cudaGetLastError();
   }
   // tiles of 1024 amplitudes (28 qubits, 8 random terms: 6.9 ms against 7.5
   // and 8.0 ms for tiles of 512 and 2048)
-  return prec == QS_C128 ? expec_sv_u<double, 4>(amps, nq, terms, nterms, partials, st)
-                         : expec_sv_u<float, 4>(amps, nq, terms, nterms, partials, st);
+  return prec == QS_C128 ? expec_sv_u<double, 4>(amps, nq, terms, nterms, partials, st, ord)
+                         : expec_sv_u<float, 4>(amps, nq, terms, nterms, partials, st, ord);
 }
 
 cudaError_t launch_reduce_final(const double2* partials, double2* result, int accumulate, cudaStream_t st,
