@@ -337,6 +337,25 @@ qs_status qs_costmodel_train(qs_costmodel* model, const float* features, const f
 qs_status qs_circuit_plan_cost(qs_circuit* circuit, qs_costmodel* model, const qs_state* state,
                                int max_block_qubits, int window);
 
+/* Lazy qubit relabelling of a planned circuit on statevectors (Sec. "Swap
+ * gate", and the paper's reason for moving targets before a many-target
+ * gate, here on one GPU).  The tensor-core kernels tile rows on the lowest
+ * free qubits, so a block with qubits among the `low_qubits` lowest physical
+ * positions gathers strided rows.  Walking the blocks in order, a block whose
+ * qubits lie there has one of them swapped with the high position whose
+ * qubit the tensor-core blocks need last, whenever the cost model predicts
+ * the block's saving to exceed the price of a SWAP pass, swap_passes times
+ * the predicted time of a one-target pass (a SWAP moves half the state, but
+ * on a low qubit touches every sector: about 1.2).  qs_circuit_apply then applies
+ * those SWAPs (qs_apply_swap) and the blocks on the moved positions, and ends
+ * with the SWAPs back to the identity layout: the result is the same up to
+ * rounding.  low_qubits = 0 clears the relabelling; density matrices ignore
+ * it.  Replanning clears it. */
+qs_status qs_circuit_plan_relabel(qs_circuit* circuit, qs_costmodel* model, const qs_state* state, int low_qubits,
+                                  double swap_passes);
+/* SWAP passes the relabelling adds (0 when none). */
+qs_status qs_circuit_get_relabel(const qs_circuit* circuit, int* num_swaps);
+
 /* ------------------------------------------------------------------------
  * Batched engine (not in the paper): many independent states of at most 24
  * storage qubits (statevectors, or density matrices of at most 12 qubits as
@@ -413,6 +432,13 @@ qs_status qs_test_fail_allocations(int skip, int count);
  * of its bounded waits runs out, so that the next qs_synchronize reports
  * QS_ERR_TIMEOUT (once) and clears it.  Synchronises the stream. */
 qs_status qs_test_set_error_word(qs_state* state);
+
+/* Run the bounded-wait path on the GPU: one thread waits on a barrier that
+ * nothing arrives at, gives up after `polls` polls (at most 2^20), and sets
+ * the handle's error word as a tensor-core kernel does when its wait runs
+ * out.  Queued on the handle's stream; the next qs_synchronize reports
+ * QS_ERR_TIMEOUT once.  Nothing faults or hangs. */
+qs_status qs_test_bounded_wait(qs_state* state, unsigned polls);
 
 /* Largest number of terms qs_expec_pauli_sum_noalloc accepts. */
 #define QS_NOALLOC_MAX_TERMS 256

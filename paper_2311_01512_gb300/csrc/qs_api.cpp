@@ -466,6 +466,11 @@ qs_status qs_test_set_error_word(qs_state* s) {
   return QS_OK;
 }
 
+qs_status qs_test_bounded_wait(qs_state* s, unsigned polls) {
+  if (!s || s->rec || polls > (1u << 20)) return QS_ERR_ARG;
+  return cuda_status(qsk::launch_test_wait_timeout(s->d_err, polls, s->stream));
+}
+
 const char* qs_status_str(qs_status status) {
   switch (status) {
     case QS_OK: return "ok";

@@ -50,6 +50,11 @@ struct qs_circuit {
   bool planned = false;
   double* d_mats = nullptr;
   size_t mats_bytes = 0;
+  // lazy relabelling (qs_circuit_plan_relabel): physical SWAPs before each
+  // block, and the SWAPs that restore the identity layout after the last
+  bool relabel = false;
+  std::vector<std::vector<std::pair<int, int>>> swaps_before;
+  std::vector<std::pair<int, int>> swaps_after;
 };
 
 namespace {
@@ -65,6 +70,7 @@ qs_status add_gate(qs_circuit* c, CGate&& g) {
   for (int q : g.ctrls) g.qmask |= 1ull << q;
   c->gates.push_back(std::move(g));
   c->planned = false;
+  c->relabel = false;
   return QS_OK;
 }
 
@@ -162,6 +168,9 @@ void close_block(qs_circuit* c, int first, int last, uint64_t mask) {
 // given as the first gate of every block.
 qs_status qs_circuit_set_blocks_internal(qs_circuit* c, const std::vector<int>& starts, int max_block_qubits) {
   c->blocks.clear();
+  c->relabel = false;
+  c->swaps_before.clear();
+  c->swaps_after.clear();
   const int G = (int)c->gates.size();
   for (size_t i = 0; i < starts.size(); ++i) {
     const int first = starts[i], last = i + 1 < starts.size() ? starts[i + 1] : G;
@@ -323,6 +332,120 @@ qs_status qs_circuit_plan_cost(qs_circuit* c, qs_costmodel* model, const qs_stat
   return qs_circuit_set_blocks_internal(c, starts, max_block_qubits);
 }
 
+qs_status qs_circuit_plan_relabel(qs_circuit* c, qs_costmodel* model, const qs_state* s, int low_qubits,
+                                  double swap_passes) {
+  if (!c || !model || !s || s->nq != c->nq || low_qubits < 0 || low_qubits >= c->nq) return QS_ERR_ARG;
+  if (!c->planned) return QS_ERR_ARG;
+  const int B = (int)c->blocks.size(), nq = c->nq;
+  c->relabel = false;
+  c->swaps_before.assign((size_t)B, {});
+  c->swaps_after.clear();
+  if (low_qubits == 0 || s->is_density) return QS_OK;
+  // per block: its qubits, and its launch if it runs on the tensor cores
+  // (the only kernels whose speed depends on where the qubits lie)
+  std::vector<uint64_t> bmask((size_t)B, 0);
+  std::vector<int> tc((size_t)B, 0), kind((size_t)B, 0), width((size_t)B, 0), nctrl((size_t)B, 0);
+  for (int b = 0; b < B; ++b) {
+    const CBlock& bl = c->blocks[(size_t)b];
+    for (int q : bl.qubits) bmask[(size_t)b] |= 1ull << q;
+    if (bl.fused) {
+      kind[(size_t)b] = QS_COST_FUSED_DENSE;
+      width[(size_t)b] = popc64(bmask[(size_t)b]);
+      tc[(size_t)b] = width[(size_t)b] >= 2;
+    } else {
+      const CGate& g = c->gates[(size_t)bl.first];
+      if (g.kind == 0 && g.targs.size() >= 2) {
+        kind[(size_t)b] = QS_COST_DENSE;
+        width[(size_t)b] = (int)g.targs.size();
+        nctrl[(size_t)b] = (int)g.ctrls.size();
+        tc[(size_t)b] = 1;
+      }
+    }
+  }
+  std::vector<float> row(QS_COST_FEATURES);
+  auto predict_ms = [&](int k, int w, uint64_t mask, int nc, double* out) {
+    qs_status st = qs_costmodel_encode(k, w, mask, nc, 0, s, row.data());
+    float y = 0.0f;
+    if (st == QS_OK) st = qs_costmodel_predict(model, row.data(), 1, &y);
+    *out = std::exp((double)y);
+    return st;
+  };
+  // the price of a SWAP pass, in predicted one-target passes
+  double swap_ms = 0.0;
+  qs_status st = predict_ms(QS_COST_GATE1, 1, 1ull << (nq - 1), 0, &swap_ms);
+  if (st != QS_OK) return st;
+  swap_ms *= swap_passes;
+  std::vector<int> perm((size_t)nq), inv((size_t)nq);
+  for (int q = 0; q < nq; ++q) perm[(size_t)q] = inv[(size_t)q] = q;
+  auto physical = [&](uint64_t m) {
+    uint64_t r = 0;
+    for (int q = 0; q < nq; ++q)
+      if (m >> q & 1) r |= 1ull << perm[(size_t)q];
+    return r;
+  };
+  auto do_swap = [&](int p1, int p2, std::vector<std::pair<int, int>>& into) {
+    into.push_back({p1, p2});
+    const int q1 = inv[(size_t)p1], q2 = inv[(size_t)p2];
+    perm[(size_t)q1] = p2;
+    perm[(size_t)q2] = p1;
+    inv[(size_t)p1] = q2;
+    inv[(size_t)p2] = q1;
+  };
+  const uint64_t lowmask = (1ull << low_qubits) - 1;
+  int nswaps = 0;
+  for (int b = 0; b < B; ++b) {
+    if (!tc[(size_t)b]) continue;
+    for (;;) {
+      const uint64_t pm = physical(bmask[(size_t)b]);
+      const uint64_t bad = pm & lowmask;
+      if (!bad) break;
+      const int plow = __builtin_ctzll(bad);
+      // the high position whose qubit the tensor-core blocks need last (or never)
+      int best_p = -1, best_next = -1;
+      for (int p = low_qubits; p < nq; ++p) {
+        const int q = inv[(size_t)p];
+        if (bmask[(size_t)b] >> q & 1) continue;
+        int next = B + 1;
+        for (int b2 = b + 1; b2 < B; ++b2)
+          if (tc[(size_t)b2] && (bmask[(size_t)b2] >> q & 1)) {
+            next = b2;
+            break;
+          }
+        if (next >= best_next) {
+          best_next = next;
+          best_p = p;
+        }
+      }
+      if (best_p < 0) break;
+      double t_now = 0.0, t_after = 0.0;
+      st = predict_ms(kind[(size_t)b], width[(size_t)b], pm, nctrl[(size_t)b], &t_now);
+      if (st == QS_OK)
+        st = predict_ms(kind[(size_t)b], width[(size_t)b], (pm & ~(1ull << plow)) | (1ull << best_p),
+                        nctrl[(size_t)b], &t_after);
+      if (st != QS_OK) return st;
+      if (t_now - t_after <= swap_ms) break;
+      do_swap(plow, best_p, c->swaps_before[(size_t)b]);
+      ++nswaps;
+    }
+  }
+  // back to the identity layout: physical p receives logical p
+  for (int p = 0; p < nq; ++p)
+    if (inv[(size_t)p] != p) {
+      do_swap(p, perm[(size_t)p], c->swaps_after);
+      ++nswaps;
+    }
+  c->relabel = nswaps > 0;
+  return QS_OK;
+}
+
+qs_status qs_circuit_get_relabel(const qs_circuit* c, int* num_swaps) {
+  if (!c || !num_swaps) return QS_ERR_ARG;
+  int n = (int)c->swaps_after.size();
+  for (const auto& v : c->swaps_before) n += (int)v.size();
+  *num_swaps = c->relabel ? n : 0;
+  return QS_OK;
+}
+
 qs_status qs_circuit_get_plan(const qs_circuit* c, int* num_gates, int* num_blocks, int* num_fused) {
   if (!c) return QS_ERR_ARG;
   int fused = 0;
@@ -340,11 +463,36 @@ qs_status qs_circuit_apply(qs_circuit* c, qs_state* s) {
     const qs_status st = qs_circuit_plan(c, QS_PLAN_NONE, 1);
     if (st != QS_OK) return st;
   }
-  for (const CBlock& b : c->blocks) {
+  // lazy relabelling: logical qubit q lives at physical position perm[q]
+  const bool rl = c->relabel && !s->is_density && c->swaps_before.size() == c->blocks.size();
+  std::vector<int> perm((size_t)c->nq), inv((size_t)c->nq);
+  for (int q = 0; q < c->nq; ++q) perm[(size_t)q] = inv[(size_t)q] = q;
+  auto swap_phys = [&](int p1, int p2) {
+    const qs_status st = qs_apply_swap(s, p1, p2);
+    const int q1 = inv[(size_t)p1], q2 = inv[(size_t)p2];
+    perm[(size_t)q1] = p2;
+    perm[(size_t)q2] = p1;
+    inv[(size_t)p1] = q2;
+    inv[(size_t)p2] = q1;
+    return st;
+  };
+  auto mapped = [&](const std::vector<int>& v) {
+    std::vector<int> r(v);
+    if (rl)
+      for (int& q : r) q = perm[(size_t)q];
+    return r;
+  };
+  for (size_t bi = 0; bi < c->blocks.size(); ++bi) {
+    const CBlock& b = c->blocks[bi];
     qs_status st = QS_OK;
+    if (rl)
+      for (const auto& sw : c->swaps_before[bi]) {
+        st = swap_phys(sw.first, sw.second);
+        if (st != QS_OK) return st;
+      }
     if (b.fused) {
       const double* m = c->d_mats + b.mat_off;
-      std::vector<int> t(b.qubits);
+      std::vector<int> t = mapped(b.qubits);
       st = qsapi::gate_pass(s, {}, t, nullptr, m, 0, true);
       if (st == QS_OK && s->is_density) {
         for (int& q : t) q += s->nq;
@@ -352,16 +500,21 @@ qs_status qs_circuit_apply(qs_circuit* c, qs_state* s) {
       }
     } else {
       const CGate& g = c->gates[b.first];
+      const std::vector<int> ct = mapped(g.ctrls), tg = mapped(g.targs);
       if (g.kind == 0)
-        st = qs_apply_ctrl_multi_target(s, g.ctrls.data(), (int)g.ctrls.size(), g.targs.data(), (int)g.targs.size(),
-                                        g.data.data());
+        st = qs_apply_ctrl_multi_target(s, ct.data(), (int)ct.size(), tg.data(), (int)tg.size(), g.data.data());
       else if (g.kind == 1)
-        st = qs_apply_diagonal(s, g.targs.data(), (int)g.targs.size(), g.data.data());
+        st = qs_apply_diagonal(s, tg.data(), (int)tg.size(), g.data.data());
       else
-        st = qs_apply_pauli_gadget(s, g.targs.data(), g.paulis.data(), (int)g.targs.size(), g.theta);
+        st = qs_apply_pauli_gadget(s, tg.data(), g.paulis.data(), (int)tg.size(), g.theta);
     }
     if (st != QS_OK) return st;
   }
+  if (rl)
+    for (const auto& sw : c->swaps_after) {
+      const qs_status st = swap_phys(sw.first, sw.second);
+      if (st != QS_OK) return st;
+    }
   return QS_OK;
 }
 

@@ -317,6 +317,8 @@ cudaError_t launch_gadget_fx(void* amps, const GadgetFxParams& p, cudaStream_t s
 cudaError_t launch_group_fx(void* amps, int op, const GroupFxParams& p, cudaStream_t st);
 // complex64 dense gates on the tensor cores, 3 <= n <= 5 (qs_tc.cu)
 cudaError_t launch_dense_tc(void* amps, const TcParams& p, cudaStream_t st);
+// test of the bounded-wait path: a wait on an mbarrier nothing arrives at, given up after `polls` polls (qs_tc.cu)
+cudaError_t launch_test_wait_timeout(int* err, uint32_t polls, cudaStream_t st);
 // complex128 dense gates on the bf16 tensor cores, exact integer slices, 3 <= n <= 5 kernel targets (qs_tc_ozaki.cu);
 // slices: 7 (49-bit operands, with double-float arithmetic) or 8 (56-bit, with block fixed point)
 cudaError_t launch_dense_ozaki(void* amps, const TcParams& p, int slices, cudaStream_t st);

@@ -481,4 +481,28 @@ cudaError_t launch_dense_tc(void* amps, const TcParams& p, cudaStream_t st) {
   }
 }
 
+// A test of the bounded-wait path: one thread waits on an mbarrier that
+// nothing arrives at, gives up after `polls` polls, and sets the error word as
+// the tensor-core kernels do when a wait runs out.
+__global__ void k_test_wait_timeout(int* err, uint32_t polls) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tcptx::mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    uint32_t spins = 0;
+    bool ran_out = false;
+    while (!tcptx::mbar_try_wait(&bar, 0u))
+      if (++spins > polls) {
+        ran_out = true;
+        break;
+      }
+    if (ran_out) atomicExch(err, 1);
+  }
+}
+
+cudaError_t launch_test_wait_timeout(int* err, uint32_t polls, cudaStream_t st) {
+  k_test_wait_timeout<<<1, 32, 0, st>>>(err, polls);
+  return cudaGetLastError();
+}
+
 }  // namespace qsk

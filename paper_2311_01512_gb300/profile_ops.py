@@ -1,18 +1,19 @@
 """Fixed sequence of hot-path kernel launches for profiling (ncu) at a chosen
-size: one-target gate, 3-qubit diagonal, weight-6 Pauli gadget, dense gates
-on 2 targets (complex128, double-float) and on 3, 4 and 5 targets (complex128,
-bf16 tensor cores), and a 5-target dense gate on a complex64 state (tf32
-tensor cores), each repeated.
+size, in the default complex128 arithmetic (block fixed point): one-target
+gate, 3-qubit diagonal, weight-6 Pauli gadget, a Z-only (phase) gadget, dense
+gates on 2, 3, 4 and 5 targets (bf16 tensor cores, eight integer slices; two
+targets run on the three-target kernel), and a 5-target dense gate on a
+complex64 state (tf32 tensor cores), each repeated.
 
     python -m paper_2311_01512_gb300.profile_ops --qubits 28 --reps 3
 
-With --traffic-csv it instead turns an ncu CSV of dram__bytes_read.sum and
-dram__bytes_write.sum over one repetition of that sequence into DRAM bytes
-per launch, scaled to a full pass over --scale-to qubits (traffic grows with
-the amplitudes processed), keyed by the bench's kernel families and stamped
-with the kernel sources' digest:
+With --traffic-csv it instead turns ncu CSVs of dram__bytes_read.sum and
+dram__bytes_write.sum (one capture per kernel, each over one repetition of
+that sequence) into DRAM bytes per launch, scaled to a full pass over
+--scale-to qubits (traffic grows with the amplitudes processed), keyed by the
+bench's kernel families and stamped with the kernel sources' digest:
 
-    python -m paper_2311_01512_gb300.profile_ops --qubits 28 --traffic-csv traffic28.csv \
+    python -m paper_2311_01512_gb300.profile_ops --qubits 28 --traffic-csv t_gate1.csv t_diag.csv ... \
         --scale-to 30 --out profiles/dram_traffic.json
 
 With --all it instead launches every kernel family of the library once, on
@@ -31,23 +32,25 @@ import json
 import numpy as np
 
 # launch order of one repetition -> the bench's kernel family names
-_FAMILIES = {"k_gate1_df": ["k_gate1"], "k_diag_df": ["k_diag"], "k_gadget_df": ["k_gadget"],
-             "k_dense_ozaki<3": ["k_dense<2>", "k_dense<3>"], "k_dense_ozaki<4": ["k_dense<4>"],
-             "k_dense_ozaki<5": ["k_dense<5>"], "k_dense_tc<5": ["c64 k_dense<5>"]}
+_FAMILIES = {"k_gate1_fx": ["k_gate1"], "k_diag_fx": ["k_diag"], "k_gadget_fx": ["k_gadget"],
+             "k_phase_fx": ["k_phase"], "k_dense_ozaki<3": ["k_dense<2>", "k_dense<3>"],
+             "k_dense_ozaki<4": ["k_dense<4>"], "k_dense_ozaki<5": ["k_dense<5>"], "k_dense_tc<5": ["c64 k_dense<5>"]}
 
 
-def summarize_traffic(path, qubits, scale_to, out):
+def summarize_traffic(paths, qubits, scale_to, out):
     from . import build
-    rows = list(csv.reader(open(path)))
-    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
-    hdr = rows[hi]
-    ki, mi, vi, ii = hdr.index("Kernel Name"), hdr.index("Metric Name"), hdr.index("Metric Value"), hdr.index("ID")
     launches = {}
-    for r in rows[hi + 1:]:
-        if len(r) <= vi:
-            continue
-        d = launches.setdefault(r[ii], {"name": r[ki].split("(")[0].replace("void ", "").replace("qsk::", "")})
-        d[r[mi]] = float(r[vi].replace(",", ""))
+    for n, path in enumerate(paths):
+        rows = list(csv.reader(open(path)))
+        hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+        hdr = rows[hi]
+        ki, mi, vi, ii = (hdr.index("Kernel Name"), hdr.index("Metric Name"), hdr.index("Metric Value"),
+                          hdr.index("ID"))
+        for r in rows[hi + 1:]:
+            if len(r) <= vi:
+                continue
+            d = launches.setdefault((n, r[ii]), {"name": r[ki].split("(")[0].replace("void ", "").replace("qsk::", "")})
+            d[r[mi]] = float(r[vi].replace(",", ""))
     scale = 2.0 ** (scale_to - qubits)
     fam, pending = {}, {k: list(v) for k, v in _FAMILIES.items()}
     for d in launches.values():
@@ -68,7 +71,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--qubits", type=int, default=28)
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--traffic-csv")
+    ap.add_argument("--traffic-csv", nargs="+")
     ap.add_argument("--scale-to", type=int, default=30)
     ap.add_argument("--out", default="profiles/dram_traffic.json")
     ap.add_argument("--all", action="store_true")
@@ -100,6 +103,7 @@ def main(argv=None):
         qs.qs_apply_ctrl_multi_target(s128.handle, [], [17], u)
         qs.qs_apply_diagonal(s128.handle, [1, 7, 20], diag)
         qs.qs_apply_pauli_gadget(s128.handle, [0, 3, 8, 15, 22, nq - 1], [1, 2, 3, 1, 2, 3], 0.4)
+        qs.qs_apply_pauli_gadget(s128.handle, [0, 4, 9, 17], [3, 3, 3, 3], 0.4)
         for n in (2, 3, 4, 5):
             qs.qs_apply_ctrl_multi_target(s128.handle, [], targets[n], mats[n])
         qs.qs_apply_ctrl_multi_target(s64.handle, [], targets[5], mats[5])

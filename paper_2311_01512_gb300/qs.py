@@ -45,6 +45,7 @@ SIGNATURES = {
     "qs_get_info": (_I, [_P, _IP, _IP, _IP, _IP]),
     "qs_test_fail_allocations": (_I, [_I, _I]),
     "qs_test_set_error_word": (_I, [_P]),
+    "qs_test_bounded_wait": (_I, [_P, ctypes.c_uint]),
     "qs_device_ptr": (_I, [_P, ctypes.POINTER(_P)]),
     "qs_set_arithmetic": (_I, [_P, _I, _I]),
     "qs_set_tensor_cores": (_I, [_P, _I]),
@@ -92,6 +93,8 @@ SIGNATURES = {
     "qs_costmodel_train": (_I, [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), _I, _I, _I,
                                 ctypes.c_float, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_float)]),
     "qs_circuit_plan_cost": (_I, [_P, _P, _P, _I, _I]),
+    "qs_circuit_plan_relabel": (_I, [_P, _P, _P, _I, ctypes.c_double]),
+    "qs_circuit_get_relabel": (_I, [_P, _IP]),
     "qs_batch_create": (_I, [_I, _IP, _I, _P, ctypes.POINTER(_P)]),
     "qs_batch_create_mixed": (_I, [_I, _IP, _IP, _I, _P, ctypes.POINTER(_P)]),
     "qs_batch_add_kraus": (_I, [_P, _I, _IP, _I, _DP, _I]),
@@ -322,6 +325,12 @@ def qs_test_set_error_word(h):
     _check(_lib.qs_test_set_error_word(h), "qs_test_set_error_word")
 
 
+def qs_test_bounded_wait(h, polls):
+    """Test hook: a device wait that nothing ends runs out after `polls`
+    polls and sets the handle's error word (see include/qs.h)."""
+    _check(_lib.qs_test_bounded_wait(h, int(polls)), "qs_test_bounded_wait")
+
+
 def qs_calc_norm_or_trace(h):
     out = (ctypes.c_double * 2)()
     _check(_lib.qs_calc_norm_or_trace(h, out), "qs_calc_norm_or_trace")
@@ -461,6 +470,15 @@ class Circuit:
         _check(_lib.qs_circuit_plan_cost(self.handle, model.handle, state_handle, int(max_block_qubits), int(window)),
                "qs_circuit_plan_cost")
         return self.stats()
+
+    def plan_relabel(self, model, state_handle, low_qubits=5, swap_passes=1.2):
+        """Lazy qubit relabelling of the current plan (see include/qs.h);
+        returns the number of SWAP passes it adds."""
+        _check(_lib.qs_circuit_plan_relabel(self.handle, model.handle, state_handle, int(low_qubits),
+                                            float(swap_passes)), "qs_circuit_plan_relabel")
+        n = _I()
+        _check(_lib.qs_circuit_get_relabel(self.handle, ctypes.byref(n)), "qs_circuit_get_relabel")
+        return n.value
 
     def apply(self, state_handle):
         _check(_lib.qs_circuit_apply(self.handle, state_handle), "qs_circuit_apply")

@@ -140,3 +140,28 @@ def test_error_word_reported_once_as_timeout(qs):
     want = orc.apply_ctrl_multi_target(psi, [], [1, 4, 7], u)
     assert float(np.max(np.abs(st.get_amps() - want))) < 1e-14
     st.close()
+
+
+@pytest.mark.gpu
+def test_device_wait_runs_out_and_reports(qs):
+    """A wait on a barrier that nothing arrives at gives up after its bounded
+    number of polls on the GPU and sets the error word; qs_synchronize reports
+    QS_ERR_TIMEOUT once and the handle keeps working."""
+    nq = 8
+    rng = np.random.default_rng(88)
+    psi = wl.random_statevector(nq, rng)
+    st = qs.State(nq, density=False, prec=qs.QS_C128)
+    st.set_amps(psi)
+    qs.qs_synchronize(st.handle)
+    qs.qs_test_bounded_wait(st.handle, 4096)
+    with pytest.raises(qs.QSError) as ei:
+        qs.qs_synchronize(st.handle)
+    assert "QS_ERR_TIMEOUT" in str(ei.value)
+    qs.qs_synchronize(st.handle)
+    with pytest.raises(qs.QSError):
+        qs.qs_test_bounded_wait(st.handle, (1 << 20) + 1)
+    u = wl.haar_unitary(2, rng)
+    qs.qs_apply_ctrl_multi_target(st.handle, [], [5], u)
+    want = orc.apply_ctrl_multi_target(psi, [], [5], u)
+    assert float(np.max(np.abs(st.get_amps() - want))) < 1e-14
+    st.close()

@@ -114,3 +114,37 @@ def test_fused_c64_matches_per_gate_c128_at_22_qubits(qs):
         got = st.get_amps().astype(np.complex128)
         fid = abs(np.vdot(ref, got)) ** 2 / (np.vdot(ref, ref).real * np.vdot(got, got).real)
         assert 1.0 - fid <= 1e-6, (plan, width, 1.0 - fid)
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_relabelled_circuit_matches_oracle(qs, prec):
+    """Lazy relabelling with its SWAP price set so low that every tensor-core
+    block with a qubit among the 5 lowest positions gets SWAPs: the circuit's
+    result must still equal the gate-by-gate oracle (the layout is restored at
+    the end), and replanning clears the relabelling."""
+    from paper_2311_01512_gb300 import costmodel
+    rng = wl.rng_for("relabel-%d" % prec)
+    nq = 13
+    psi = wl.random_statevector(nq, rng)
+    ops = wl.unitary_circuit(nq, 150, rng)
+    want = orc.run_ops(psi, ops, is_density=False)
+    dtype = np.complex128 if prec == 1 else np.complex64
+    st = qs.State(nq, density=False, prec=prec)
+    st.set_amps(psi.astype(dtype))
+    model, _ = costmodel.load()
+    circ = qs.Circuit(nq, ops)
+    circ.plan_cost(model, st.handle, max_block_qubits=5 if prec == 1 else 6, window=16)
+    nswaps = circ.plan_relabel(model, st.handle, low_qubits=5, swap_passes=-1e30)
+    assert nswaps > 0
+    circ.apply(st.handle)
+    qs.qs_synchronize(st.handle)
+    got = st.get_amps().astype(np.complex128)
+    # complex64: 150 gates in FP32-level arithmetic, as in the fused complex64 test
+    tol = 2e-14 if prec == 1 else 150 * 2.0 ** -22 * float(np.max(np.abs(want)))
+    assert float(np.max(np.abs(got - want))) <= tol
+    assert circ.plan_relabel(model, st.handle, low_qubits=0) == 0
+    circ.plan(qs.QS_PLAN_GREEDY, 4)
+    assert circ.plan_relabel(model, st.handle, low_qubits=5, swap_passes=1e30) == 0
+    circ.close()
+    model.close()
+    st.close()
