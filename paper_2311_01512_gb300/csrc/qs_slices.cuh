@@ -160,4 +160,94 @@ QS_HD int64_t combine_levels8(const uint32_t* b) {
   return (int64_t)(acc + (uint64_t)(int64_t)low);
 }
 
+
+// ---------------------------------------------------------------------------
+// Offset-packed amplitude digits.  For s >= 1 the unsigned field d_s + 64 of
+// T sits in 7 bits; the bf16 number whose exponent is 2^7 and whose stored
+// significand is that field equals 128 + (d_s + 64) = d_s + 192, with bit
+// pattern 0x4300 | field.  So the (re, im) word of digit s is two shifted
+// fields and one constant, with no float arithmetic.  The offset adds
+// 192 sum_k b_t(k, n) to each level L = s + t with s >= 1; the tensor-core
+// kernel starts each accumulator (with one initialising MMA) at
+//   P_L(n) = M - 192 sum_{t=0..L-1} sum_k b_t(k, n),
+// M = 0 (K = 64), or M = 1.25 2^23 (K <= 32), where the accumulator then ends
+// as the FP32 number magic + level whose bit pattern is 0x4B200000 + level.
+// Every partial sum stays an integer below 2^24 in magnitude (checked on the
+// host over the extreme digits), so the accumulation stays exact.  The top
+// digit d_0 is signed and keeps the float path.
+// ---------------------------------------------------------------------------
+constexpr int kDigitOffset = 192;
+constexpr float kPreMagic = 10485760.0f;        // 1.25 2^23
+constexpr uint32_t kPreMagicBits = 0x4B200000u;
+constexpr uint32_t kFaddMagicBits = 0x4B400000u;  // 1.5 2^23, added in the epilogue when M = 0
+
+// bit position in T of digit s >= 1 (seven or eight slices)
+template <int KS>
+QS_HD constexpr int digit_pos(int s) { return 1 + 7 * (KS - 1 - s); }
+
+// packed bf16 pair (re in bits 0..15, im in 16..31) of digit S >= 1
+template <int KS, int S>
+QS_HD uint32_t packed_pair(uint64_t tre, uint64_t tim) {
+  constexpr int p = digit_pos<KS>(S);
+  uint32_t im;
+  if constexpr (p >= 16)
+    im = (uint32_t)(tim >> (p - 16)) & 0x7F0000u;
+  else
+    im = (uint32_t)(tim << (16 - p)) & 0x7F0000u;
+  return 0x43004300u | ((uint32_t)(tre >> p) & 127u) | im;
+}
+
+// P = p[0] + 256 p[1] + 65536 p[2] with |p[i]| <= 256 (exact in bf16), each
+// part rounded to nearest, for |P| < 2^24: the B column of the initialising
+// MMA, whose A rows are (1, 256, 65536).
+QS_HD void split_start(int P, int* p) {
+  p[2] = (P + (P >= 0 ? 32768 : -32768)) / 65536;
+  const int r = P - 65536 * p[2];
+  p[1] = (r + (r >= 0 ? 128 : -128)) / 256;
+  p[0] = r - 256 * p[1];
+}
+
+// packed words of digits S..KS-1 into w[S..KS-1]
+template <int KS, int S = 1>
+QS_HD void packed_digits(uint64_t tre, uint64_t tim, uint32_t* w) {
+  w[S] = packed_pair<KS, S>(tre, tim);
+  if constexpr (S + 1 < KS) packed_digits<KS, S + 1>(tre, tim, w);
+}
+
+// T of a double for seven or eight slices
+template <int KS>
+QS_HD uint64_t fixed_ks(uint32_t hw, uint32_t lw, int emax) {
+  if constexpr (KS == 8)
+    return fixed_t8(hw, lw, emax);
+  else
+    return fixed_t(hw, lw, emax);
+}
+
+// top digit d_0 of T as an exact float
+template <int KS>
+QS_HD float top_digit(uint64_t t) {
+  const uint32_t d0 = (uint32_t)((int32_t)(uint32_t)(t >> 32) >> (KS == 8 ? 18 : 11));
+  return qsdf::u2f(0x4B400000u + d0) - 12582912.0f;
+}
+
+// sum_L level_L 2^(7(KS-1-L)) (divided by 2^8, rounded down, for eight
+// slices) from the bit patterns b_L = mb + level_L, merging adjacent levels
+// in 32 bits first: q = 128 level_L + level_(L+1) stays below 2^28 in magnitude.
+template <int KS>
+QS_HD int64_t combine_pairs(const uint32_t* b, uint32_t mb) {
+  const uint32_t off = 129u * mb;
+  const int32_t q0 = (int32_t)(b[0] * 128u + b[1] - off);
+  const int32_t q1 = (int32_t)(b[2] * 128u + b[3] - off);
+  const int32_t q2 = (int32_t)(b[4] * 128u + b[5] - off);
+  if constexpr (KS == 8) {
+    const int32_t q3 = (int32_t)(b[6] * 128u + b[7] - off);
+    return (int64_t)((uint64_t)(int64_t)q0 << 34) + (int64_t)((uint64_t)(int64_t)q1 << 20) +
+           (int64_t)q2 * 64 + (int64_t)(q3 >> 8);
+  } else {
+    const int32_t l6 = (int32_t)(b[6] - mb);
+    return (int64_t)((uint64_t)(int64_t)q0 << 35) + (int64_t)((uint64_t)(int64_t)q1 << 21) +
+           (int64_t)q2 * 128 + (int64_t)l6;
+  }
+}
+
 }  // namespace qsoz
