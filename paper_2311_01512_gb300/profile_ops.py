@@ -16,6 +16,14 @@ bench's kernel families and stamped with the kernel sources' digest:
     python -m paper_2311_01512_gb300.profile_ops --qubits 28 --traffic-csv t_gate1.csv t_diag.csv ... \
         --scale-to 30 --out profiles/dram_traffic.json
 
+With --dense-times it instead times complex128 dense gates (block fixed
+point: eight-slice tensor-core kernels) on a state of --qubits qubits at
+three placements per target count (lowest qubits, spread, highest qubits)
+and one controlled case, each the median of --reps CUDA-event timings after
+one untimed launch, and prints ms and GB/s of amplitudes read and written:
+
+    python -m paper_2311_01512_gb300.profile_ops --qubits 30 --reps 5 --dense-times
+
 With --all it instead launches every kernel family of the library once, on
 a statevector of --qubits qubits in both precisions and a density matrix of
 --qubits / 2 qubits (its Choi vector as large): the streaming gates, the
@@ -67,6 +75,44 @@ def summarize_traffic(paths, qubits, scale_to, out):
     print(json.dumps(rec, indent=1))
 
 
+def dense_times(nq, reps):
+    import torch
+    from . import qs
+    from . import workloads as wl
+    st = qs.State(nq, density=False, prec=qs.QS_C128)
+    st.tensor.real.normal_()
+    st.tensor.imag.normal_()
+    st.tensor /= torch.linalg.vector_norm(st.tensor)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(3)
+    spread = [0, 4, 9, 17, 25]
+    cases = {n: [list(range(n)), spread[:n] if n > 2 else [3, 9], list(range(nq - n, nq))] for n in (2, 3, 4, 5)}
+
+    def timed(ctrls, targs, u):
+        ts = []
+        for r in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st.stream)
+            qs.qs_apply_ctrl_multi_target(st.handle, ctrls, targs, u)
+            e1.record(st.stream)
+            e1.synchronize()
+            if r:
+                ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    nbytes = 2 * 16 * (1 << nq)
+    for n, placements in cases.items():
+        u = wl.haar_unitary(1 << n, rng)
+        for targs in placements:
+            ms = timed([], targs, u)
+            print("%d targets %-18s %8.3f ms %8.1f GB/s" % (n, targs, ms, nbytes / ms / 1e6))
+        c = [q for q in range(nq) if q not in placements[1]][-1]
+        ms = timed([c], placements[1], u)
+        print("%d targets %-18s %8.3f ms %8.1f GB/s (control %d)" % (n, placements[1], ms, nbytes / 2 / ms / 1e6, c))
+    print("norm", qs.qs_calc_norm_or_trace(st.handle).real)
+    st.close()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--qubits", type=int, default=28)
@@ -75,7 +121,11 @@ def main(argv=None):
     ap.add_argument("--scale-to", type=int, default=30)
     ap.add_argument("--out", default="profiles/dram_traffic.json")
     ap.add_argument("--all", action="store_true")
+    ap.add_argument("--dense-times", action="store_true")
     args = ap.parse_args(argv)
+    if args.dense_times:
+        dense_times(args.qubits, args.reps)
+        return
     if args.traffic_csv:
         summarize_traffic(args.traffic_csv, args.qubits, args.scale_to, args.out)
         return
