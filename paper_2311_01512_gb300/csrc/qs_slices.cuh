@@ -207,6 +207,46 @@ QS_HD void split_start(int P, int* p) {
   p[0] = r - 256 * p[1];
 }
 
+// byte permute (PTX prmt / __byte_perm): byte i of the result is byte
+// ((sel >> 4i) & 7) of the eight bytes (y:x)
+QS_HD uint32_t byte_perm(uint32_t x, uint32_t y, uint32_t sel) {
+#if defined(__CUDA_ARCH__)
+  return __byte_perm(x, y, sel);
+#else
+  const uint64_t v = ((uint64_t)y << 32) | x;
+  uint32_t r = 0;
+  for (int i = 0; i < 4; ++i) r |= (uint32_t)((v >> (8 * ((sel >> (4 * i)) & 7))) & 0xFF) << (8 * i);
+  return r;
+#endif
+}
+
+// packed_pair through one byte permute where the field's byte-aligned 16-bit
+// window lies in one 32-bit word of T (all digits but the one at bit 29): the
+// re and im windows side by side, one shift, one mask-and-or.
+template <int KS, int S>
+QS_HD uint32_t packed_pair_fast(uint64_t tre, uint64_t tim) {
+  constexpr int p = digit_pos<KS>(S);
+  constexpr int wb = p / 8;                 // first byte of the window in T
+  constexpr int r = p - 8 * wb;             // the field's offset in it
+  if constexpr (wb == 3) {
+    return packed_pair<KS, S>(tre, tim);
+  } else {
+    constexpr int hiw = wb >= 4;             // which 32-bit word
+    constexpr uint32_t B = (uint32_t)(wb - 4 * hiw);
+    constexpr uint32_t sel = B | ((B + 1) << 4) | ((B + 4) << 8) | ((B + 5) << 12);
+    const uint32_t xr = (uint32_t)(hiw ? tre >> 32 : tre), xi = (uint32_t)(hiw ? tim >> 32 : tim);
+    const uint32_t x = byte_perm(xr, xi, sel);
+    return ((r ? x >> r : x) & 0x007F007Fu) | 0x43004300u;
+  }
+}
+
+// packed words of digits S..KS-1 into w[S..KS-1] (byte-permute form)
+template <int KS, int S = 1>
+QS_HD void packed_digits_fast(uint64_t tre, uint64_t tim, uint32_t* w) {
+  w[S] = packed_pair_fast<KS, S>(tre, tim);
+  if constexpr (S + 1 < KS) packed_digits_fast<KS, S + 1>(tre, tim, w);
+}
+
 // packed words of digits S..KS-1 into w[S..KS-1]
 template <int KS, int S = 1>
 QS_HD void packed_digits(uint64_t tre, uint64_t tim, uint32_t* w) {
@@ -247,6 +287,26 @@ QS_HD int64_t combine_pairs(const uint32_t* b, uint32_t mb) {
     const int32_t l6 = (int32_t)(b[6] - mb);
     return (int64_t)((uint64_t)(int64_t)q0 << 35) + (int64_t)((uint64_t)(int64_t)q1 << 21) +
            (int64_t)q2 * 128 + (int64_t)l6;
+  }
+}
+
+// The same for accumulators started at the magic (bit patterns
+// kPreMagicBits + level, K <= 32, so |level| <= 1310720): the merged words
+// r = 128 b_L + b_(L+1) then stay below 2^32 without wrapping (they equal
+// q + 129 kPreMagicBits mod 2^32 = q + 0xDB200000 with |q| < 1.7 2^27), so
+// they are used unsigned and the offsets leave as one 64-bit constant
+// (divisible by 2^8 where the floor applies).
+template <int KS>
+QS_HD int64_t combine_pairs_pre(const uint32_t* b) {
+  constexpr uint64_t off = (129ull * kPreMagicBits) & 0xFFFFFFFFull;
+  const uint32_t r0 = b[0] * 128u + b[1], r1 = b[2] * 128u + b[3], r2 = b[4] * 128u + b[5];
+  if constexpr (KS == 8) {
+    constexpr uint64_t C = off * ((1ull << 34) + (1ull << 20) + (1ull << 6)) + (off >> 8);
+    const uint32_t r3 = b[6] * 128u + b[7];
+    return (int64_t)(((uint64_t)r0 << 34) + ((uint64_t)r1 << 20) + ((uint64_t)r2 << 6) + (uint64_t)(r3 >> 8) - C);
+  } else {
+    constexpr uint64_t C = off * ((1ull << 35) + (1ull << 21) + (1ull << 7)) + kPreMagicBits;
+    return (int64_t)(((uint64_t)r0 << 35) + ((uint64_t)r1 << 21) + ((uint64_t)r2 << 7) + (uint64_t)b[6] - C);
   }
 }
 

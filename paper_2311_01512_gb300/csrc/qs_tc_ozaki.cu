@@ -581,11 +581,10 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_dense_ozaki_ws(double2* __res
     const int q = warp & 3, eh = warp >> 2;
     const int g = 32 * q + lane;
     const bool row_ok = g < (1 << row_bits);
-    const uint64_t roff = rowoff[g];
     const uint32_t lane_addr = (uint32_t)(32 * q) << 16;
-    uint64_t te[EPE];
+    uint64_t te[EPE];                         // byte offsets of this thread's amplitudes in a tile
 #pragma unroll
-    for (int i = 0; i < EPE; ++i) te[i] = toff[eh * EPE + i];
+    for (int i = 0; i < EPE; ++i) te[i] = (rowoff[g] | toff[eh * EPE + i]) << 4;
     uint64_t xb = insert_zeros(blockIdx.x, p.hi_ins, p.nhi);
     for (int i = 0;; ++i, xb = step(xb, gstep)) {
       const uint64_t c = blockIdx.x + (uint64_t)i * grid;
@@ -596,7 +595,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_dense_ozaki_ws(double2* __res
         break;
       }
       const int egs = meta_ex[m * kRows + g];
-      const uint64_t rb = xb | p.ctrl_mask | roff;
+      char* tp = reinterpret_cast<char*>(psi) + ((xb | p.ctrl_mask) << 4);
       if (wait_ring_warp(accfull + k, (uint32_t)(i / NTM) & 1u, abort_flag)) {
         *abort_flag = 1;
         break;
@@ -624,12 +623,13 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_dense_ozaki_ws(double2* __res
             uint32_t bits[KS];
 #pragma unroll
             for (int L = 0; L < KS; ++L) bits[L] = __float_as_uint(v[L][qq]);
-            const double r = __ll2double_rn(qsoz::combine_pairs<KS>(bits, qsoz::kPreMagicBits));
+            const double r = __ll2double_rn(qsoz::combine_pairs_pre<KS>(bits));
             const int hi = __double2hiint(r);   // 0 only for r = 0, which stays 0
-            o[qq] = __hiloint2double(hi + (hi != 0 ? egs + scl[qq] : 0), __double2loint(r));
+            o[qq] = __hiloint2double(hi != 0 ? hi + egs + scl[qq] : 0, __double2loint(r));
           }
 #pragma unroll
-          for (int qq = 0; qq < 8; qq += 2) psi[rb | te[(cc + qq) >> 1]] = make_double2(o[qq], o[qq + 1]);
+          for (int qq = 0; qq < 8; qq += 2)
+            *reinterpret_cast<double2*>(tp + te[(cc + qq) >> 1]) = make_double2(o[qq], o[qq + 1]);
         }
       }
     }
@@ -638,16 +638,15 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_dense_ozaki_ws(double2* __res
     const int pt = tid - 32 * kWsE, pw = pt >> 5;
     const int g = 16 * pw + (lane >> 1), h = lane & 1;
     const bool row_ok = g < (1 << row_bits);
-    const uint64_t roff = rowoff[g];
-    uint64_t tp[EPP];
+    uint64_t tp[EPP];                         // byte offsets of this thread's amplitudes in a tile
 #pragma unroll
-    for (int i = 0; i < EPP; ++i) tp[i] = toff[h * EPP + i];
+    for (int i = 0; i < EPP; ++i) tp[i] = (rowoff[g] | toff[h * EPP + i]) << 4;
     const uint32_t stg_addr = smem_u32(stg) + (uint32_t)pt * 16u;
     auto issue = [&](uint64_t x, int slot) {
-      const uint64_t rb = x | p.ctrl_mask | roff;
+      const char* base = reinterpret_cast<const char*>(psi) + ((x | p.ctrl_mask) << 4);
 #pragma unroll
       for (int i = 0; i < EPP; ++i)
-        cp_async16(stg_addr + (uint32_t)(slot * W::SLOT + i * PT * 16), row_ok ? (const void*)(psi + (rb | tp[i])) : psi,
+        cp_async16(stg_addr + (uint32_t)(slot * W::SLOT + i * PT * 16), row_ok ? (const void*)(base + tp[i]) : psi,
                    row_ok ? 16u : 0u);
     };
     uint64_t xi = insert_zeros(blockIdx.x, p.hi_ins, p.nhi);   // base of the next tile to issue
@@ -702,7 +701,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_dense_ozaki_ws(double2* __res
           const uint32_t* w = R[i2 + e];
           const uint64_t tr = qsoz::fixed_ks<KS>(w[0], w[1], eg), ti = qsoz::fixed_ks<KS>(w[2], w[3], eg);
           pk[e][0] = pack_bf16(qsoz::top_digit<KS>(tr), qsoz::top_digit<KS>(ti));
-          qsoz::packed_digits<KS>(tr, ti, pk[e]);
+          qsoz::packed_digits_fast<KS>(tr, ti, pk[e]);
         }
         const uint32_t off = canon_off16(g, 2 * (h * EPP + i2), K);
 #pragma unroll

@@ -41,8 +41,8 @@ import numpy as np
 
 # launch order of one repetition -> the bench's kernel family names
 _FAMILIES = {"k_gate1_fx": ["k_gate1"], "k_diag_fx": ["k_diag"], "k_gadget_fx": ["k_gadget"],
-             "k_phase_fx": ["k_phase"], "k_dense_ozaki<3": ["k_dense<2>", "k_dense<3>"],
-             "k_dense_ozaki<4": ["k_dense<4>"], "k_dense_ozaki<5": ["k_dense<5>"], "k_dense_tc<5": ["c64 k_dense<5>"]}
+             "k_phase_fx": ["k_phase"], "k_dense_ozaki_ws<3": ["k_dense<2>", "k_dense<3>"],
+             "k_dense_ozaki_ws<4": ["k_dense<4>"], "k_dense_ozaki<5": ["k_dense<5>"], "k_dense_tc<5": ["c64 k_dense<5>"]}
 
 
 def summarize_traffic(paths, qubits, scale_to, out):

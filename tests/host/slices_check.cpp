@@ -73,9 +73,11 @@ static void check_packed(std::mt19937_64& rng) {
     if (it % 89 == 0) xi = -0.0;
     const int emax = std::max({floor_e, bexp(xr), bexp(xi)}) + (it % 3 == 0 ? 0 : (int)(rng() % 5));
     const uint64_t tr = fixed_of(KS, xr, emax), ti = fixed_of(KS, xi, emax);
-    uint32_t w[KS];
+    uint32_t w[KS], wf[KS];
     qsoz::packed_digits<KS>(tr, ti, w);
+    qsoz::packed_digits_fast<KS>(tr, ti, wf);
     for (int s = 1; s < KS; ++s) {
+      CHECK(w[s] == wf[s], "%d: byte-permute packing of digit %d", KS, s);
       CHECK(bf16_value(w[s]) == (float)(qsoz::kDigitOffset + digit_of(KS, tr, s)), "%d: packed re digit %d", KS, s);
       CHECK(bf16_value(w[s] >> 16) == (float)(qsoz::kDigitOffset + digit_of(KS, ti, s)), "%d: packed im digit %d",
             KS, s);
@@ -90,7 +92,7 @@ static void check_packed(std::mt19937_64& rng) {
   for (int pass = 0; pass < 2; ++pass) {
     const uint32_t mb = pass == 0 ? qsoz::kPreMagicBits : qsoz::kFaddMagicBits;
     const float magic = pass == 0 ? qsoz::kPreMagic : 12582912.0f;
-    const int top = pass == 0 ? (KS == 8 ? 1310720 : 1 << 20) : top64;
+    const int top = pass == 0 ? (KS == 8 ? 1310720 : 1179648) : top64;   // K <= 32 level bounds
     std::uniform_int_distribution<int> lev(-top, top), lev0(-(1 << 20), 1 << 20);
     for (int it = 0; it < 1000000; ++it) {
       uint32_t bits[KS];
@@ -104,7 +106,20 @@ static void check_packed(std::mt19937_64& rng) {
       }
       const __int128 ref = KS == 8 ? (sum >> 8) : sum;
       CHECK((__int128)qsoz::combine_pairs<KS>(bits, mb) == ref, "%d: combine_pairs", KS);
+      if (pass == 0)
+        CHECK((__int128)qsoz::combine_pairs_pre<KS>(bits) == ref, "%d: combine_pairs_pre", KS);
     }
+  }
+
+  // the merged words of combine_pairs_pre do not wrap for any levels within
+  // the K <= 32 bound
+  {
+    const long long top = KS == 8 ? 1310720 : 1179648, off = (129ll * qsoz::kPreMagicBits) & 0xFFFFFFFFll;
+    for (long long hi : {-top, top})
+      for (long long lo : {-top, top}) {
+        const long long r = 128 * hi + lo + off;
+        CHECK(r >= 0 && r < (1ll << 32), "%d: merged word wraps", KS);
+      }
   }
 
   // preloaded accumulators: every partial sum of P_L and the products, in any
