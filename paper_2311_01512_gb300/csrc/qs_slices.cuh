@@ -290,22 +290,23 @@ QS_HD int64_t combine_pairs(const uint32_t* b, uint32_t mb) {
   }
 }
 
-// The same for accumulators started at the magic (bit patterns
-// kPreMagicBits + level, K <= 32, so |level| <= 1310720): the merged words
-// r = 128 b_L + b_(L+1) then stay below 2^32 without wrapping (they equal
-// q + 129 kPreMagicBits mod 2^32 = q + 0xDB200000 with |q| < 1.7 2^27), so
-// they are used unsigned and the offsets leave as one 64-bit constant
-// (divisible by 2^8 where the floor applies).
-template <int KS>
-QS_HD int64_t combine_pairs_pre(const uint32_t* b) {
-  constexpr uint64_t off = (129ull * kPreMagicBits) & 0xFFFFFFFFull;
+// The same with the merged words used unsigned: r = 128 b_L + b_(L+1) equals
+// q + 129 MB mod 2^32, and for the level bounds of the kernels it does not
+// wrap (MB = kPreMagicBits, K <= 32, |level| <= 1310720: r within
+// 0xDB200000 +- 1.7e8; MB = kFaddMagicBits, K <= 64, |level| <= 2621440: r
+// within 0xEB400000 +- 3.39e8 < 2^32), so the offsets leave as one 64-bit
+// constant (divisible by 2^8 where the floor applies).
+template <int KS, uint32_t MB>
+QS_HD int64_t combine_pairs_u(const uint32_t* b) {
+  constexpr uint64_t off = (129ull * MB) & 0xFFFFFFFFull;
   const uint32_t r0 = b[0] * 128u + b[1], r1 = b[2] * 128u + b[3], r2 = b[4] * 128u + b[5];
   if constexpr (KS == 8) {
+    static_assert((off & 255u) == 0, "floor of the last word");
     constexpr uint64_t C = off * ((1ull << 34) + (1ull << 20) + (1ull << 6)) + (off >> 8);
     const uint32_t r3 = b[6] * 128u + b[7];
     return (int64_t)(((uint64_t)r0 << 34) + ((uint64_t)r1 << 20) + ((uint64_t)r2 << 6) + (uint64_t)(r3 >> 8) - C);
   } else {
-    constexpr uint64_t C = off * ((1ull << 35) + (1ull << 21) + (1ull << 7)) + kPreMagicBits;
+    constexpr uint64_t C = off * ((1ull << 35) + (1ull << 21) + (1ull << 7)) + MB;
     return (int64_t)(((uint64_t)r0 << 35) + ((uint64_t)r1 << 21) + ((uint64_t)r2 << 7) + (uint64_t)b[6] - C);
   }
 }

@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(THREADS, CTAS) k_dense_ozaki(double2* __restri
 #pragma unroll
           for (int L = 0; L < kS; ++L)
             bits[L] = kMagicPre ? __float_as_uint(v[L][q]) : __float_as_uint(v[L][q] + 12582912.0f);
-          const double r = __ll2double_rn(qsoz::combine_pairs<KS>(bits, kMB));
+          const double r = __ll2double_rn(qsoz::combine_pairs_u<KS, kMB>(bits));
           const int hi = __double2hiint(r);                // 0 only for r = 0, which stays 0
           o[q] = __hiloint2double(hi + (hi != 0 ? egs + scl[q] : 0), __double2loint(r));
         }
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(THREADS, CTAS) k_dense_ozaki(double2* __restri
         const uint32_t* w = R[i + e];
         const uint64_t tr = qsoz::fixed_ks<KS>(w[0], w[1], eg), ti = qsoz::fixed_ks<KS>(w[2], w[3], eg);
         pk[e][0] = pack_bf16(qsoz::top_digit<KS>(tr), qsoz::top_digit<KS>(ti));
-        qsoz::packed_digits<KS>(tr, ti, pk[e]);
+        qsoz::packed_digits_fast<KS>(tr, ti, pk[e]);
       }
       const uint32_t off = canon_off16(g, 2 * (l0 + i), K);
 #pragma unroll
@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_dense_ozaki_ws(double2* __res
             uint32_t bits[KS];
 #pragma unroll
             for (int L = 0; L < KS; ++L) bits[L] = __float_as_uint(v[L][qq]);
-            const double r = __ll2double_rn(qsoz::combine_pairs_pre<KS>(bits));
+            const double r = __ll2double_rn(qsoz::combine_pairs_u<KS, qsoz::kPreMagicBits>(bits));
             const int hi = __double2hiint(r);   // 0 only for r = 0, which stays 0
             o[qq] = __hiloint2double(hi != 0 ? hi + egs + scl[qq] : 0, __double2loint(r));
           }

@@ -88,11 +88,10 @@ static void check_packed(std::mt19937_64& rng) {
 
   // combine_pairs for both magic patterns (levels within the K <= 32 bound for
   // the preloaded magic, within the K = 64 bound for the added one)
-  const int top64 = KS == 8 ? (5 << 19) : (1 << 22) - 1;
   for (int pass = 0; pass < 2; ++pass) {
     const uint32_t mb = pass == 0 ? qsoz::kPreMagicBits : qsoz::kFaddMagicBits;
     const float magic = pass == 0 ? qsoz::kPreMagic : 12582912.0f;
-    const int top = pass == 0 ? (KS == 8 ? 1310720 : 1179648) : top64;   // K <= 32 level bounds
+    const int top = pass == 0 ? (KS == 8 ? 1310720 : 1179648) : (KS == 8 ? 2621440 : 2359296);   // level bounds
     std::uniform_int_distribution<int> lev(-top, top), lev0(-(1 << 20), 1 << 20);
     for (int it = 0; it < 1000000; ++it) {
       uint32_t bits[KS];
@@ -106,19 +105,21 @@ static void check_packed(std::mt19937_64& rng) {
       }
       const __int128 ref = KS == 8 ? (sum >> 8) : sum;
       CHECK((__int128)qsoz::combine_pairs<KS>(bits, mb) == ref, "%d: combine_pairs", KS);
-      if (pass == 0)
-        CHECK((__int128)qsoz::combine_pairs_pre<KS>(bits) == ref, "%d: combine_pairs_pre", KS);
+      const long long got_u = pass == 0 ? qsoz::combine_pairs_u<KS, qsoz::kPreMagicBits>(bits)
+                                        : qsoz::combine_pairs_u<KS, qsoz::kFaddMagicBits>(bits);
+      CHECK((__int128)got_u == ref, "%d: combine_pairs_u (pass %d)", KS, pass);
     }
   }
 
-  // the merged words of combine_pairs_pre do not wrap for any levels within
-  // the K <= 32 bound
-  {
-    const long long top = KS == 8 ? 1310720 : 1179648, off = (129ll * qsoz::kPreMagicBits) & 0xFFFFFFFFll;
+  // the merged words of combine_pairs_u do not wrap for any levels within
+  // the K <= 32 bound (preloaded magic) or the K <= 64 bound (added magic)
+  for (int pass = 0; pass < 2; ++pass) {
+    const long long top = pass == 0 ? (KS == 8 ? 1310720 : 1179648) : (KS == 8 ? 2621440 : 2359296);
+    const long long off = (129ll * (pass == 0 ? qsoz::kPreMagicBits : qsoz::kFaddMagicBits)) & 0xFFFFFFFFll;
     for (long long hi : {-top, top})
       for (long long lo : {-top, top}) {
         const long long r = 128 * hi + lo + off;
-        CHECK(r >= 0 && r < (1ll << 32), "%d: merged word wraps", KS);
+        CHECK(r >= 0 && r < (1ll << 32), "%d: merged word wraps (pass %d)", KS, pass);
       }
   }
 
