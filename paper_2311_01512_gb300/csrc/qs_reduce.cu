@@ -134,6 +134,31 @@ struct GroupDf {
   int first, count;
 };
 
+// Virtual tile positions handed out in increasing order: ctr[0] is the next
+// position, ctr[1] counts finished blocks; the last block to finish resets
+// both, so the slot reads as zero in the final reduction.  Thread 0 fetches
+// one position ahead (s_v double-buffered), the block reads it after the
+// barrier that ends a tile.
+struct TileCounter {
+  unsigned long long* ctr;
+  __device__ void first(uint64_t* s_v) const {
+    if (threadIdx.x == 0) s_v[0] = atomicAdd(ctr, 1ull);
+    __syncthreads();
+  }
+  __device__ void prefetch(uint64_t* s_v, int it) const {
+    if (threadIdx.x == 0) s_v[(it + 1) & 1] = atomicAdd(ctr, 1ull);
+  }
+  __device__ void finish() const {
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (atomicAdd(ctr + 1, 1ull) == gridDim.x - 1) {
+        atomicExch(ctr, 0ull);
+        atomicExch(ctr + 1, 0ull);
+      }
+    }
+  }
+};
+
 // Tile visited at virtual position v (TileOrder in qs_internal.h): zero bits
 // inserted at the pivots into c = v >> r, then the basis vectors selected by
 // the low r bits of v.
@@ -151,13 +176,16 @@ __device__ __forceinline__ uint64_t ordered_tile(uint64_t v, const TileOrder& o)
 
 // Work mapping: a block takes tiles of 256 E consecutive amplitudes (thread t
 // holds amplitudes t, t + 256, ... of the tile) and runs every group over the
-// tile.  A group whose highest flip bit lies above the tile either visits the
+// tile.  Tiles are handed out in increasing virtual order by a counter
+// (TileCounter), so the blocks stay on neighbouring virtual tiles: a coset of
+// the order is processed while it is in L2, however unevenly the blocks run.  A group whose highest flip bit lies above the tile either visits the
 // whole tile or none of it, so the test is made once per tile and group; the
 // E partner loads of a visited tile are in flight together.
 template <typename R, int E>
 __global__ void __launch_bounds__(256) k_expec_sv(const typename Cplx<R>::T* __restrict__ psi, int nq,
                                                   const PauliTerm* __restrict__ terms, int nterms,
-                                                  double2* __restrict__ partials, const __grid_constant__ TileOrder ord) {
+                                                  double2* __restrict__ partials, const __grid_constant__ TileOrder ord,
+                                                  TileCounter tc) {
   using qsdf::df;
   using T2 = typename Cplx<R>::T;
   extern __shared__ unsigned char sm_raw[];
@@ -188,7 +216,12 @@ __global__ void __launch_bounds__(256) k_expec_sv(const typename Cplx<R>::T* __r
   constexpr uint64_t kTile = 256ull * E;
   const uint64_t dim = 1ull << nq;
   const uint64_t ntiles = dim > kTile ? dim / kTile : 1;
-  for (uint64_t vt = blockIdx.x; vt < ntiles; vt += gridDim.x) {
+  __shared__ uint64_t s_v[2];
+  tc.first(s_v);
+  for (int it = 0;; ++it) {
+    const uint64_t vt = s_v[it & 1];
+    if (vt >= ntiles) break;
+    tc.prefetch(s_v, it);
     const uint64_t base = ordered_tile(vt, ord) * kTile;
     uint64_t iu[E];
     bool ok[E];
@@ -250,7 +283,9 @@ __global__ void __launch_bounds__(256) k_expec_sv(const typename Cplx<R>::T* __r
         }
       }
     }
+    __syncthreads();                        // the prefetched position is visible, the other slot free
   }
+  tc.finish();
   const double2 s = block_sum(make_double2(qsdf::finish(acc), 0.0));
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
@@ -261,7 +296,7 @@ template <int E>
 __global__ void __launch_bounds__(256) k_expec_sv_f64(const double2* __restrict__ psi, int nq,
                                                       const PauliTerm* __restrict__ terms, int nterms,
                                                       double2* __restrict__ partials,
-                                                      const __grid_constant__ TileOrder ord) {
+                                                      const __grid_constant__ TileOrder ord, TileCounter tc) {
   extern __shared__ unsigned char sm_raw[];
   PauliTerm* ts = reinterpret_cast<PauliTerm*>(sm_raw);
   GroupDf* gs = reinterpret_cast<GroupDf*>(ts + nterms);
@@ -286,7 +321,12 @@ __global__ void __launch_bounds__(256) k_expec_sv_f64(const double2* __restrict_
   constexpr uint64_t kTile = 256ull * E;
   const uint64_t dim = 1ull << nq;
   const uint64_t ntiles = dim > kTile ? dim / kTile : 1;
-  for (uint64_t vt = blockIdx.x; vt < ntiles; vt += gridDim.x) {
+  __shared__ uint64_t s_v[2];
+  tc.first(s_v);
+  for (int it = 0;; ++it) {
+    const uint64_t vt = s_v[it & 1];
+    if (vt >= ntiles) break;
+    tc.prefetch(s_v, it);
     const uint64_t base = ordered_tile(vt, ord) * kTile;
     uint64_t iu[E];
     bool ok[E];
@@ -331,7 +371,9 @@ __global__ void __launch_bounds__(256) k_expec_sv_f64(const double2* __restrict_
         }
       }
     }
+    __syncthreads();                        // the prefetched position is visible, the other slot free
   }
+  tc.finish();
   const double2 s = block_sum(make_double2(acc, 0.0));
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
@@ -568,16 +610,21 @@ cudaError_t launch_expec_dm(qs_prec prec, const void* amps, int nq, const PauliT
 // tiles together and a coset of the tile order is processed while it is in
 // L2.  The other partial slots are zeroed (the final sum stays in a fixed
 // order for a given kernel and GPU).
+// The last partial slot holds the kernels' TileCounter (zeroed here with the
+// unused slots, and zero again when the kernel ends), so the grid is at most
+// kReduceBlocks - 1.
 template <typename K>
 static cudaError_t resident_grid(K kernel, size_t smem, double2* partials, cudaStream_t st, unsigned* grid) {
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem);
   if (e != cudaSuccess) return e;
   const int g = per_sm > 0 ? per_sm * num_sms() : 1;
-  *grid = (unsigned)(g < kReduceBlocks ? g : kReduceBlocks);
-  if (*grid < (unsigned)kReduceBlocks)
-    return cudaMemsetAsync(partials + *grid, 0, sizeof(double2) * (kReduceBlocks - *grid), st);
-  return cudaSuccess;
+  *grid = (unsigned)(g < kReduceBlocks - 1 ? g : kReduceBlocks - 1);
+  return cudaMemsetAsync(partials + *grid, 0, sizeof(double2) * (kReduceBlocks - *grid), st);
+}
+
+static TileCounter tile_counter(double2* partials) {
+  return TileCounter{reinterpret_cast<unsigned long long*>(partials + kReduceBlocks - 1)};
 }
 
 template <typename R, int E>
@@ -595,7 +642,7 @@ static cudaError_t expec_sv_u(const void* amps, int nq, const PauliTerm* terms, 
   const cudaError_t e = resident_grid(k_expec_sv<R, E>, smem, partials, st, &grid);
   if (e != cudaSuccess) return e;
   k_expec_sv<R, E><<<grid, 256, smem, st>>>(static_cast<const typename Cplx<R>::T*>(amps), nq, terms, nterms,
-                                            partials, ord);
+                                            partials, ord, tile_counter(partials));
   return cudaGetLastError();
 }
 
@@ -616,7 +663,7 @@ cudaError_t launch_expec_sv(qs_prec prec, const void* amps, int nq, const PauliT
     const cudaError_t e = resident_grid(k_expec_sv_f64<4>, per * (size_t)nterms, partials, st, &grid);
     if (e != cudaSuccess) return e;
     k_expec_sv_f64<4><<<grid, 256, per * (size_t)nterms, st>>>(static_cast<const double2*>(amps), nq, terms, nterms,
-                                                                partials, ord);
+                                                                partials, ord, tile_counter(partials));
     return cudaGetLastError();
   }
   // tiles of 1024 amplitudes (28 qubits, 8 random terms: 6.9 ms against 7.5

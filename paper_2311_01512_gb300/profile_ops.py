@@ -24,6 +24,14 @@ one untimed launch, and prints ms and GB/s of amplitudes read and written:
 
     python -m paper_2311_01512_gb300.profile_ops --qubits 30 --reps 5 --dense-times
 
+With --expec-times it instead times the statevector Pauli-sum expectation
+(qs_expec_pauli_sum, wall clock around the synchronous call, median of
+--reps after one untimed call) on a seeded complex128 state of --qubits
+qubits with 8 and 100 random terms, in block fixed point (native FP64
+reduction) and in double-float:
+
+    python -m paper_2311_01512_gb300.profile_ops --qubits 28 --reps 5 --expec-times
+
 With --all it instead launches every kernel family of the library once, on
 a statevector of --qubits qubits in both precisions and a density matrix of
 --qubits / 2 qubits (its Choi vector as large): the streaming gates, the
@@ -113,6 +121,37 @@ def dense_times(nq, reps):
     st.close()
 
 
+def expec_times(nq, reps):
+    import time
+    import torch
+    from . import qs
+    from . import workloads as wl
+    stream = torch.cuda.Stream()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    with torch.cuda.stream(stream):
+        psi = torch.randn(1 << nq, dtype=torch.complex128, device="cuda", generator=gen)
+        psi /= torch.linalg.vector_norm(psi)
+    stream.synchronize()
+    st = qs.State(nq, prec=qs.QS_C128, stream=stream, storage=psi)
+    rng = np.random.default_rng(1)
+    out = {}
+    for arith, code in (("fx", qs.QS_ARITH_FX), ("df", qs.QS_ARITH_DF)):
+        qs.qs_set_arithmetic(st.handle, code)
+        for nterms in (8, 100):
+            paulis, coeffs = wl.random_pauli_sum(nq, nterms, rng)
+            qs.qs_expec_pauli_sum(st.handle, paulis, coeffs)
+            ts = []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                v = qs.qs_expec_pauli_sum(st.handle, paulis, coeffs)
+                ts.append(time.perf_counter() - t0)
+            out["%s_%d_terms" % (arith, nterms)] = {"ms_median": round(1e3 * float(np.median(ts)), 3),
+                                                     "value": float(v.real)}
+    print(json.dumps(out))
+    st.close()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--qubits", type=int, default=28)
@@ -122,7 +161,11 @@ def main(argv=None):
     ap.add_argument("--out", default="profiles/dram_traffic.json")
     ap.add_argument("--all", action="store_true")
     ap.add_argument("--dense-times", action="store_true")
+    ap.add_argument("--expec-times", action="store_true")
     args = ap.parse_args(argv)
+    if args.expec_times:
+        expec_times(args.qubits, args.reps)
+        return
     if args.dense_times:
         dense_times(args.qubits, args.reps)
         return
