@@ -134,45 +134,47 @@ __host__ __device__ constexpr int scale_off() { return KS == 8 ? 53 : 54; }
 // Per-CTA constants of a dense gate: the column exponent maxima of B (in
 // csc), B's digit slices, the initialising MMA's operands (A rows
 // (1, 256, 65536, 0, ...), B columns holding P_L(n) in three parts), the
-// target offsets of the group members and the row offsets of the tile.
+// target offsets of the group members and the row offsets of the tile.  Every
+// step runs over all (column, row) pairs of B at once, the maxima and the
+// digit column sums (colsum: KS x N ints) through shared-memory atomics, so
+// the setup is short next to one tile even for small states.
 template <int NT, int KS, bool kMagicPre>
 __device__ void tile_constants(const TcParams& p, unsigned char* b_dig, unsigned char* a_pre, unsigned char* b_pre,
-                               int* csc, uint64_t* toff, uint64_t* rowoff, int tid, int nthr) {
+                               int* csc, int* colsum, uint64_t* toff, uint64_t* rowoff, int tid, int nthr) {
   constexpr int D = 1 << NT, K = 2 * D, N = 2 * D, BBYTES = N * K * 2;
-  for (int n = tid; n < N; n += nthr) {
-    int e = emax_floor<KS>();
-    for (int k = 0; k < K; ++k) e = max(e, qsoz::biased_exp((uint32_t)__double2hiint(realified(p, D, k, n))));
-    csc[n] = e;
+  for (int n = tid; n < N; n += nthr) csc[n] = emax_floor<KS>();
+  for (int i = tid; i < KS * N; i += nthr) colsum[i] = 0;
+  __syncthreads();
+  for (int idx = tid; idx < N * K; idx += nthr) {
+    const int n = idx / K, k = idx % K;
+    atomicMax(csc + n, qsoz::biased_exp((uint32_t)__double2hiint(realified(p, D, k, n))));
   }
   __syncthreads();
-  // one thread per column: digit slices, their column sums, the starts P_L(n)
-  for (int n = tid; n < N; n += nthr) {
-    int colsum[KS];
+  for (int idx = tid; idx < N * K; idx += nthr) {
+    const int n = idx / K, k = idx % K;
+    const double v = realified(p, D, k, n);
+    float f[KS];
+    digits<KS>((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v), csc[n], f);
+    const uint32_t off = canon_off16(n, k, K);
 #pragma unroll
-    for (int t = 0; t < KS; ++t) colsum[t] = 0;
-    for (int k = 0; k < K; ++k) {
-      const double v = realified(p, D, k, n);
-      float f[KS];
-      digits<KS>((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v), csc[n], f);
-      const uint32_t off = canon_off16(n, k, K);
-#pragma unroll
-      for (int t = 0; t < KS; ++t) {
-        *reinterpret_cast<uint16_t*>(b_dig + t * BBYTES + off) = (uint16_t)(pack_bf16(f[t], 0.0f) & 0xFFFFu);
-        colsum[t] += (int)f[t];
-      }
+    for (int t = 0; t < KS; ++t) {
+      *reinterpret_cast<uint16_t*>(b_dig + t * BBYTES + off) = (uint16_t)(pack_bf16(f[t], 0.0f) & 0xFFFFu);
+      if (f[t] != 0.0f) atomicAdd(colsum + t * N + n, (int)f[t]);
     }
+  }
+  __syncthreads();
+  // the start values P_L(n) = M - 192 sum_{t < L} colsum_t(n), one (L, n) per thread
+  for (int idx = tid; idx < KS * N; idx += nthr) {
+    const int L = idx / N, n = idx % N;
     int corr = 0;
+    for (int t = 0; t < L; ++t) corr += colsum[t * N + n];
+    int pp[3];
+    qsoz::split_start((kMagicPre ? (int)qsoz::kPreMagic : 0) - qsoz::kDigitOffset * corr, pp);
+    const int col = L * N + n;
 #pragma unroll
-    for (int L = 0; L < KS; ++L) {
-      if (L > 0) corr += colsum[L - 1];
-      int pp[3];
-      qsoz::split_start((kMagicPre ? (int)qsoz::kPreMagic : 0) - qsoz::kDigitOffset * corr, pp);
-      const int col = L * N + n;
-#pragma unroll
-      for (int k = 0; k < 16; ++k)
-        *reinterpret_cast<uint16_t*>(b_pre + canon_off16(col, k, 16)) =
-            (uint16_t)(pack_bf16(k < 3 ? (float)pp[k] : 0.0f, 0.0f) & 0xFFFFu);
-    }
+    for (int k = 0; k < 16; ++k)
+      *reinterpret_cast<uint16_t*>(b_pre + canon_off16(col, k, 16)) =
+          (uint16_t)(pack_bf16(k < 3 ? (float)pp[k] : 0.0f, 0.0f) & 0xFFFFu);
   }
   for (int idx = tid; idx < kRows * 16; idx += nthr) {
     const int g = idx >> 4, k = idx & 15;
@@ -244,11 +246,12 @@ __global__ void __launch_bounds__(THREADS, CTAS) k_dense_ozaki(double2* __restri
   uint64_t* mbar = tile_base + 2;                                     // 2
   int* csc = reinterpret_cast<int*>(mbar + 2);                        // N: (column exponent - 2100) << 20
   int* rowexp = csc + N;                                              // 2 x kRows: exponent field of the row maximum
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(rowexp + 2 * kRows);
+  int* colsum = rowexp + 2 * kRows;                                   // KS x N: digit column sums (setup)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(colsum + kS * N);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  tile_constants<NT, KS, kMagicPre>(p, b_dig, a_pre, b_pre, csc, toff, rowoff, tid, THREADS);
+  tile_constants<NT, KS, kMagicPre>(p, b_dig, a_pre, b_pre, csc, colsum, toff, rowoff, tid, THREADS);
   const int row_bits = p.tile_bits - NT;
   for (int g = tid; g < kRows; g += THREADS) {
     rowexp[g] = 0;
@@ -428,7 +431,7 @@ template <int NT, int THREADS, int NBUF, int CTAS, int kS>
 static cudaError_t dense_ozaki_nt(void* amps, const TcParams& p, cudaStream_t st) {
   constexpr int D = 1 << NT, K = 2 * D, N = 2 * D;
   constexpr size_t smem = (size_t)NBUF * kS * (kRows * K * 2) + (size_t)kS * (N * K * 2) + kRows * 32 +
-                          (size_t)kS * N * 32 + 8 * (D + kRows + 4) + 4 * (N + 2 * kRows) + 16;
+                          (size_t)kS * N * 32 + 8 * (D + kRows + 4) + 4 * (N + 2 * kRows + kS * N) + 16;
   static_assert(smem * CTAS <= 227 * 1024, "shared memory");
   static_assert(CTAS * tmem_cols(NBUF * kS * N) <= 512, "tensor memory");
   static bool attr_done = false;
@@ -508,7 +511,8 @@ struct Ws {
   static constexpr size_t bar_off = rowoff_off + 8 * kRows;
   static constexpr size_t csc_off = bar_off + 8 * (2 * NA + 2 * NTM + NM);
   static constexpr size_t ex_off = csc_off + 4 * N;
-  static constexpr size_t slot_off = ex_off + 4 * (size_t)NM * kRows;
+  static constexpr size_t colsum_off = ex_off + 4 * (size_t)NM * kRows;
+  static constexpr size_t slot_off = colsum_off + 4 * (size_t)KS * N;
   static constexpr size_t bytes = slot_off + 16;
   static_assert(LCOLS <= TSTRIDE && NTM * TSTRIDE <= 512, "tensor memory");
   static_assert(bytes <= 227 * 1024, "shared memory");
@@ -537,11 +541,12 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_dense_ozaki_ws(double2* __res
   uint64_t* mready = tempty + NTM;
   int* csc = reinterpret_cast<int*>(smem + W::csc_off);
   int* meta_ex = reinterpret_cast<int*>(smem + W::ex_off);
+  int* colsum = reinterpret_cast<int*>(smem + W::colsum_off);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + W::slot_off);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + W::slot_off + 4);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  tile_constants<NT, KS, true>(p, b_dig, a_pre, b_pre, csc, toff, rowoff, tid, kWsThreads);
+  tile_constants<NT, KS, true>(p, b_dig, a_pre, b_pre, csc, colsum, toff, rowoff, tid, kWsThreads);
   if (tid == 0) {
 #pragma unroll
     for (int j = 0; j < NA; ++j) {
@@ -768,18 +773,22 @@ static cudaError_t dense_ozaki_ws(void* amps, const TcParams& p, cudaStream_t st
 // double-buffered 256-thread CTAs; 4 targets 11.2 ms as two 256-thread CTAs
 // against 13.9 ms as one double-buffered 512-thread CTA).  Tensor memory
 // (seven levels of N columns per buffer) bounds the CTAs per SM.
+// Passes of fewer tiles than SMs (small states) go to the single-CTA kernels,
+// whose setup is lighter than the warp-specialised kernel's (one tile per CTA
+// leaves nothing to pipeline).
 cudaError_t launch_dense_ozaki(void* amps, const TcParams& p, int slices, cudaStream_t st) {
+  const bool small = p.ntiles < (uint64_t)num_sms();
   if (slices == 8) {
     switch (p.n) {
-      case 3: return dense_ozaki_ws<3, 8>(amps, p, st);
-      case 4: return dense_ozaki_ws<4, 8>(amps, p, st);
+      case 3: return small ? dense_ozaki_nt<3, 128, 1, 4, 8>(amps, p, st) : dense_ozaki_ws<3, 8>(amps, p, st);
+      case 4: return small ? dense_ozaki_nt<4, 256, 1, 2, 8>(amps, p, st) : dense_ozaki_ws<4, 8>(amps, p, st);
       case 5: return dense_ozaki_nt<5, 512, 1, 1, 8>(amps, p, st);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (p.n) {
-    case 3: return dense_ozaki_ws<3, 7>(amps, p, st);
-    case 4: return dense_ozaki_ws<4, 7>(amps, p, st);
+    case 3: return small ? dense_ozaki_nt<3, 128, 1, 4, 7>(amps, p, st) : dense_ozaki_ws<3, 7>(amps, p, st);
+    case 4: return small ? dense_ozaki_nt<4, 256, 1, 2, 7>(amps, p, st) : dense_ozaki_ws<4, 7>(amps, p, st);
     case 5: return dense_ozaki_nt<5, 512, 1, 1, 7>(amps, p, st);
     default: return cudaErrorInvalidValue;
   }
