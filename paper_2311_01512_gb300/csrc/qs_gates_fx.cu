@@ -105,16 +105,26 @@ __global__ void __launch_bounds__(256) k_diag_fx(double2* __restrict__ psi, cons
 #pragma unroll
   for (int q = 0; q < N; ++q) tp[q] = p.tpos[q];
   __syncthreads();
+  // two amplitudes per iteration (i and i + stride): both loads are in flight together
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.namps; i += stride) {
-    int j = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.namps; i += 2 * stride) {
+    const uint64_t i2 = i + stride;
+    const bool has2 = i2 < p.namps;
+    const double2 v0 = psi[i];
+    const double2 v1 = has2 ? psi[i2] : make_double2(0.0, 0.0);
 #pragma unroll
-    for (int q = 0; q < N; ++q) j |= (int)((i >> tp[q]) & 1) << q;
-    const double2 v = psi[i];
-    const Wd wr = words(v.x), wi = words(v.y);
-    const uint32_t exf = emax2(wr, wi);
-    const DiagFxEntry e = d[j];
-    psi[i] = cmul(part(e.re), part(e.im), part(e.nim), cfx(wr, wi, exf), qsfx::scale_for((int)(exf >> 20), e.em));
+    for (int u = 0; u < 2; ++u) {
+      const uint64_t iu = u ? i2 : i;
+      if (u && !has2) break;
+      const double2 v = u ? v1 : v0;
+      int j = 0;
+#pragma unroll
+      for (int q = 0; q < N; ++q) j |= (int)((iu >> tp[q]) & 1) << q;
+      const Wd wr = words(v.x), wi = words(v.y);
+      const uint32_t exf = emax2(wr, wi);
+      const DiagFxEntry e = d[j];
+      psi[iu] = cmul(part(e.re), part(e.im), part(e.nim), cfx(wr, wi, exf), qsfx::scale_for((int)(exf >> 20), e.em));
+    }
   }
 }
 
@@ -156,14 +166,24 @@ __global__ void __launch_bounds__(256) k_gadget_fx(double2* __restrict__ psi, co
 // Phase gadget: alpha_i -> (c + i s_i) alpha_i, s_i = -+sin(phi) by parity.
 __global__ void __launch_bounds__(256) k_phase_fx(double2* __restrict__ psi, const __grid_constant__ GadgetFxParams p) {
   const Part c = part(p.c), s = part(p.s), ns = part(p.ns);
+  // two amplitudes per iteration (i and i + stride): both loads are in flight together
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.nwork; i += stride) {
-    const double2 v = psi[i];
-    const Wd wr = words(v.x), wi = words(v.y);
-    const uint32_t exf = emax2(wr, wi);
-    const bool odd = parity64(i & p.yz);
-    const Part si = odd ? ns : s, nsi = odd ? s : ns;
-    psi[i] = cmul(c, si, nsi, cfx(wr, wi, exf), qsfx::scale_for((int)(exf >> 20), p.em));
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.nwork; i += 2 * stride) {
+    const uint64_t i2 = i + stride;
+    const bool has2 = i2 < p.nwork;
+    const double2 v0 = psi[i];
+    const double2 v1 = has2 ? psi[i2] : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const uint64_t iu = u ? i2 : i;
+      if (u && !has2) break;
+      const double2 v = u ? v1 : v0;
+      const Wd wr = words(v.x), wi = words(v.y);
+      const uint32_t exf = emax2(wr, wi);
+      const bool odd = parity64(iu & p.yz);
+      const Part si = odd ? ns : s, nsi = odd ? s : ns;
+      psi[iu] = cmul(c, si, nsi, cfx(wr, wi, exf), qsfx::scale_for((int)(exf >> 20), p.em));
+    }
   }
 }
 
