@@ -1,4 +1,4 @@
-// Host driver for the block fixed-point arithmetic (qs_fx.cuh): reads dot
+// Host program for the block fixed-point arithmetic (qs_fx.cuh): reads dot
 // products from stdin and prints what the kernels compute for them, so that
 // the Python test can compare with exact rational arithmetic.
 //
