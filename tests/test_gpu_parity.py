@@ -492,7 +492,7 @@ def test_tensor_core_gate_matches_cuda_cores(qs, nq, n, s, place):
 
 @pytest.mark.parametrize("nq,n,s", [(5, 5, 0), (8, 3, 2), (10, 4, 1), (12, 5, 0), (13, 3, 0), (14, 4, 2),
                                      (3, 2, 0), (4, 2, 1), (9, 2, 3), (13, 2, 0), (16, 5, 1), (17, 3, 1),
-                                     (19, 4, 0), (20, 3, 0), (20, 2, 1), (21, 4, 1)])
+                                     (19, 4, 0), (20, 3, 0), (20, 2, 1), (21, 4, 1), (20, 5, 0), (21, 5, 1)])
 @pytest.mark.parametrize("kind", ["haar", "wide", "sparse"])
 @pytest.mark.parametrize("place", ["random", "lowest", "highest"])
 @pytest.mark.parametrize("arith", ["fx", "df"])
@@ -503,8 +503,9 @@ def test_complex128_tensor_core_gate(qs, nq, n, s, kind, place, arith):
     fixed point runs eight slices (56-bit operands), double-float seven.  Two
     targets run on the three-target kernel with an identity on a free qubit;
     (3, 2, 0) and (4, 2, 1) leave a single free qubit, so the tile has one row.
-    Passes of fewer tiles than SMs run the single-CTA kernels, larger ones (the
-    19-21-qubit cases, 256-1024 tiles) the warp-specialised kernel."""
+    Passes of fewer tiles than SMs run the single-CTA kernels; larger 2-4-target
+    passes (the 19-21-qubit cases, 256-1024 tiles) the warp-specialised kernel,
+    and five targets the single-CTA kernel at every size (here up to 256 tiles)."""
     rng = np.random.default_rng(900 + 31 * nq + 7 * n + s + len(kind) + 3 * len(place))
     qsel = [int(x) for x in rng.choice(nq, n + s, replace=False)]
     if place == "lowest":
