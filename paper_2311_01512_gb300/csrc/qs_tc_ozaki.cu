@@ -145,13 +145,15 @@ __device__ void tile_constants(const TcParams& p, unsigned char* b_dig, unsigned
   for (int n = tid; n < N; n += nthr) csc[n] = emax_floor<KS>();
   for (int i = tid; i < KS * N; i += nthr) colsum[i] = 0;
   __syncthreads();
+  // column fastest across threads: the lanes of a warp update different
+  // columns' maxima and sums (no same-address atomics)
   for (int idx = tid; idx < N * K; idx += nthr) {
-    const int n = idx / K, k = idx % K;
+    const int n = idx % N, k = idx / N;
     atomicMax(csc + n, qsoz::biased_exp((uint32_t)__double2hiint(realified(p, D, k, n))));
   }
   __syncthreads();
   for (int idx = tid; idx < N * K; idx += nthr) {
-    const int n = idx / K, k = idx % K;
+    const int n = idx % N, k = idx / N;
     const double v = realified(p, D, k, n);
     float f[KS];
     digits<KS>((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v), csc[n], f);
