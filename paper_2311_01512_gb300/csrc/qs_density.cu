@@ -76,14 +76,17 @@ __global__ void __launch_bounds__(256) k_group(typename Cplx<R>::T* __restrict__
         idx[m] = v;
       }
       if (OP == G_DEPHASE2) {
+        // the 12 scaled members (those with t1 or t2 differing between the two
+        // halves), loaded in two batches of six before their stores, since a
+        // load cannot move above a store to the same array
+        constexpr int sc[12] = {1, 2, 3, 4, 6, 7, 8, 9, 11, 12, 13, 14};
 #pragma unroll
-        for (int m = 0; m < 16; ++m) {
-          const bool d1 = ((m >> 0) & 1) != ((m >> 2) & 1);
-          const bool d2 = ((m >> 1) & 1) != ((m >> 3) & 1);
-          if (d1 || d2) {
-            const T2 a = rho[idx[m]];
-            rho[idx[m]] = mk<R>(f0 * a.x, f0 * a.y);
-          }
+        for (int b0 = 0; b0 < 12; b0 += 6) {
+          T2 a[6];
+#pragma unroll
+          for (int u = 0; u < 6; ++u) a[u] = rho[idx[sc[b0 + u]]];
+#pragma unroll
+          for (int u = 0; u < 6; ++u) rho[idx[sc[b0 + u]]] = mk<R>(f0 * a[u].x, f0 * a[u].y);
         }
       } else {  // two-qubit depolarising
         const T2 a = rho[idx[0]], b = rho[idx[5]], c = rho[idx[10]], d = rho[idx[15]];
@@ -91,11 +94,14 @@ __global__ void __launch_bounds__(256) k_group(typename Cplx<R>::T* __restrict__
         rho[idx[5]] = mk<R>(f0 * b.x + f1 * ((a.x + c.x) + d.x), f0 * b.y + f1 * ((a.y + c.y) + d.y));
         rho[idx[10]] = mk<R>(f0 * c.x + f1 * ((a.x + b.x) + d.x), f0 * c.y + f1 * ((a.y + b.y) + d.y));
         rho[idx[15]] = mk<R>(f0 * d.x + f1 * ((a.x + b.x) + c.x), f0 * d.y + f1 * ((a.y + b.y) + c.y));
+        constexpr int oth[12] = {1, 2, 3, 4, 6, 7, 8, 9, 11, 12, 13, 14};
 #pragma unroll
-        for (int m = 0; m < 16; ++m) {
-          if (m == 0 || m == 5 || m == 10 || m == 15) continue;
-          const T2 x = rho[idx[m]];
-          rho[idx[m]] = mk<R>(f2 * x.x, f2 * x.y);
+        for (int b0 = 0; b0 < 12; b0 += 6) {         // loads of a batch before its stores
+          T2 x[6];
+#pragma unroll
+          for (int u = 0; u < 6; ++u) x[u] = rho[idx[oth[b0 + u]]];
+#pragma unroll
+          for (int u = 0; u < 6; ++u) rho[idx[oth[b0 + u]]] = mk<R>(f2 * x[u].x, f2 * x[u].y);
         }
       }
     }

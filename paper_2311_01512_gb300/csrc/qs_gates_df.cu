@@ -362,10 +362,14 @@ __global__ void __launch_bounds__(256) k_group_df(double2* __restrict__ rho, con
         }
         rho[idx[mem[m]]] = make_double2(qsdf::finish(re), qsdf::finish(im));
       }
+      constexpr int oth[12] = {1, 2, 3, 4, 6, 7, 8, 9, 11, 12, 13, 14};
 #pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        if (m == 0 || m == 5 || m == 10 || m == 15) continue;
-        rho[idx[m]] = scale_df(f2, split2(rho[idx[m]]));
+      for (int b0 = 0; b0 < 12; b0 += 6) {            // loads of a batch before its stores
+        double2 x[6];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) x[u] = rho[idx[oth[b0 + u]]];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) rho[idx[oth[b0 + u]]] = scale_df(f2, split2(x[u]));
       }
     }
   }

@@ -253,13 +253,32 @@ __global__ void __launch_bounds__(256) k_group_fx(double2* __restrict__ rho, con
         idx[m] = v;
       }
       constexpr int mem[4] = {0, 5, 10, 15};
+      // the 12 other members, scaled one by one, in three batches of four;
+      // each batch is loaded before the stores of the one before it (a load
+      // cannot move above a store to the same array)
+      constexpr int oth[12] = {1, 2, 3, 4, 6, 7, 8, 9, 11, 12, 13, 14};
+      double2 ob[2][4];
+      auto scale_batch = [&](const double2* v, int b0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const Wd vr = words(v[u].x), vi = words(v[u].y);
+          const uint32_t e = emax2(vr, vi);
+          const CPart x = cfx(vr, vi, e);
+          const qsfx::Scale se = qsfx::scale_for((int)(e >> 20), p.em[2]);
+          rho[idx[oth[b0 + u]]] = make_double2(lin1(x.re, f[2], se), lin1(x.im, f[2], se));
+        }
+      };
       Wd wr[4], wi[4];
       uint32_t ex = 0;
+      double2 dv[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) dv[m] = rho[idx[mem[m]]];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ob[0][u] = rho[idx[oth[u]]];
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
-        const double2 v = rho[idx[mem[m]]];
-        wr[m] = words(v.x);
-        wi[m] = words(v.y);
+        wr[m] = words(dv[m].x);
+        wi[m] = words(dv[m].y);
         ex = max(ex, emax2(wr[m], wi[m]));
       }
       CPart s[4];
@@ -280,15 +299,12 @@ __global__ void __launch_bounds__(256) k_group_fx(double2* __restrict__ rho, con
         rho[idx[mem[m]]] = make_double2(qsfx::finish_s(re, s0), qsfx::finish_s(im, s0));
       }
 #pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        if (m == 0 || m == 5 || m == 10 || m == 15) continue;
-        const double2 v = rho[idx[m]];
-        const Wd vr = words(v.x), vi = words(v.y);
-        const uint32_t e = emax2(vr, vi);
-        const CPart x = cfx(vr, vi, e);
-        const qsfx::Scale se = qsfx::scale_for((int)(e >> 20), p.em[2]);
-        rho[idx[m]] = make_double2(lin1(x.re, f[2], se), lin1(x.im, f[2], se));
-      }
+      for (int u = 0; u < 4; ++u) ob[1][u] = rho[idx[oth[4 + u]]];
+      scale_batch(ob[0], 0);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ob[0][u] = rho[idx[oth[8 + u]]];
+      scale_batch(ob[1], 4);
+      scale_batch(ob[0], 8);
     }
   }
 }
