@@ -24,7 +24,12 @@
 // (1, 256, 65536, 0, ...) against a B whose column holds P = p0 + 256 p1 +
 // 65536 p2 in three bf16-exact parts.
 //
-// Work mapping: thread (warp w, lane) owns row g = 32 (w mod 4) + lane (the
+// Two kernels share these pieces.  k_dense_ozaki (below; five targets, and any
+// pass of fewer tiles than SMs) runs every phase in every thread;
+// k_dense_ozaki_ws (two to four targets) gives gathering and slicing, MMA
+// issue and the epilogue to separate warps (its own comment further down).
+//
+// k_dense_ozaki's work mapping: thread (warp w, lane) owns row g = 32 (w mod 4) + lane (the
 // tensor-memory lane that warp may read) and the amplitudes l in
 // [c EPT, (c+1) EPT), c = w / 4, of that row, for the gather, the slicing and
 // the epilogue alike, so the row's exponent and base index stay in registers.
