@@ -235,6 +235,26 @@ inline TileOrder make_tile_order(const PauliTerm* terms, int n) {
   return o;
 }
 
+// Tile visited at virtual position v: zero bits inserted at the pivots into
+// c = v >> r, then the basis vectors selected by the low r bits of v.  So the
+// 2^r positions c 2^r .. (c + 1) 2^r - 1 are one coset of the span of the
+// basis, the tiles that a term's flip mask pairs with each other.  Host and
+// device (the host build is checked on the CPU).
+#if defined(__CUDACC__)
+__host__ __device__
+#endif
+inline uint64_t ordered_tile(uint64_t v, const TileOrder& o) {
+  const int r = o.r;
+  uint64_t t = v >> r;
+  for (int j = 0; j < r; ++j) {
+    const int p = o.piv[j];
+    t = ((t >> p) << (p + 1)) | (t & ((1ull << p) - 1));
+  }
+  for (int j = 0; j < r; ++j)
+    if ((v >> j) & 1) t ^= o.basis[j];
+  return t;
+}
+
 // Block composition (qs_fuse.cu): one gate of a block, on block-local bits.
 struct ComposeInstr {
   int kind;              // 0 dense with controls, 1 diagonal, 2 Pauli gadget

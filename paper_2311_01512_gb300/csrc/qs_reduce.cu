@@ -159,21 +159,6 @@ struct TileCounter {
   }
 };
 
-// Tile visited at virtual position v (TileOrder in qs_internal.h): zero bits
-// inserted at the pivots into c = v >> r, then the basis vectors selected by
-// the low r bits of v.
-__device__ __forceinline__ uint64_t ordered_tile(uint64_t v, const TileOrder& o) {
-  const int r = o.r;
-  uint64_t t = v >> r;
-  for (int j = 0; j < r; ++j) {
-    const int p = o.piv[j];
-    t = ((t >> p) << (p + 1)) | (t & ((1ull << p) - 1));
-  }
-  for (int j = 0; j < r; ++j)
-    if ((v >> j) & 1) t ^= o.basis[j];
-  return t;
-}
-
 // Work mapping: a block takes tiles of 256 E consecutive amplitudes (thread t
 // holds amplitudes t, t + 256, ... of the tile) and runs every group over the
 // tile.  Tiles are handed out in increasing virtual order by a counter
