@@ -34,10 +34,10 @@ STATE_SEED = 2311015121
 CPU_SAMPLE_QUBITS = 20
 ARITH_CODE = {"fx": 2, "df": 0, "f64": 1}     # qs_arith
 DTYPE = {
-    "fx": ("c128 storage; arithmetic at least FP64: one-target gates, diagonals and gadgets in 60-bit block "
-           "fixed point with exact integer products and one rounding per output (error <= 2^-53 |y| + "
-           "2^-55 max|x| max|m|), 2-5-target gates as eight exact 7-bit slices (56-bit operands) on the "
-           "bf16 tensor cores"),
+    "fx": ("c128 storage; arithmetic at least FP64: one- and two-target gates, diagonals and gadgets in 60-bit "
+           "block fixed point with exact integer products and one rounding per output (error <= 2^-53 |y| + "
+           "2^-55 max|x| max|m|, 2^-54 for the two-target gates' eight terms), 3-5-target gates as eight exact "
+           "7-bit slices (56-bit operands) on the bf16 tensor cores"),
     "df": "c128 storage, double-float (2xf32, 47-bit) arithmetic",
     "f64": "c128 storage, native f64 arithmetic",
 }

@@ -226,6 +226,26 @@ qsk::FxPart fx_part(double v, int em) {
 }
 bool is_fx(const qs_state* s) { return s->prec == QS_C128 && s->arith == QS_ARITH_FX; }
 
+// Superoperator sum_m conj(K_m) (x) K_m of one-qubit operators K_m (row-major
+// 2x2, re/im interleaved) as a 4x4 matrix (Sec. "Kraus map"): row r = 2 i + k,
+// column c = 2 j + l, entry sum_m conj(K_m[i][j]) K_m[k][l]; index bit 0 acts
+// on the ket qubit t, bit 1 on the bra qubit t + N.  The same entries as the
+// device superoperator kernel; here the block fixed-point constants of the
+// one pass are made from it on the host.
+void superop1(const double* kraus, int num_ops, double* sup) {
+  for (int e = 0; e < 32; ++e) sup[e] = 0.0;
+  for (int m = 0; m < num_ops; ++m) {
+    const double* K = kraus + 8 * m;
+    for (int r = 0; r < 4; ++r)
+      for (int c = 0; c < 4; ++c) {
+        const int a = 2 * (r >> 1) + (c >> 1), b = 2 * (r & 1) + (c & 1);
+        const double ar = K[2 * a], ai = -K[2 * a + 1], br = K[2 * b], bi = K[2 * b + 1];
+        sup[2 * (4 * r + c)] += ar * br - ai * bi;
+        sup[2 * (4 * r + c) + 1] += ar * bi + ai * br;
+      }
+  }
+}
+
 // One dense or one-target gate pass on storage positions (already shifted).
 qs_status gate_pass(qs_state* s, const std::vector<int>& ctrls, const std::vector<int>& targs, const double* host_mat,
                     const void* dev_mat, int conj, bool force_dense) {
@@ -253,6 +273,38 @@ qs_status gate_pass(qs_state* s, const std::vector<int>& ctrls, const std::vecto
     p.ctrl_mask = cmask;
     p.npairs = 1ull << (s->ns - p.nins);
     return cuda_status(qsk::launch_gate1_fx(s->amps, p, s->stream));
+  }
+  if (n == 2 && is_fx(s) && host_mat && !force_dense) {
+    // u_jk = mat[4 j + k] (conjugated when conj); rows (out_j.re, out_j.im)
+    // over (a_k.re, a_k.im), k = 0..3
+    qsk::Gate2FxParams p{};
+    for (int j = 0; j < 4; ++j) {
+      double ur[4], ui[4];
+      for (int k = 0; k < 4; ++k) {
+        ur[k] = host_mat[2 * (4 * j + k)];
+        ui[k] = conj ? -host_mat[2 * (4 * j + k) + 1] : host_mat[2 * (4 * j + k) + 1];
+      }
+      p.em[j] = fx_em({ur[0], ui[0], ur[1], ui[1], ur[2], ui[2], ur[3], ui[3]});
+      for (int k = 0; k < 4; ++k) {
+        p.m[2 * j][2 * k] = fx_part(ur[k], p.em[j]);
+        p.m[2 * j][2 * k + 1] = fx_part(-ui[k], p.em[j]);
+        p.m[2 * j + 1][2 * k] = fx_part(ui[k], p.em[j]);
+        p.m[2 * j + 1][2 * k + 1] = fx_part(ur[k], p.em[j]);
+      }
+    }
+    std::vector<int> ins(ctrls);
+    ins.push_back(targs[0]);
+    ins.push_back(targs[1]);
+    std::sort(ins.begin(), ins.end());
+    p.nins = (int)ins.size();
+    for (int i = 0; i < p.nins; ++i) p.ins[i] = (int8_t)ins[i];
+    p.t0 = targs[0];
+    p.t1 = targs[1];
+    p.lo = std::min(targs[0], targs[1]);
+    p.hi = std::max(targs[0], targs[1]);
+    p.ctrl_mask = cmask;
+    p.nquads = 1ull << (s->ns - p.nins);
+    return cuda_status(qsk::launch_gate2_fx(s->amps, p, s->stream));
   }
   if (n == 1 && df && !force_dense) {
     qsk::Gate1DfParams p{};
@@ -579,6 +631,12 @@ qs_status qs_apply_ctrl_multi_target(qs_state* s, const int* ctrls, int nctrl, c
   qs_status st = check_qubits(s->nq, targs, ntarg, ctrls, nctrl);
   if (st != QS_OK) return st;
   std::vector<int> c(ctrls, ctrls + nctrl), t(targs, targs + ntarg);
+  if (s->is_density && nctrl == 0 && ntarg == 1 && is_fx(s)) {
+    // U on t and U^* on t + N in one two-target pass of conj(U) (x) U
+    double sup[32];
+    superop1(mat, 1, sup);
+    return gate_pass(s, {}, {t[0], t[0] + s->nq}, sup, nullptr, 0);
+  }
   const size_t mat_bytes = sizeof(double) * 2 * (size_t(1) << (2 * ntarg));
   const void* dmat = nullptr;
   int slot = -1;
@@ -727,6 +785,12 @@ qs_status qs_apply_kraus(qs_state* s, const int* targs, int n, const double* kra
   if (st != QS_OK) return st;
   const size_t kbytes = sizeof(double) * 2 * (size_t(1) << (2 * n)) * (size_t)num_ops;
   if (kbytes > kSlotBytes) return QS_ERR_ARG;
+  if (n == 1 && is_fx(s)) {
+    // S on (t, t + N), one two-target pass with its constants made on the host
+    double sup[32];
+    superop1(kraus, num_ops, sup);
+    return gate_pass(s, {}, {targs[0], targs[0] + s->nq}, sup, nullptr, 0);
+  }
   const void* dk = nullptr;
   void* dsup = nullptr;
   int slot_k = -1, slot_s = -1;

@@ -43,8 +43,17 @@
 // from: truncation of the x_k (< 2^(ex-1082) each, times |m_k|), rounding of
 // the m_k (<= 2^(em-1083) each, times |x_k|), the dropped l_x l_m and floor
 // (< 5 units of 2^(ex+em-2104) = 5 2^-58 2^(ex+em-2046)), then the final
-// rounding.  The host test tests/host/fx_check.cpp checks this bound against
-// exact rational arithmetic.
+// rounding.
+//
+// An output over K <= 8 terms (the eight real parts of the four amplitudes of
+// a two-target gate) accumulates its terms 0..3 and 4..7 in two such
+// accumulators, so every partial sum keeps the bounds above, and
+//     V = A_lo + floor(B_lo / 2^30) + A_hi + floor(B_hi / 2^30),   |V| < 2^63
+// (|V| is below sum_k |X_k M_k| / 2^60 + 10 <= 8 (2^60 - 2^7) + 10).  The
+// error terms count as before with K = 8 and two floors, (7 K + 8) 2^-60 X Mx:
+//     |fx(y) - y| <= 2^-53 |y| + 2^-54 X Mx    (K <= 8).
+// The host test tests/host/fx_check.cpp checks both bounds against exact
+// rational arithmetic.
 //
 // The same code compiles for the host (tested on the CPU) and the device.
 #pragma once
@@ -192,16 +201,23 @@ QS_HD Scale scale_for(int ex, int em) {
   return s;
 }
 
-QS_HD double finish_s(const Acc& a, Scale s) {
-  const double r = i64_to_double(acc_value(a));
+// V rounded once to double and scaled by 2^sc.
+QS_HD double finish_v(int64_t v, Scale s) {
+  const double r = i64_to_double(v);
   uint32_t hw, lw;
   qsdf::d2w(r, hw, lw);
   const bool ok = (hw & 0x7FFFFFFFu) > s.thr;
   return qsdf::w2d(ok ? hw + s.inc : 0u, ok ? lw : 0u);
 }
 
+QS_HD double finish_s(const Acc& a, Scale s) { return finish_v(acc_value(a), s); }
+
+// An output accumulated in two halves (terms 0..3 in lo, 4..7 in hi).
+QS_HD double finish2_s(const Acc& lo, const Acc& hi, Scale s) { return finish_v(acc_value(lo) + acc_value(hi), s); }
+
 // The accumulated sum as a double: V rounded once, times 2^(ex + em - 2104).
 QS_HD double finish(const Acc& a, int ex, int em) { return finish_s(a, scale_for(ex, em)); }
+QS_HD double finish2(const Acc& lo, const Acc& hi, int ex, int em) { return finish2_s(lo, hi, scale_for(ex, em)); }
 
 // Largest biased exponent of a set of doubles (exponent fields compared in
 // place, on the high words).

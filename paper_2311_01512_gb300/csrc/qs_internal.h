@@ -129,6 +129,21 @@ struct Gate1FxParams {
   int8_t ins[kMaxQ];
 };
 
+// Two-target gate: rows r = 2 j + (0: re, 1: im) of output amplitude j over
+// the columns c = 2 k + (0: re, 1: im) of input amplitude k, j and k = b0 + 2 b1
+// with b0 the bit at t0 and b1 the bit at t1; rows 2j and 2j+1 share the
+// exponent em[j] (of u_j0 .. u_j3).
+struct Gate2FxParams {
+  FxPart m[8][8];
+  int em[4];
+  uint64_t nquads;
+  uint64_t ctrl_mask;
+  int t0, t1;
+  int lo, hi;            // the targets sorted (the no-control index path)
+  int nins;
+  int8_t ins[kMaxQ];
+};
+
 // Diagonal entry d_j: parts of Re, Im and -Im with their shared exponent.
 struct DiagFxEntry {
   FxPart re, im, nim;
@@ -331,6 +346,7 @@ cudaError_t launch_diag_df(void* amps, const DiagParams& p, cudaStream_t st);
 cudaError_t launch_gadget_df(void* amps, const GadgetDfParams& p, cudaStream_t st);
 // complex128 in block fixed point (qs_gates_fx.cu)
 cudaError_t launch_gate1_fx(void* amps, const Gate1FxParams& p, cudaStream_t st);
+cudaError_t launch_gate2_fx(void* amps, const Gate2FxParams& p, cudaStream_t st);
 cudaError_t launch_diag_fx(void* amps, const DiagFxParams& p, cudaStream_t st);
 cudaError_t launch_gadget_fx(void* amps, const GadgetFxParams& p, cudaStream_t st);
 // G_DEPOL1, G_DEPOL2, G_DAMP, G_PAULI1

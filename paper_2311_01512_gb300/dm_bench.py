@@ -45,8 +45,8 @@ def op_bytes(op, nq):
     kind = op["op"]
     if kind == "unitary":
         s = len(op["ctrls"])
-        if s == 0 and len(op["targs"]) == 2:
-            return full                     # one pass of conj(U) (x) U on 4 targets
+        if s == 0 and len(op["targs"]) <= 2:
+            return full                     # one pass of conj(U) (x) U on 2 or 4 targets
         return 2 * full >> s                # U on t, then U* on t + N
     if kind == "gadget":
         return 2 * full
@@ -169,7 +169,8 @@ def large(qs, wl, torch, peak_gbs, reps=1):
         e1.synchronize()
         ex_ms = e0.elapsed_time(e1)
     out = {"workload": "15-qubit density matrix (30-qubit Choi vector, 16 GiB), 400 ops",
-           "arithmetic": "complex128, the default block fixed point (dense 2-5-target passes: eight slices)",
+           "arithmetic": "complex128, the default block fixed point (two-target passes on the CUDA cores, "
+                         "3-5-target passes as eight slices on the tensor cores)",
            "runs": reps, "ms_total": total_ms, "ms_runs": totals, "gb_total": total_bytes / 1e9,
            "gbs": total_bytes / total_ms / 1e6,
            "frac_of_peak": (total_bytes / total_ms / 1e6) / peak_gbs if peak_gbs else None,

@@ -1,8 +1,8 @@
 """Fixed sequence of hot-path kernel launches for profiling (ncu) at a chosen
 size, in the default complex128 arithmetic (block fixed point): one-target
 gate, 3-qubit diagonal, weight-6 Pauli gadget, a Z-only (phase) gadget, dense
-gates on 2, 3, 4 and 5 targets (bf16 tensor cores, eight integer slices; two
-targets run on the three-target kernel), and a 5-target dense gate on a
+gates on 2 targets (CUDA cores, block fixed point) and on 3, 4 and 5 targets
+(bf16 tensor cores, eight integer slices), and a 5-target dense gate on a
 complex64 state (tf32 tensor cores), each repeated.
 
     python -m paper_2311_01512_gb300.profile_ops --qubits 28 --reps 3
@@ -17,7 +17,8 @@ bench's kernel families and stamped with the kernel sources' digest:
         --scale-to 30 --out profiles/dram_traffic.json
 
 With --dense-times it instead times complex128 dense gates (block fixed
-point: eight-slice tensor-core kernels) on a state of --qubits qubits at
+point: the two-target CUDA-core kernel, eight-slice tensor-core kernels for
+three to five targets) on a state of --qubits qubits at
 three placements per target count (lowest qubits, spread, highest qubits)
 and one controlled case, each the median of --reps CUDA-event timings after
 one untimed launch, and prints ms and GB/s of amplitudes read and written:
@@ -35,7 +36,7 @@ reduction) and in double-float:
 With --all it instead launches every kernel family of the library once, on
 a statevector of --qubits qubits in both precisions and a density matrix of
 --qubits / 2 qubits (its Choi vector as large): the streaming gates, the
-tensor-core gates on 2-6 targets, SWAP, the channels, the superoperator and
+dense gates on 2-6 targets, SWAP, the channels, the superoperator and
 Kraus map, the partial trace, the expectation kernels, norm and trace, the
 fused-block composition.  It is the sequence for a per-kernel table of DRAM
 bytes and times.
@@ -49,7 +50,7 @@ import numpy as np
 
 # launch order of one repetition -> the bench's kernel family names
 _FAMILIES = {"k_gate1_fx": ["k_gate1"], "k_diag_fx": ["k_diag"], "k_gadget_fx": ["k_gadget"],
-             "k_phase_fx": ["k_phase"], "k_dense_ozaki_ws<3": ["k_dense<2>", "k_dense<3>"],
+             "k_phase_fx": ["k_phase"], "k_gate2_fx": ["k_dense<2>"], "k_dense_ozaki_ws<3": ["k_dense<3>"],
              "k_dense_ozaki_ws<4": ["k_dense<4>"], "k_dense_ozaki<5": ["k_dense<5>"], "k_dense_tc<5": ["c64 k_dense<5>"]}
 
 
@@ -233,7 +234,7 @@ def every_kernel(nq):
         qs.qs_apply_pauli_gadget(h, [0, 3, 8, 15, 22, nq - 1], [1, 2, 3, 1, 2, 3], 0.4)   # gadget
         qs.qs_apply_pauli_gadget(h, [0, 4, 9, 17], [3, 3, 3, 3], 0.4)        # phase gadget
         for n in range(2, 7 if prec == qs.QS_C64 else 6):
-            qs.qs_apply_ctrl_multi_target(h, [], targets[n], mats[n])        # tensor-core gates
+            qs.qs_apply_ctrl_multi_target(h, [], targets[n], mats[n])        # dense gates (c128 2: CUDA cores)
         qs.qs_apply_swap(h, 3, 17)
         qs.qs_expec_pauli_sum(h, paulis, coeffs)                             # off-diagonal terms
         qs.qs_expec_pauli_sum(h, zs, rng.standard_normal(16))                # Walsh-Hadamard diagonal terms

@@ -7,10 +7,14 @@ For every dot product y = sum_k x_k m_k, K <= 4, the result must satisfy
 
     |fx(y) - y| <= 2^-53 |y| + 2^-55 max|x_k| max|m_k|
 
+and for 4 < K <= 8 (two accumulators, the two-target gate's rows)
+
+    |fx(y) - y| <= 2^-53 |y| + 2^-54 max|x_k| max|m_k|
+
 (plus the flush of subnormal inputs and outputs), every fixed-point constant
 must be m rounded to nearest on its group's grid, and on random unitary gate
-rows the fixed-point results must be on average at least as accurate as IEEE
-FP64 evaluation with fused multiply-adds.  CPU only."""
+rows (one and two targets) the fixed-point results must be on average at least
+as accurate as IEEE FP64 evaluation with fused multiply-adds.  CPU only."""
 
 import math
 import os
@@ -78,7 +82,8 @@ def check_case(xs, ms, y, consts):
     # flushed subnormal inputs contribute their whole product to the error
     flushed = sum(abs(Fraction(x) * Fraction(m)) for x, m in zip(xs, ms) if x != 0 and bexp(x) == 0)
     flushed += sum(abs(Fraction(x) * Fraction(m)) for x, m in zip(xs, ms) if m != 0 and bexp(m) == 0)
-    bound = U * abs(exact) + Fraction(1, 2 ** 55) * X * M + flushed + Fraction(TINY)
+    second = Fraction(1, 2 ** 55) if len(xs) <= 4 else Fraction(1, 2 ** 54)
+    bound = U * abs(exact) + second * X * M + flushed + Fraction(TINY)
     err = abs(Fraction(y) - exact)
     assert err <= bound, (xs, ms, y, float(exact), float(err), float(bound))
     # the constants: m rounded to nearest on the grid 2^(em - 1082) of its group
@@ -97,10 +102,10 @@ def gauss_pair(rng, spread):
     return rng.gauss(0.0, 1.0) * 2.0 ** rng.randint(-spread, 0)
 
 
-def random_cases(rng, n):
+def random_cases(rng, n, kmin=1, kmax=4):
     cases = []
     for it in range(n):
-        K = rng.randint(1, 4)
+        K = rng.randint(kmin, kmax)
         spread = (0, 3, 12, 80)[it % 4]
         scale = 2.0 ** rng.randint(-40, 40)
         xs = [gauss_pair(rng, spread) * scale for _ in range(K)]
@@ -158,6 +163,29 @@ def unitary_rows(rng, n):
     return cases
 
 
+def unitary4_rows(rng, n):
+    """Rows of random 4x4 unitaries realified over the eight parts of four
+    amplitudes (moduli near 2^-15): the two-target gate's rows."""
+    cases = []
+    for _ in range(n):
+        cols = []
+        for _ in range(4):   # Gram-Schmidt on four Gaussian columns
+            v = [complex(rng.gauss(0, 1), rng.gauss(0, 1)) for _ in range(4)]
+            for c in cols:
+                ip = sum(a.conjugate() * b for a, b in zip(c, v))
+                v = [b - ip * a for a, b in zip(c, v)]
+            nrm = math.sqrt(sum(abs(z) ** 2 for z in v))
+            cols.append([z / nrm for z in v])
+        x = [rng.gauss(0, 1) * 2.0 ** -15 for _ in range(8)]   # (re, im) of four amplitudes
+        j = rng.randrange(4)
+        u = [cols[k][j] for k in range(4)]                       # row j: u_jk
+        re = [v for k in range(4) for v in (u[k].real, -u[k].imag)]
+        im = [v for k in range(4) for v in (u[k].imag, u[k].real)]
+        cases.append((x, re))
+        cases.append((x, im))
+    return cases
+
+
 def test_fx_bound_random(fx_exe):
     rng = random.Random(2311015120)
     cases = random_cases(rng, 12000)
@@ -205,6 +233,56 @@ def test_fx_not_less_accurate_than_fp64(fx_exe):
         s = sum(abs(Fraction(x) * Fraction(m)) for x, m in zip(xs, ms))
         y64 = ms[0] * xs[0]
         for k in range(1, 4):
+            y64 = fma(ms[k], xs[k], y64)
+        e_fx.append(float(err / (U * s)))
+        e_64.append(float(abs(Fraction(y64) - exact) / (U * s)))
+    e_fx.sort()
+    e_64.sort()
+    q = int(0.999 * len(e_fx))
+    assert sum(e_fx) / len(e_fx) <= sum(e_64) / len(e_64)
+    assert e_fx[q] <= e_64[q]
+
+
+def test_fx_bound_eight_terms(fx_exe):
+    """Dot products of five to eight terms, summed in two accumulators as the
+    two-target gate does, within the K <= 8 bound."""
+    rng = random.Random(2311015123)
+    cases = random_cases(rng, 8000, 5, 8)
+    for (xs, ms), (y, consts) in zip(cases, run_cases(fx_exe, cases)):
+        check_case(xs, ms, y, consts)
+
+
+def test_fx_eight_terms_extremes(fx_exe):
+    """The largest sums eight terms can reach: every x and m with all
+    significand bits set at the top of its block, all products of one sign
+    (|V| within 2^11 of 2^63), and their cancelling mixtures."""
+    top = 2.0 - 2.0 ** -52
+    cases = []
+    for sx in (1.0, -1.0):
+        for sm in (1.0, -1.0):
+            cases.append(([sx * top] * 8, [sm * top] * 8))
+    cases.append(([top, -top] * 4, [top] * 8))
+    cases.append(([top] * 7 + [2.0 ** -60], [top] * 8))
+    cases.append(([top * 2.0 ** -15] * 8, [top * 2.0 ** -3] * 8))
+    for (xs, ms), (y, consts) in zip(cases, run_cases(fx_exe, cases)):
+        check_case(xs, ms, y, consts)
+    ys = [y for y, _ in run_cases(fx_exe, cases[:4])]
+    assert ys[0] == ys[3] > 0 and ys[1] == ys[2] == -ys[0]
+
+
+def test_fx_two_target_rows_not_less_accurate_than_fp64(fx_exe):
+    """On the two-target gate's rows (random 4x4 unitaries, random amplitudes)
+    the mean and 99.9th percentile of the error, in units of 2^-53 sum|x_k m_k|,
+    are no larger than those of FP64 evaluated as a product then seven fused
+    multiply-adds."""
+    rng = random.Random(2311015124)
+    cases = unitary4_rows(rng, 1500)
+    e_fx, e_64 = [], []
+    for (xs, ms), (y, consts) in zip(cases, run_cases(fx_exe, cases)):
+        err, exact, _ = check_case(xs, ms, y, consts)
+        s = sum(abs(Fraction(x) * Fraction(m)) for x, m in zip(xs, ms))
+        y64 = ms[0] * xs[0]
+        for k in range(1, 8):
             y64 = fma(ms[k], xs[k], y64)
         e_fx.append(float(err / (U * s)))
         e_64.append(float(abs(Fraction(y64) - exact) / (U * s)))
