@@ -82,7 +82,13 @@ typedef enum { QS_C64 = 0, QS_C128 = 1 } qs_prec;
  *     multiply-adds, and each output is rounded once.  Error of an output
  *     y = sum_k x_k m_k: at most 2^-53 |y| + 2^-55 max|x_k| max|m_k|.
  *     Inputs must be finite; subnormals count as zero.
- *   - Dense gates with 2..5 targets run on the bf16 tensor cores with eight
+ *   - Two-target gates use the same block fixed point (eight terms per
+ *     output, summed in two 64-bit accumulators of four terms): at most
+ *     2^-53 |y| + 2^-54 max|x_k| max|m_k|.  So does a one-qubit unitary or
+ *     Kraus map on a density matrix, applied as one two-target pass of
+ *     conj(U) (x) U or of its superoperator on (t, t + N).
+ *   - Dense gates with 3..5 targets (and two-target fused blocks) run on the
+ *     bf16 tensor cores with eight
  *     exact 7-bit integer slices of 56-bit operands (rows and columns scaled
  *     by their largest exponent), exact FP32 level sums, one rounding.
  *   - Everything else (6-target dense gates, dephasing, superoperators,
@@ -164,7 +170,9 @@ qs_status qs_init_pure_densmatr(qs_state* rho, const qs_state* psi, double weigh
  * (re, im) doubles.  1 <= ntarg <= QS_MAX_DENSE_TARGETS, nctrl >= 0; ctrls
  * may be NULL when nctrl = 0.  On a density matrix this applies
  * U rho U^dagger: U on (ctrls, targs), then U^* on the same qubits shifted by
- * N (Sec. "Unitary gates", Eq. (unitary on a vectorised density matrix)). */
+ * N (Sec. "Unitary gates", Eq. (unitary on a vectorised density matrix));
+ * without controls, one or two targets (one: in block fixed point; two: on
+ * the tensor-core path) take one pass of conj(U) (x) U instead. */
 qs_status qs_apply_ctrl_multi_target(qs_state* state, const int* ctrls, int nctrl, const int* targs,
                                      int ntarg, const double* mat);
 
@@ -192,7 +200,9 @@ qs_status qs_apply_pauli_gadget(qs_state* state, const int* targs, const int* pa
 
 /* Kraus map rho -> sum_m K_m rho K_m^dagger on n targets, 1 <= n <= 3
  * (Sec. "Kraus map"): the superoperator S = sum_m conj(K_m) (x) K_m is built
- * on the device and applied as a dense 2n-target gate on targs u targs + N.
+ * on the device and applied as a dense 2n-target gate on targs u targs + N
+ * (for n = 1 in block fixed point its 16 entries are formed on the host with
+ * the pass's fixed-point constants).
  * kraus: num_ops matrices of 2^n x 2^n complex128, each row-major (re, im).
  * Density matrices only. */
 qs_status qs_apply_kraus(qs_state* state, const int* targs, int n, const double* kraus, int num_ops);
