@@ -457,8 +457,9 @@ def main_ours(args):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 16,
                "upload_ms_per_step": sum(up_ms) / len(up_ms), "ms_per_step": e_total / K, "steps": K,
                "clocks": e_clk,
-               "note": ("pinned host state uploaded through qs_set_amps every step, %d ops, norm read back, "
-                        "in sequence on one device state" % NUM_OPS),
+               "note": ("pinned host state uploaded through qs_set_amps every step (read by the library's copy "
+                        "kernel from page-locked memory), %d ops, norm read back, in sequence on one device state"
+                        % NUM_OPS),
                "final_norm": out_norm.real}
 
     fused = None

@@ -147,7 +147,13 @@ qs_status qs_device_ptr(const qs_state* state, void** d_amps);
 
 /* Copy count amplitudes from host memory (interleaved re, im in the state's
  * precision) into storage indices [first, first + count).  Queued on the
- * state's stream; pinned host memory makes the copy asynchronous. */
+ * state's stream.  From page-locked host memory (pinned allocations or
+ * registered ranges) a copy of at least 1 MiB whose host and device
+ * addresses and size are multiples of 16 bytes is made by a kernel that
+ * reads the buffer through its mapped device pointer; any other copy goes
+ * through cudaMemcpyAsync (synchronous staging for pageable memory).  The
+ * host buffer must stay valid and unchanged until the stream reaches the
+ * copy.  QS_ERR_CUDA if the launch or copy fails. */
 qs_status qs_set_amps(qs_state* state, const void* host_amps, size_t first, size_t count);
 
 /* Copy storage indices [first, first + count) to host memory; synchronises. */

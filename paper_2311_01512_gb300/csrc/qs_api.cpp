@@ -588,14 +588,28 @@ qs_status qs_device_ptr(const qs_state* s, void** d_amps) {
   return QS_OK;
 }
 
+// Uploads of at least this many bytes from page-locked memory use the SM copy.
+constexpr size_t kSmCopyMinBytes = size_t(1) << 20;
+
 qs_status qs_set_amps(qs_state* s, const void* host_amps, size_t first, size_t count) {
   if (s && s->rec) return QS_ERR_ARG;   // not while recording
   if (!s || (!host_amps && count)) return QS_ERR_ARG;
   const size_t total = size_t(1) << s->ns;
   if (first > total || count > total - first) return QS_ERR_ARG;
   const size_t b = amp_bytes(s->prec);
-  return cuda_status(cudaMemcpyAsync(static_cast<char*>(s->amps) + first * b, host_amps, count * b,
-                                     cudaMemcpyHostToDevice, s->stream));
+  char* dst = static_cast<char*>(s->amps) + first * b;
+  const size_t bytes = count * b;
+  // Page-locked host memory (pinned allocations, registered ranges) is read by
+  // the SMs through its mapped device pointer (qsk::launch_copy16); pageable
+  // memory, small copies and unaligned ranges go through the copy engine.
+  if (bytes >= kSmCopyMinBytes && bytes % 16 == 0 && reinterpret_cast<uintptr_t>(dst) % 16 == 0) {
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, host_amps) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+        attr.devicePointer && reinterpret_cast<uintptr_t>(attr.devicePointer) % 16 == 0)
+      return cuda_status(qsk::launch_copy16(dst, attr.devicePointer, bytes, s->stream));
+    cudaGetLastError();   // a failed query leaves no sticky error; clear it
+  }
+  return cuda_status(cudaMemcpyAsync(dst, host_amps, bytes, cudaMemcpyHostToDevice, s->stream));
 }
 
 qs_status qs_get_amps(const qs_state* s, void* host_amps, size_t first, size_t count) {

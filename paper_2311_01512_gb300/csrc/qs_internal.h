@@ -383,6 +383,8 @@ cudaError_t launch_superop(const double* kraus, int num_ops, int n, double* sup,
 cudaError_t launch_dm_from_pure(qs_prec prec, void* rho, const void* psi, int nq, double weight,
                                 int accumulate, cudaStream_t st, bool f64);
 cudaError_t launch_init_zero(qs_prec prec, void* amps, int ns, cudaStream_t st);
+// bytes (a multiple of 16) from src (device-accessible, 16-byte aligned) to dst
+cudaError_t launch_copy16(void* dst, const void* src, size_t bytes, cudaStream_t st);
 
 // Reductions: stage one writes kReduceBlocks complex128 partial sums, stage two
 // sums them in a fixed order into result[0] (added to result[0] if accumulate).
