@@ -160,18 +160,21 @@ __global__ void __launch_bounds__(256) k_diag_fx(double2* __restrict__ psi, cons
 #pragma unroll
   for (int q = 0; q < N; ++q) tp[q] = p.tpos[q];
   __syncthreads();
-  // two amplitudes per iteration (i and i + stride): both loads are in flight together
+  // four amplitudes per iteration (i + u stride, u < 4): their loads are in flight together
+  constexpr int U = 4;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.namps; i += 2 * stride) {
-    const uint64_t i2 = i + stride;
-    const bool has2 = i2 < p.namps;
-    const double2 v0 = psi[i];
-    const double2 v1 = has2 ? psi[i2] : make_double2(0.0, 0.0);
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.namps; i += U * stride) {
+    double2 vs[U];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const uint64_t iu = u ? i2 : i;
-      if (u && !has2) break;
-      const double2 v = u ? v1 : v0;
+    for (int u = 0; u < U; ++u) {
+      const uint64_t iu = i + u * stride;
+      vs[u] = iu < p.namps ? psi[iu] : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint64_t iu = i + u * stride;
+      if (iu >= p.namps) break;
+      const double2 v = vs[u];
       int j = 0;
 #pragma unroll
       for (int q = 0; q < N; ++q) j |= (int)((iu >> tp[q]) & 1) << q;
