@@ -14,6 +14,7 @@
 
 #include "qs.h"
 #include "qs_df.cuh"
+#include "qs_superop1.h"
 #include "qs_fx.cuh"
 #include "qs_alloc.h"
 #include "qs_internal.h"
@@ -225,26 +226,6 @@ qsk::FxPart fx_part(double v, int em) {
   return qsk::FxPart{q.h, q.l};
 }
 bool is_fx(const qs_state* s) { return s->prec == QS_C128 && s->arith == QS_ARITH_FX; }
-
-// Superoperator sum_m conj(K_m) (x) K_m of one-qubit operators K_m (row-major
-// 2x2, re/im interleaved) as a 4x4 matrix (Sec. "Kraus map"): row r = 2 i + k,
-// column c = 2 j + l, entry sum_m conj(K_m[i][j]) K_m[k][l]; index bit 0 acts
-// on the ket qubit t, bit 1 on the bra qubit t + N.  The same entries as the
-// device superoperator kernel; here the block fixed-point constants of the
-// one pass are made from it on the host.
-void superop1(const double* kraus, int num_ops, double* sup) {
-  for (int e = 0; e < 32; ++e) sup[e] = 0.0;
-  for (int m = 0; m < num_ops; ++m) {
-    const double* K = kraus + 8 * m;
-    for (int r = 0; r < 4; ++r)
-      for (int c = 0; c < 4; ++c) {
-        const int a = 2 * (r >> 1) + (c >> 1), b = 2 * (r & 1) + (c & 1);
-        const double ar = K[2 * a], ai = -K[2 * a + 1], br = K[2 * b], bi = K[2 * b + 1];
-        sup[2 * (4 * r + c)] += ar * br - ai * bi;
-        sup[2 * (4 * r + c) + 1] += ar * bi + ai * br;
-      }
-  }
-}
 
 // One dense or one-target gate pass on storage positions (already shifted).
 qs_status gate_pass(qs_state* s, const std::vector<int>& ctrls, const std::vector<int>& targs, const double* host_mat,
@@ -648,7 +629,7 @@ qs_status qs_apply_ctrl_multi_target(qs_state* s, const int* ctrls, int nctrl, c
   if (s->is_density && nctrl == 0 && ntarg == 1 && is_fx(s)) {
     // U on t and U^* on t + N in one two-target pass of conj(U) (x) U
     double sup[32];
-    superop1(mat, 1, sup);
+    qsh::superop1(mat, 1, sup);
     return gate_pass(s, {}, {t[0], t[0] + s->nq}, sup, nullptr, 0);
   }
   const size_t mat_bytes = sizeof(double) * 2 * (size_t(1) << (2 * ntarg));
@@ -802,7 +783,7 @@ qs_status qs_apply_kraus(qs_state* s, const int* targs, int n, const double* kra
   if (n == 1 && is_fx(s)) {
     // S on (t, t + N), one two-target pass with its constants made on the host
     double sup[32];
-    superop1(kraus, num_ops, sup);
+    qsh::superop1(kraus, num_ops, sup);
     return gate_pass(s, {}, {targs[0], targs[0] + s->nq}, sup, nullptr, 0);
   }
   const void* dk = nullptr;
