@@ -224,21 +224,18 @@ __global__ void __launch_bounds__(256) k_gadget_fx(double2* __restrict__ psi, co
 // Phase gadget: alpha_i -> (c + i s_i) alpha_i, s_i = -+sin(phi) by parity.
 __global__ void __launch_bounds__(256) k_phase_fx(double2* __restrict__ psi, const __grid_constant__ GadgetFxParams p) {
   const Part c = part(p.c), s = part(p.s), ns = part(p.ns);
-  // four amplitudes per iteration (i + u stride, u < 4): their loads are in flight together
-  constexpr int U = 4;
+  // two amplitudes per iteration (i and i + stride): both loads are in flight together
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.nwork; i += U * stride) {
-    double2 vs[U];
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.nwork; i += 2 * stride) {
+    const uint64_t i2 = i + stride;
+    const bool has2 = i2 < p.nwork;
+    const double2 v0 = psi[i];
+    const double2 v1 = has2 ? psi[i2] : make_double2(0.0, 0.0);
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint64_t iu = i + u * stride;
-      vs[u] = iu < p.nwork ? psi[iu] : make_double2(0.0, 0.0);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint64_t iu = i + u * stride;
-      if (iu >= p.nwork) break;
-      const double2 v = vs[u];
+    for (int u = 0; u < 2; ++u) {
+      const uint64_t iu = u ? i2 : i;
+      if (u && !has2) break;
+      const double2 v = u ? v1 : v0;
       const Wd wr = words(v.x), wi = words(v.y);
       const uint32_t exf = emax2(wr, wi);
       const bool odd = parity64(iu & p.yz);
